@@ -1,0 +1,232 @@
+"""FP64 CPU oracle for the Tucker-tensor Fock-exchange hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this package: only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` use it.  It shares no code with the CUDA library.
+
+It follows the paper (arXiv 2401.04189, "Convolution operation" section) step by step, in
+plain numpy float64, with ``np.tensordot`` as the only library primitive (one mode-n
+product = one tensordot):
+
+  rho_ij = psi_i * psi_j                                  pair density (the step before Eq. TuckerDecompField)
+  G_ij   = rho_ij x1 U1^T x2 U2^T x3 U3^T                 Tucker core on a shared basis (Eq. TuckerDecompField)
+  C_td[a,b] = w_b exp(-theta_t (x_a - x_b)^2)             1-D convolution matrix, nodal quadrature (Eq. discInteg)
+  A_td   = C_td U_d                                       1-D convolutions of the basis functions (Eq. final)
+  phi_ij = sum_t mu_t G_ij x1 A_t1 x2 A_t2 x3 A_t3        separable convolution (Eqs. gauss, final)
+  W_i    = - sum_j psi_j * phi_ij                         action of the exchange operator (Eqs. ExchangeOperator, hadam)
+  E_x    = 1/2 sum_i sum_x w(x) psi_i(x) W_i(x)           exact-exchange energy with alpha = 1 (Eq. for S[phi])
+
+Readings of the paper (it is silent on these): the basis U_d is shared by all pairs and
+orthonormal in the Euclidean inner product on nodal values; the 1-D integrals use the
+nodal trapezoid quadrature of the uniform grid; occupations are 1 and alpha = 1.
+
+Gradients are not in the paper; they are derived from the definitions above with
+L = sum_t mu_t (x)_d (A_td U_d^T), so that phi_ij = L rho_ij:
+  L^T y          = (sum_t mu_t y x1 A_t1^T x2 A_t2^T x3 A_t3^T) x1 U1 x2 U2 x3 U3
+  dE/dpsi_k      = w * W_k - sum_j psi_j * L^T(w * rho_kj)
+  VJP of W for a cotangent Wbar over the targets:
+    grad_tgt_k   = - sum_j psi_j * L^T(Wbar_k * psi_j)
+    grad_occ_j   = - sum_k Wbar_k * phi_kj - sum_k psi_k * L^T(Wbar_k * psi_j)
+
+Independent references used by the pins (brute force and closed forms) are at the end.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "Setup", "conv_matrix", "mode_product", "project", "expand", "expand_transpose",
+    "apply_L", "apply_LT", "pair_potential", "exchange_apply", "exchange_energy",
+    "exchange_energy_grad", "exchange_apply_vjp",
+    "direct_gaussian_kernel_potential", "direct_coulomb_potential",
+    "gaussian_charge_potential", "gaussian_kernel_charge_potential",
+]
+
+
+# ----------------------------------------------------------------------------------
+# set-up: 1-D convolution matrices (Eqs. quadVal / discInteg, with nodal quadrature)
+# ----------------------------------------------------------------------------------
+def conv_matrix(x, w, theta):
+    """C[a, b] = w_b * exp(-theta * (x_a - x_b)^2): the 1-D convolution integral of a
+    nodal field evaluated at node a by the trapezoid rule (Eq. discInteg)."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    d = x[:, None] - x[None, :]
+    return np.exp(-float(theta) * d * d) * w[None, :]
+
+
+class Setup:
+    """Everything that does not depend on the orbitals: grid, weights, basis, and the
+    Gaussian-sum coefficients of 1/r, plus the derived A_td = C_td U_d."""
+
+    def __init__(self, x, w, U, theta, mu):
+        self.x = [np.asarray(v, dtype=np.float64) for v in x]
+        self.w = [np.asarray(v, dtype=np.float64) for v in w]
+        self.U = [np.asarray(u, dtype=np.float64) for u in U]
+        self.theta = np.asarray(theta, dtype=np.float64)
+        self.mu = np.asarray(mu, dtype=np.float64)
+        self.T = len(self.theta)
+        # A[t][d] = C_td U_d, an [n_d, r_d] matrix
+        self.A = [[conv_matrix(self.x[d], self.w[d], self.theta[t]) @ self.U[d] for d in range(3)]
+                  for t in range(self.T)]
+        self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]
+
+    @classmethod
+    def from_system(cls, s):
+        return cls(s.x, s.w, s.U, s.theta, s.mu)
+
+
+# ----------------------------------------------------------------------------------
+# tensor algebra
+# ----------------------------------------------------------------------------------
+def mode_product(X, M, mode):
+    """(X x_mode M)[..., i, ...] = sum_k M[i, k] X[..., k, ...]."""
+    return np.moveaxis(np.tensordot(M, X, axes=(1, mode)), 0, mode)
+
+
+def project(rho, U):
+    """Core of rho on the shared basis: G = rho x1 U1^T x2 U2^T x3 U3^T (Eq. TuckerDecompField)."""
+    G = rho
+    for d in range(3):
+        G = mode_product(G, U[d].T, d)
+    return G
+
+
+def expand(G, S: Setup):
+    """phi = sum_t mu_t G x1 A_t1 x2 A_t2 x3 A_t3 (Eq. final: a weighted sum over the
+    Gaussian terms of tensor products of 1-D convolutions applied to the Tucker core)."""
+    phi = None
+    for t in range(S.T):
+        Y = G
+        for d in range(3):
+            Y = mode_product(Y, S.A[t][d], d)
+        phi = S.mu[t] * Y if phi is None else phi + S.mu[t] * Y
+    return phi
+
+
+def expand_transpose(y, S: Setup):
+    """H = sum_t mu_t y x1 A_t1^T x2 A_t2^T x3 A_t3^T (the adjoint of `expand`)."""
+    H = None
+    for t in range(S.T):
+        Y = y
+        for d in range(3):
+            Y = mode_product(Y, S.A[t][d].T, d)
+        H = S.mu[t] * Y if H is None else H + S.mu[t] * Y
+    return H
+
+
+def apply_L(rho, S: Setup):
+    """phi = L rho: project onto the core, then the separable Gaussian-sum convolution."""
+    return expand(project(rho, S.U), S)
+
+
+def apply_LT(y, S: Setup):
+    """L^T y = (sum_t mu_t y x_d A_td^T) x_d U_d."""
+    H = expand_transpose(y, S)
+    for d in range(3):
+        H = mode_product(H, S.U[d], d)
+    return H
+
+
+def pair_potential(psi_a, psi_b, S: Setup):
+    """phi_ab for one orbital pair: rho = psi_a * psi_b, then L rho."""
+    return apply_L(np.asarray(psi_a, np.float64) * np.asarray(psi_b, np.float64), S)
+
+
+# ----------------------------------------------------------------------------------
+# the operator, its energy and derivatives
+# ----------------------------------------------------------------------------------
+def exchange_apply(psi_occ, S: Setup, psi_tgt=None):
+    """W_i = - sum_j psi_j * phi_ij for every target i (Eqs. ExchangeOperator, hadam).
+    psi_tgt defaults to psi_occ.  Every ordered pair is computed separately."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    tgt = occ if psi_tgt is None else np.asarray(psi_tgt, dtype=np.float64)
+    W = np.zeros_like(tgt)
+    for i in range(tgt.shape[0]):
+        for j in range(occ.shape[0]):
+            W[i] -= occ[j] * pair_potential(tgt[i], occ[j], S)
+    return W
+
+
+def exchange_energy(psi_occ, S: Setup, W=None):
+    """E_x = 1/2 sum_i sum_x w(x) psi_i(x) W_i(x) (the exchange term of S[phi], alpha = 1)."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    if W is None:
+        W = exchange_apply(occ, S)
+    return 0.5 * float(np.sum(S.w3[None] * occ * W))
+
+
+def exchange_energy_grad(psi_occ, S: Setup):
+    """(E_x, dE_x/dpsi): dE/dpsi_k = w * W_k - sum_j psi_j * L^T(w * rho_kj)."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    W = exchange_apply(occ, S)
+    g = S.w3[None] * W
+    for k in range(occ.shape[0]):
+        for j in range(occ.shape[0]):
+            g[k] -= occ[j] * apply_LT(S.w3 * occ[k] * occ[j], S)
+    return exchange_energy(occ, S, W), g
+
+
+def exchange_apply_vjp(psi_occ, psi_tgt, grad_out, S: Setup):
+    """(grad_occ, grad_tgt) of f = sum_k <grad_out_k, W_k> (plain sum over grid points)."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    tgt = np.asarray(psi_tgt, dtype=np.float64)
+    Wb = np.asarray(grad_out, dtype=np.float64)
+    g_occ = np.zeros_like(occ)
+    g_tgt = np.zeros_like(tgt)
+    for k in range(tgt.shape[0]):
+        for j in range(occ.shape[0]):
+            zeta = apply_LT(Wb[k] * occ[j], S)
+            g_tgt[k] -= occ[j] * zeta
+            g_occ[j] -= Wb[k] * pair_potential(tgt[k], occ[j], S) + tgt[k] * zeta
+    return g_occ, g_tgt
+
+
+# ----------------------------------------------------------------------------------
+# independent references for the pins
+# ----------------------------------------------------------------------------------
+def direct_gaussian_kernel_potential(rho, x, w, theta, mu):
+    """Brute force O(n^6 T): phi(r) = sum_{r'} w(r') rho(r') sum_t mu_t exp(-theta_t |r - r'|^2),
+    with 3-D distances and product weights -- no separation of variables."""
+    X = np.stack(np.meshgrid(*x, indexing="ij"), -1).reshape(-1, 3)
+    wq = (w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]).reshape(-1)
+    q = wq * np.asarray(rho, np.float64).reshape(-1)
+    d2 = np.sum((X[:, None, :] - X[None, :, :]) ** 2, axis=-1)
+    K = np.zeros_like(d2)
+    for th, m in zip(theta, mu):
+        K += m * np.exp(-th * d2)
+    return (K @ q).reshape(np.shape(rho))
+
+
+def direct_coulomb_potential(rho, x, w):
+    """Brute force phi(r) = sum_{r' != r} w(r') rho(r') / |r - r'| (self term skipped)."""
+    X = np.stack(np.meshgrid(*x, indexing="ij"), -1).reshape(-1, 3)
+    wq = (w[0][:, None, None] * w[1][None, :, None] * w[2][None, None, :]).reshape(-1)
+    q = wq * np.asarray(rho, np.float64).reshape(-1)
+    d = np.sqrt(np.sum((X[:, None, :] - X[None, :, :]) ** 2, axis=-1))
+    np.fill_diagonal(d, np.inf)
+    return ((1.0 / d) @ q).reshape(np.shape(rho))
+
+
+def gaussian_charge_potential(a, r):
+    """Potential of the unit charge (a/pi)^{3/2} exp(-a r^2): erf(sqrt(a) r) / r,
+    with the limit 2 sqrt(a/pi) at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    small = r < 1e-12
+    from math import erf
+    out[~small] = np.vectorize(erf)(math.sqrt(a) * r[~small]) / r[~small]
+    out[small] = 2.0 * math.sqrt(a / math.pi)
+    return out
+
+
+def gaussian_kernel_charge_potential(a, r, theta, mu):
+    """Continuous convolution of the unit Gaussian charge with the Gaussian-sum kernel:
+    sum_t mu_t (a / (a + theta_t))^{3/2} exp(-a theta_t r^2 / (a + theta_t))."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.zeros_like(r)
+    for th, m in zip(theta, mu):
+        out += m * (a / (a + th)) ** 1.5 * np.exp(-a * th * r * r / (a + th))
+    return out

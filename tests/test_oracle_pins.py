@@ -1,0 +1,309 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+closed forms, brute-force direct sums with 3-D distances, textbook bounds, exact
+invariants of the operator at full rank, transposes and finite differences.
+
+Each pin is chosen to fail on a plausible mistake: a transposed convolution matrix
+(non-uniform weights in the brute-force test), a mixed-up mode (different n per mode),
+a dropped mu_t or a wrong theta_t (brute force and closed form), a wrong sign or factor
+(energy of a Gaussian orbital), a wrong adjoint (dot-product and finite-difference tests).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _random_setup(rng, n, r, T, uniform=False, full_rank=False):
+    xs, ws, Us = [], [], []
+    for d in range(3):
+        if uniform:
+            x, w = W.uniform_grid(n[d], 3.0)
+        else:
+            x = np.sort(rng.uniform(-3.0, 3.0, n[d]))
+            w = rng.uniform(0.2, 0.8, n[d])
+        xs.append(x)
+        ws.append(w)
+        if full_rank:
+            Us.append(np.eye(n[d]))
+        else:
+            Q, _ = np.linalg.qr(rng.standard_normal((n[d], r[d])))
+            Us.append(Q)
+    theta = rng.uniform(0.05, 2.0, T)
+    mu = rng.uniform(0.1, 1.0, T)
+    return O.Setup(xs, ws, Us, theta, mu)
+
+
+# ---------------------------------------------------------------------------------
+# Gaussian-sum approximation of 1/r (Eq. gauss): error on [r1, r2] against 1/r itself
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("T,n,L,tol", [(30, 32, 8.0, 3e-6), (35, 64, 10.0, 2e-6),
+                                       (40, 96, 12.0, 1e-6), (45, 160, 16.0, 1e-6)])
+def test_exp_sum_matches_inverse_r_on_grid_range(T, n, L, tol):
+    h = 2 * L / (n - 1)
+    r1, r2 = h, 2 * L * math.sqrt(3)
+    theta, mu, reported = W.exp_sum_inverse_r(T, r1, r2)
+    assert np.all(theta > 0) and np.all(mu > 0)
+    r = np.geomspace(r1, r2, 20001)                       # denser than the fit's own sample
+    approx = np.exp(-np.outer(r * r, theta)) @ mu
+    err = np.max(np.abs(approx * r - 1.0))
+    assert err < tol
+    assert abs(err - reported) < 0.2 * reported + 1e-12
+    # the paper notes the fit fails below r1 (1/r is singular there)
+    r_small = np.array([0.05 * r1])
+    assert abs((np.exp(-np.outer(r_small ** 2, theta)) @ mu)[0] * r_small[0] - 1) > 10 * tol
+
+
+# ---------------------------------------------------------------------------------
+# 1-D convolution matrices (Eq. discInteg) against the closed-form Gaussian convolution
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("a,theta", [(1.0, 0.5), (0.3, 2.0), (2.5, 0.01)])
+def test_conv_matrix_resolved_gaussian_closed_form(a, theta):
+    x, w = W.uniform_grid(97, 12.0)           # h = 0.25; (a + theta) h^2 <= 0.3: resolved
+    C = O.conv_matrix(x, w, theta)
+    f = np.exp(-a * x * x)
+    got = C @ f
+    exact = math.sqrt(math.pi / (a + theta)) * np.exp(-a * theta * x * x / (a + theta))
+    inner = np.abs(x) <= 4.0
+    assert np.max(np.abs(got - exact)[inner]) < 1e-10
+
+
+# ---------------------------------------------------------------------------------
+# Projection: textbook HOSVD error bound, idempotence, exactness in the span
+# ---------------------------------------------------------------------------------
+def test_projection_hosvd_error_bound():
+    s = W.config_small()
+    rho = s.psi[0].astype(np.float64) ** 2
+    for r in (4, 8, 12):
+        U = W.density_hosvd_basis(s.psi[:1], (r, r, r))      # HOSVD of rho = psi_0^2 itself
+        P = O.project(rho, U)
+        for d in range(3):
+            P = O.mode_product(P, U[d], d)
+        err2 = np.sum((rho - P) ** 2)
+        bound = 0.0
+        for d in range(3):
+            M = np.moveaxis(rho, d, 0).reshape(rho.shape[d], -1)
+            sv = np.linalg.svd(M, compute_uv=False)
+            bound += np.sum(sv[r:] ** 2)
+        # truncated HOSVD: ||rho - P rho||^2 <= sum_d sum_{discarded} sigma_d^2
+        assert err2 <= bound * (1 + 1e-9)
+        assert err2 > 0
+
+
+def test_projection_idempotent_and_exact_on_span():
+    rng = np.random.default_rng(5)
+    n, r = (9, 11, 13), (4, 5, 6)
+    S = _random_setup(rng, n, r, 2)
+    rho = rng.standard_normal(n)
+    G = O.project(rho, S.U)
+    P1 = G
+    for d in range(3):
+        P1 = O.mode_product(P1, S.U[d], d)
+    G2 = O.project(P1, S.U)
+    assert _rel(G2, G) < 1e-13
+    # a separable field whose factors lie in span(U_d) is reproduced exactly
+    f = [S.U[d] @ rng.standard_normal(r[d]) for d in range(3)]
+    sep = np.einsum("a,b,c->abc", *f)
+    G = O.project(sep, S.U)
+    back = G
+    for d in range(3):
+        back = O.mode_product(back, S.U[d], d)
+    assert _rel(back, sep) < 1e-13
+
+
+# ---------------------------------------------------------------------------------
+# Whole potential at full rank against the brute-force O(n^6 T) sum with 3-D distances
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1])
+def test_full_rank_potential_equals_direct_sum(seed):
+    rng = np.random.default_rng(seed)
+    n = (7, 9, 11)                                # different per mode: catches mode mix-ups
+    S = _random_setup(rng, n, n, 3, full_rank=True)
+    rho = rng.standard_normal(n)
+    phi = O.apply_L(rho, S)
+    ref = O.direct_gaussian_kernel_potential(rho, S.x, S.w, S.theta, S.mu)
+    assert _rel(phi, ref) < 1e-12
+
+
+def test_direct_sum_reference_is_sensitive_to_transposed_weights():
+    # the brute-force reference must tell C = K D apart from C = D K on a non-uniform grid
+    rng = np.random.default_rng(3)
+    n = (7, 8, 9)
+    S = _random_setup(rng, n, n, 2, full_rank=True)
+    rho = rng.standard_normal(n)
+    ref = O.direct_gaussian_kernel_potential(rho, S.x, S.w, S.theta, S.mu)
+    wrong = 0
+    for t in range(S.T):
+        Y = rho
+        for d in range(3):
+            Ct = O.conv_matrix(S.x[d], S.w[d], S.theta[t])
+            Ct = Ct / S.w[d][None, :] * S.w[d][:, None]          # weights on the wrong index
+            Y = O.mode_product(Y, Ct, d)
+        wrong = wrong + S.mu[t] * Y
+    assert _rel(wrong, ref) > 1e-3
+
+
+# ---------------------------------------------------------------------------------
+# Physics: potential of a Gaussian charge is erf(sqrt(a) r)/r (O(h^2) on the grid)
+# ---------------------------------------------------------------------------------
+def test_gaussian_charge_potential_closed_form_and_convergence():
+    a, L = 1.0, 7.0
+    errs, sep_errs = [], []
+    for n in (15, 29, 57):
+        x, w = W.uniform_grid(n, L)
+        h = x[1] - x[0]
+        theta, mu, _ = W.exp_sum_inverse_r(30, h, 2 * L * math.sqrt(3))
+        S = O.Setup([x] * 3, [w] * 3, [np.eye(n)] * 3, theta, mu)
+        X = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1)
+        r = np.linalg.norm(X, axis=-1)
+        rho = (a / math.pi) ** 1.5 * np.exp(-a * r * r)
+        phi = O.apply_L(rho, S)
+        exact = O.gaussian_charge_potential(a, r)
+        inner = r <= 3.0
+        errs.append(np.max(np.abs(phi - exact)[inner]) / np.max(exact))
+        # the continuous convolution with the fitted kernel: its error comes only from
+        # distances below r1 = h, where the fit departs from 1/r, so it is also O(h^2)
+        sep = O.gaussian_kernel_charge_potential(a, r[inner], theta, mu)
+        sep_errs.append(np.max(np.abs(sep - exact[inner])) / np.max(exact))
+    assert errs[-1] < 1e-2 and sep_errs[-1] < 5e-3
+    # second order in h: halving h cuts the error by about 4
+    assert errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 2.5
+    assert sep_errs[0] / sep_errs[1] > 2.5 and sep_errs[1] / sep_errs[2] > 2.5
+
+
+def test_gaussian_orbital_exchange_energy_closed_form():
+    # psi = (2a/pi)^{3/4} exp(-a r^2): rho = psi^2 is a unit Gaussian charge of exponent 2a,
+    # whose Coulomb self-energy is J = sqrt(2 * 2a / pi); one orbital gives E_x = -J/2.
+    a, L = 0.8, 7.0
+    errs = []
+    for n in (15, 29, 57):
+        x, w = W.uniform_grid(n, L)
+        theta, mu, _ = W.exp_sum_inverse_r(30, x[1] - x[0], 2 * L * math.sqrt(3))
+        S = O.Setup([x] * 3, [w] * 3, [np.eye(n)] * 3, theta, mu)
+        X = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1)
+        psi = (2 * a / math.pi) ** 0.75 * np.exp(-a * np.sum(X * X, -1))
+        E = O.exchange_energy(psi[None], S)
+        errs.append(abs(E + 0.5 * math.sqrt(4 * a / math.pi)))
+        assert E < 0
+    assert errs[-1] / (0.5 * math.sqrt(4 * a / math.pi)) < 5e-3
+    assert errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 2.5
+
+
+def test_true_coulomb_brute_force_agrees_within_self_cell_error():
+    a, L, n = 1.0, 5.0, 13
+    x, w = W.uniform_grid(n, L)
+    h = x[1] - x[0]
+    theta, mu, _ = W.exp_sum_inverse_r(30, h, 2 * L * math.sqrt(3))
+    S = O.Setup([x] * 3, [w] * 3, [np.eye(n)] * 3, theta, mu)
+    X = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1)
+    r = np.linalg.norm(X, axis=-1)
+    rho = (a / math.pi) ** 1.5 * np.exp(-a * r * r)
+    phi = O.apply_L(rho, S)
+    bf = O.direct_coulomb_potential(rho, S.x, S.w)
+    # away from r < h the two sums differ only by the fit error and the self/near cells
+    far = r > 2 * h
+    rel = np.max(np.abs(phi - bf)[far]) / np.max(np.abs(bf))
+    assert rel < 0.2
+
+
+# ---------------------------------------------------------------------------------
+# Operator invariants: symmetric and negative semidefinite exactly at full rank
+# ---------------------------------------------------------------------------------
+def test_exchange_matrix_symmetric_nsd_at_full_rank():
+    s = W.config_small(n=14, n_orb=3, rank=14, T=8, L=5.0, full_rank=True)
+    S = O.Setup.from_system(s)
+    psi = s.psi.astype(np.float64)
+    Wk = O.exchange_apply(psi, S)
+    M = np.einsum("axyz,bxyz->ab", psi * S.w3[None], Wk)
+    assert np.max(np.abs(M - M.T)) / np.max(np.abs(M)) < 1e-12
+    assert np.max(np.linalg.eigvalsh(0.5 * (M + M.T))) < 1e-12 * np.max(np.abs(M))
+
+
+def test_exchange_matrix_nearly_symmetric_at_truncated_rank():
+    s = W.config_small(n=14, n_orb=3, rank=10, T=8, L=5.0)
+    S = O.Setup.from_system(s)
+    psi = s.psi.astype(np.float64)
+    M = np.einsum("axyz,bxyz->ab", psi * S.w3[None], O.exchange_apply(psi, S))
+    asym = np.max(np.abs(M - M.T)) / np.max(np.abs(M))
+    assert 0 < asym < 0.05
+
+
+def test_pair_potential_symmetric_in_the_pair():
+    s = W.config_small(n=12, n_orb=2, rank=6, T=4, L=5.0)
+    S = O.Setup.from_system(s)
+    a, b = s.psi.astype(np.float64)
+    assert _rel(O.pair_potential(a, b, S), O.pair_potential(b, a, S)) < 1e-14
+
+
+# ---------------------------------------------------------------------------------
+# Transposes and derivatives
+# ---------------------------------------------------------------------------------
+def test_transpose_dot_product():
+    rng = np.random.default_rng(7)
+    n, r = (8, 10, 12), (3, 4, 5)
+    S = _random_setup(rng, n, r, 3)
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(n)
+    lhs = np.sum(O.apply_L(x, S) * y)
+    rhs = np.sum(x * O.apply_LT(y, S))
+    assert abs(lhs - rhs) < 1e-13 * (abs(lhs) + np.linalg.norm(x) * np.linalg.norm(y))
+
+
+def test_energy_gradient_finite_differences():
+    s = W.config_small(n=10, n_orb=3, rank=6, T=4, L=5.0)
+    S = O.Setup.from_system(s)
+    psi = s.psi.astype(np.float64)
+    E, g = O.exchange_energy_grad(psi, S)
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        v = rng.standard_normal(psi.shape)
+        v /= np.linalg.norm(v)
+        eps = 1e-4
+        fd = (O.exchange_energy(psi + eps * v, S) - O.exchange_energy(psi - eps * v, S)) / (2 * eps)
+        assert abs(fd - np.sum(g * v)) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_energy_gradient_full_rank_is_twice_weighted_W():
+    s = W.config_small(n=10, n_orb=2, rank=10, T=4, L=5.0, full_rank=True)
+    S = O.Setup.from_system(s)
+    psi = s.psi.astype(np.float64)
+    _, g = O.exchange_energy_grad(psi, S)
+    Wk = O.exchange_apply(psi, S)
+    assert _rel(g, 2 * S.w3[None] * Wk) < 1e-12
+
+
+def test_apply_vjp_finite_differences():
+    s = W.config_small(n=10, n_orb=3, rank=6, T=4, L=5.0)
+    S = O.Setup.from_system(s)
+    occ = s.psi.astype(np.float64)
+    tgt = occ[:2] * 1.3 + 0.1 * occ[1:3]
+    rng = np.random.default_rng(13)
+    Wb = rng.standard_normal(tgt.shape)
+    g_occ, g_tgt = O.exchange_apply_vjp(occ, tgt, Wb, S)
+
+    def f(o, t):
+        return np.sum(Wb * O.exchange_apply(o, S, psi_tgt=t))
+
+    eps = 1e-4
+    for _ in range(3):
+        vo = rng.standard_normal(occ.shape)
+        vt = rng.standard_normal(tgt.shape)
+        fd_o = (f(occ + eps * vo, tgt) - f(occ - eps * vo, tgt)) / (2 * eps)
+        fd_t = (f(occ, tgt + eps * vt) - f(occ, tgt - eps * vt)) / (2 * eps)
+        assert abs(fd_o - np.sum(g_occ * vo)) < 1e-6 * max(1.0, abs(fd_o))
+        assert abs(fd_t - np.sum(g_tgt * vt)) < 1e-6 * max(1.0, abs(fd_t))
+
+
+def test_apply_linear_in_target_quadratic_in_occupied():
+    s = W.config_small(n=10, n_orb=2, rank=6, T=3, L=5.0)
+    S = O.Setup.from_system(s)
+    occ = s.psi.astype(np.float64)
+    W1 = O.exchange_apply(occ, S, psi_tgt=occ[:1])
+    assert _rel(O.exchange_apply(occ, S, psi_tgt=2 * occ[:1]), 2 * W1) < 1e-14
+    assert _rel(O.exchange_apply(3 * occ, S, psi_tgt=occ[:1]), 9 * W1) < 1e-14
