@@ -1,0 +1,188 @@
+/*
+ * tuxc.h -- C ABI of the GB300 Tucker-tensor Fock-exchange library (libtuxc.so).
+ *
+ * The library applies the Fock exchange operator of a block of real orbitals on a
+ * tensor-product grid, following arXiv 2401.04189 ("Convolution operation" section):
+ *
+ *   (K psi)_i(r) = - sum_j psi_j(r) * phi_ij(r),     phi_ij = conv(psi_i psi_j, 1/|r|)
+ *                                                    (Eqs. ExchangeOperator, varphi, hadam)
+ *
+ * with every pair density projected onto a shared Tucker basis U1, U2, U3 (Eq. tucker,
+ * Eq. TuckerDecompField) and 1/r replaced by a sum of T Gaussians (Eq. gauss), so that the
+ * 3-D convolution is a weighted sum of tensor products of 1-D convolutions (Eq. final),
+ * each evaluated with nodal quadrature as a matrix product (Eq. discInteg):
+ *
+ *   rho_ij = psi_i * psi_j
+ *   G_ij   = rho_ij x1 U1^T x2 U2^T x3 U3^T                               [r1][r2][r3]
+ *   A_td   = C_td U_d,  C_td[a][b] = w_b exp(-theta_t (x_a - x_b)^2)       [n_d][r_d]
+ *   phi_ij = sum_t mu_t G_ij x1 A_t1 x2 A_t2 x3 A_t3                       [n1][n2][n3]
+ *   W_i    = - sum_j psi_j * phi_ij
+ *   E_x    = 1/2 sum_i sum_r w(r) psi_i(r) W_i(r)       (exact-exchange energy, alpha = 1)
+ *
+ * Occupations are 1, there is no spin factor and alpha = 1: callers scale.
+ *
+ * Conventions for every entry point
+ *  - Orbital blocks are float32, C-contiguous [count][n1][n2][n3] (z fastest), in device
+ *    memory of the current CUDA device, 16-byte aligned.  Outputs must not alias inputs.
+ *  - Every call is asynchronous on the caller's stream; nothing is synchronised.  Scalars
+ *    (energies) are written to caller-owned device memory.
+ *  - Every call returns a status: TX_OK (0) or a negative TX_ERR_* code.  Arguments are
+ *    validated on the host before any launch; a failed validation launches nothing.
+ *    No exception or abort crosses the ABI.  tx_status_string() names a code;
+ *    tx_last_error_message() gives the detail of the last failure on this thread.
+ *  - A context belongs to one device and must be used from one host thread at a time.
+ */
+#ifndef TUXC_H
+#define TUXC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tx_stream_t;   /* same object as cudaStream_t; NULL = legacy default stream */
+typedef struct tx_ctx tx_ctx;
+
+enum tx_status {
+    TX_OK = 0,
+    TX_ERR_INVALID_ARG = -1,          /* null pointer, non-positive size, non-finite value */
+    TX_ERR_SHAPE = -2,                /* rank larger than grid size, inconsistent extents */
+    TX_ERR_NOT_ORTHONORMAL = -3,      /* U_d^T U_d deviates from I by more than 1e-10 */
+    TX_ERR_UNSUPPORTED_PRECISION = -4,
+    TX_ERR_CUDA = -5,                 /* a CUDA runtime call failed; see tx_last_error_message */
+    TX_ERR_OOM = -6,                  /* device allocation for the context workspace failed */
+    TX_ERR_TIMEOUT = -7,              /* a bounded device-side wait gave up (see tx_check_device_error) */
+    TX_ERR_NOT_SETUP = -8,            /* NULL or destroyed context */
+    TX_ERR_UNSUPPORTED_SHAPE = -9,    /* shape outside what the selected precision's kernels handle */
+    TX_ERR_ALIGNMENT = -10            /* a device pointer is not 16-byte aligned */
+};
+
+/* Arithmetic of the mode-product GEMMs.  Accumulation is float32 in every mode; set-up
+ * (the A_td matrices) and the final energy reduction are float64. */
+enum tx_precision {
+    TX_PREC_FP32 = 0,     /* plain float32 CUDA-core kernels (reference GPU form) */
+    TX_PREC_BF16 = 1,     /* tcgen05 kind::f16, bf16 operands, fp32 accumulate in TMEM */
+    TX_PREC_TF32 = 2,     /* tcgen05 kind::tf32, one pass */
+    TX_PREC_TF32X3 = 3,   /* tcgen05 kind::tf32, split precision: hi*hi + hi*lo + lo*hi */
+    TX_PREC_BF16X3 = 4    /* tcgen05 kind::f16, bf16 split precision: hi*hi + hi*lo + lo*hi */
+};
+
+/*
+ * tx_tucker_setup -- build a context for one grid, basis and Gaussian sum.
+ *
+ * Defines the operator of Eqs. tucker, gauss, quadVal and discInteg (the 1-D convolution
+ * matrices are precomputed once, as the paper does after Eq. discInteg).
+ *   n[3]              grid sizes n1, n2, n3 (>= 2)
+ *   x1, x2, x3        host float64 node coordinates, n_d each
+ *   w1, w2, w3        host float64 quadrature weights, n_d each (> 0)
+ *   r[3]              Tucker ranks (1 <= r_d <= n_d)
+ *   U1, U2, U3        host float64 [n_d][r_d] row-major, U_d^T U_d = I (checked to 1e-10)
+ *   T                 number of Gaussian terms (>= 1)
+ *   gauss_exponents   host float64 theta[T] (> 0)
+ *   gauss_weights     host float64 mu[T] (finite, > 0)
+ *   precision         enum tx_precision
+ *   stream            stream for the set-up copies and kernels
+ * The host arrays are copied; the caller may free them when the call returns.  A_td is
+ * computed on the device in float64 (mu_t folded into A_t3 before rounding) and rounded
+ * to the operand formats of `precision`.  On success *ctx owns all its device memory and
+ * is released by tx_destroy.  On failure *ctx is set to NULL.
+ */
+int tx_tucker_setup(tx_ctx** ctx, const int n[3],
+                    const double* x1, const double* x2, const double* x3,
+                    const double* w1, const double* w2, const double* w3,
+                    const int r[3], const double* U1, const double* U2, const double* U3,
+                    int T, const double* gauss_exponents, const double* gauss_weights,
+                    int precision, tx_stream_t stream);
+
+/* Release every device allocation of the context (after synchronising its last stream). */
+void tx_destroy(tx_ctx* ctx);
+
+/* Change the GEMM arithmetic of an existing context (operand copies are rebuilt). */
+int tx_set_precision(tx_ctx* ctx, int precision, tx_stream_t stream);
+
+/*
+ * tx_exchange_apply -- out = K psi_tgt (Eqs. ExchangeOperator / hadam): for every target i,
+ *   out_i = - sum_{j < n_occ} psi_occ_j * phi_ij.
+ *   psi_occ   device float32 [n_occ][n1][n2][n3]
+ *   psi_tgt   device float32 [n_tgt][n1][n2][n3]; NULL means the targets are psi_occ
+ *             itself (n_tgt must then equal n_occ).  If psi_tgt points inside psi_occ at an
+ *             orbital boundary, the targets are that slice of the occupied block and each
+ *             pair potential shared by two targets is computed once (phi_ij = phi_ji).
+ *   out       device float32 [n_tgt][n1][n2][n3], overwritten
+ */
+int tx_exchange_apply(tx_ctx* ctx, const float* psi_occ, int n_occ,
+                      const float* psi_tgt, int n_tgt, float* out, tx_stream_t stream);
+
+/*
+ * tx_exchange_apply_energy -- out = K psi_occ and E_x = 1/2 sum_i <psi_i, out_i>_w in one
+ * pass (the energy sums are taken in the same epilogue as the Hadamard products).
+ *   out    device float32 [n_occ][n1][n2][n3], overwritten
+ *   e_dev  device float64 scalar
+ */
+int tx_exchange_apply_energy(tx_ctx* ctx, const float* psi_occ, int n_occ, float* out, double* e_dev,
+                             tx_stream_t stream);
+
+/*
+ * tx_exchange_energy -- E_x = 1/2 sum_i <psi_i, W_i>_w = -1/2 sum_ij sum_r w rho_ij phi_ij
+ * (the exchange term of S[phi] with alpha = 1).  Writes one float64 to e_dev (device).
+ * No W is stored: the weighted pair sums are reduced in float64 in a fixed order.
+ */
+int tx_exchange_energy(tx_ctx* ctx, const float* psi_occ, int n_occ, double* e_dev,
+                       tx_stream_t stream);
+
+/*
+ * tx_exchange_energy_grad -- E_x and its gradient with respect to the nodal orbital values
+ * (not in the paper; derived): with L = sum_t mu_t (x)_d A_td U_d^T,
+ *   dE/dpsi_k = w * W_k - sum_j psi_j * L^T (w * rho_kj).
+ *   grad   device float32 [n_occ][n1][n2][n3], overwritten
+ *   e_dev  device float64 scalar, or NULL
+ */
+int tx_exchange_energy_grad(tx_ctx* ctx, const float* psi_occ, int n_occ, float* grad,
+                            double* e_dev, tx_stream_t stream);
+
+/*
+ * tx_exchange_apply_vjp -- vector-Jacobian product of tx_exchange_apply for a cotangent
+ * grad_out = dF/dout (plain sum over grid points):
+ *   grad_tgt_k = - sum_j psi_j * L^T(grad_out_k * psi_j)
+ *   grad_occ_j = - sum_k grad_out_k * phi_kj - sum_k psi_k * L^T(grad_out_k * psi_j)
+ * psi_tgt must be a separate target block here (autograd adds the two gradients when the
+ * caller's target and occupied tensors are the same).  grad_occ / grad_tgt are overwritten;
+ * either may be NULL to skip it.
+ */
+int tx_exchange_apply_vjp(tx_ctx* ctx, const float* psi_occ, int n_occ,
+                          const float* psi_tgt, int n_tgt, const float* grad_out,
+                          float* grad_occ, float* grad_tgt, tx_stream_t stream);
+
+/* Size in bytes of the device workspace the context currently holds. */
+size_t tx_workspace_bytes(const tx_ctx* ctx);
+
+/* Upper bound on the workspace (default 2 GiB); larger calls are split into pair batches. */
+int tx_set_workspace_limit(tx_ctx* ctx, size_t bytes);
+
+/* Reads and clears the device-side error word (bounded waits that gave up); synchronises
+ * the context's last stream.  Returns TX_OK or TX_ERR_TIMEOUT. */
+int tx_check_device_error(tx_ctx* ctx);
+
+const char* tx_status_string(int status);
+const char* tx_last_error_message(void);
+
+/*
+ * Opt-in device timing of the library's own kernels: while enabled, each launch on the calling
+ * thread is bracketed by CUDA events on its stream.  tx_profile_read synchronises those events
+ * and returns, for the kernel class `name` ("project", "expand_mode1", "consume", "adjoint",
+ * "gemm", ...), the number of launches and their summed device time in milliseconds.
+ */
+void tx_profile_enable(int enable);
+void tx_profile_reset(void);
+int tx_profile_read(const char* name, int* launches, double* total_ms);
+
+/* Number of kernel launches this library made on the calling thread since the last reset. */
+uint64_t tx_launch_count(void);
+void tx_reset_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUXC_H */

@@ -1,0 +1,287 @@
+"""ctypes binding of libtuxc.so: argument marshalling only.  Every step of the hot path runs
+in the library's CUDA kernels; if the library is missing this module raises instead of
+falling back to anything else."""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtuxc.so")
+
+TX_OK = 0
+STATUS = {
+    0: "TX_OK", -1: "TX_ERR_INVALID_ARG", -2: "TX_ERR_SHAPE", -3: "TX_ERR_NOT_ORTHONORMAL",
+    -4: "TX_ERR_UNSUPPORTED_PRECISION", -5: "TX_ERR_CUDA", -6: "TX_ERR_OOM", -7: "TX_ERR_TIMEOUT",
+    -8: "TX_ERR_NOT_SETUP", -9: "TX_ERR_UNSUPPORTED_SHAPE", -10: "TX_ERR_ALIGNMENT",
+}
+EXPORTED = [
+    "tx_tucker_setup", "tx_destroy", "tx_set_precision", "tx_exchange_apply", "tx_exchange_energy",
+    "tx_exchange_energy_grad", "tx_exchange_apply_vjp", "tx_workspace_bytes", "tx_set_workspace_limit",
+    "tx_check_device_error", "tx_status_string", "tx_last_error_message", "tx_launch_count",
+    "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
+    "tx_profile_read",
+]
+
+
+class Precision(enum.IntEnum):
+    FP32 = 0
+    BF16 = 1
+    TF32 = 2
+    TF32X3 = 3
+    BF16X3 = 4
+
+    @classmethod
+    def parse(cls, p):
+        if isinstance(p, str):
+            return cls[p.upper()]
+        return cls(int(p))
+
+
+class TuckerExchangeError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; call paper_2401_04189_gb300.build.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    L.tx_tucker_setup.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_I), _P, _P, _P, _P, _P, _P,
+                                  ctypes.POINTER(_I), _P, _P, _P, _I, _P, _P, _I, _P]
+    L.tx_tucker_setup.restype = _I
+    L.tx_destroy.argtypes = [_P]
+    L.tx_destroy.restype = None
+    L.tx_set_precision.argtypes = [_P, _I, _P]
+    L.tx_set_precision.restype = _I
+    L.tx_exchange_apply.argtypes = [_P, _P, _I, _P, _I, _P, _P]
+    L.tx_exchange_apply.restype = _I
+    L.tx_exchange_apply_energy.argtypes = [_P, _P, _I, _P, _P, _P]
+    L.tx_exchange_apply_energy.restype = _I
+    L.tx_profile_enable.argtypes = [_I]
+    L.tx_profile_enable.restype = None
+    L.tx_profile_reset.argtypes = []
+    L.tx_profile_reset.restype = None
+    L.tx_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
+    L.tx_profile_read.restype = _I
+    L.tx_exchange_energy.argtypes = [_P, _P, _I, _P, _P]
+    L.tx_exchange_energy.restype = _I
+    L.tx_exchange_energy_grad.argtypes = [_P, _P, _I, _P, _P, _P]
+    L.tx_exchange_energy_grad.restype = _I
+    L.tx_exchange_apply_vjp.argtypes = [_P, _P, _I, _P, _I, _P, _P, _P, _P]
+    L.tx_exchange_apply_vjp.restype = _I
+    L.tx_workspace_bytes.argtypes = [_P]
+    L.tx_workspace_bytes.restype = ctypes.c_size_t
+    L.tx_set_workspace_limit.argtypes = [_P, ctypes.c_size_t]
+    L.tx_set_workspace_limit.restype = _I
+    L.tx_check_device_error.argtypes = [_P]
+    L.tx_check_device_error.restype = _I
+    L.tx_status_string.argtypes = [_I]
+    L.tx_status_string.restype = ctypes.c_char_p
+    L.tx_last_error_message.argtypes = []
+    L.tx_last_error_message.restype = ctypes.c_char_p
+    L.tx_launch_count.argtypes = []
+    L.tx_launch_count.restype = ctypes.c_uint64
+    L.tx_reset_launch_count.argtypes = []
+    L.tx_reset_launch_count.restype = None
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != TX_OK:
+        msg = lib().tx_last_error_message().decode(errors="replace")
+        raise TuckerExchangeError(status, where, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Context:
+    """Owns one tx_ctx: grid, weights, basis, Gaussian sum, operand copies, workspace."""
+
+    def __init__(self, x, w, U, theta, mu, precision="fp32", stream=None):
+        L = lib()
+        self._host = [_f64(v) for v in (*x, *w, *U, theta, mu)]
+        xs, ws, Us = self._host[0:3], self._host[3:6], self._host[6:9]
+        th, m = self._host[9], self._host[10]
+        self.n = tuple(int(v.shape[0]) for v in xs)
+        self.r = tuple(int(u.shape[1]) for u in Us)
+        self.T = int(th.shape[0])
+        for d in range(3):
+            if Us[d].shape != (self.n[d], self.r[d]) or ws[d].shape != (self.n[d],):
+                raise ValueError(f"mode {d + 1}: inconsistent x / w / U shapes")
+        if m.shape != th.shape:
+            raise ValueError("theta and mu must have the same length")
+        self.precision = Precision.parse(precision)
+        n_arr = (_I * 3)(*self.n)
+        r_arr = (_I * 3)(*self.r)
+        h = _P()
+        pp = [v.ctypes.data_as(_P) for v in self._host]
+        st = L.tx_tucker_setup(ctypes.byref(h), n_arr, *pp[0:3], *pp[3:6], r_arr, *pp[6:9], self.T, pp[9], pp[10],
+                               int(self.precision), _stream(stream))
+        _check(st, "tx_tucker_setup")
+        self._h = h
+
+    @classmethod
+    def from_system(cls, s, precision="fp32", stream=None):
+        return cls(s.x, s.w, s.U, s.theta, s.mu, precision=precision, stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("context was destroyed")
+        return self._h
+
+    def set_precision(self, precision, stream=None):
+        p = Precision.parse(precision)
+        _check(lib().tx_set_precision(self.handle, int(p), _stream(stream)), "tx_set_precision")
+        self.precision = p
+
+    def set_workspace_limit(self, nbytes):
+        _check(lib().tx_set_workspace_limit(self.handle, int(nbytes)), "tx_set_workspace_limit")
+
+    def workspace_bytes(self):
+        return int(lib().tx_workspace_bytes(self.handle))
+
+    def check_device_error(self):
+        _check(lib().tx_check_device_error(self.handle), "tx_check_device_error")
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tx_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # ---- checks -------------------------------------------------------------------
+    def _block(self, t, name):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+            raise TypeError(f"{name} must be a float32 CUDA tensor")
+        if t.dim() != 4 or tuple(t.shape[1:]) != self.n:
+            raise ValueError(f"{name} must have shape [count, {self.n[0]}, {self.n[1]}, {self.n[2]}]")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+
+def tx_tucker_setup(x, w, U, theta, mu, precision="fp32", stream=None) -> Context:
+    return Context(x, w, U, theta, mu, precision=precision, stream=stream)
+
+
+def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None):
+    """out = K psi_tgt (psi_tgt None: the occupied block itself)."""
+    ctx._block(psi_occ, "psi_occ")
+    n_tgt = psi_occ.shape[0] if psi_tgt is None else ctx._block(psi_tgt, "psi_tgt").shape[0]
+    if out is None:
+        out = torch.empty((n_tgt, *ctx.n), dtype=torch.float32, device=psi_occ.device)
+    ctx._block(out, "out")
+    st = lib().tx_exchange_apply(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(psi_tgt),
+                                 0 if psi_tgt is None else n_tgt, _ptr(out), _stream(stream))
+    _check(st, "tx_exchange_apply")
+    return out
+
+
+def tx_exchange_apply_energy(ctx: Context, psi_occ, out=None, e_out=None, stream=None):
+    """(K psi_occ, E_x) in one pass."""
+    ctx._block(psi_occ, "psi_occ")
+    if out is None:
+        out = torch.empty_like(psi_occ)
+    ctx._block(out, "out")
+    if e_out is None:
+        e_out = torch.empty((), dtype=torch.float64, device=psi_occ.device)
+    st = lib().tx_exchange_apply_energy(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(out), _ptr(e_out),
+                                        _stream(stream))
+    _check(st, "tx_exchange_apply_energy")
+    return out, e_out
+
+
+def tx_profile_enable(enable=True):
+    lib().tx_profile_enable(1 if enable else 0)
+
+
+def tx_profile_reset():
+    lib().tx_profile_reset()
+
+
+def tx_profile_read(name):
+    """(launches, total device ms) of one kernel class since the last reset."""
+    n = _I()
+    ms = ctypes.c_double()
+    _check(lib().tx_profile_read(name.encode(), ctypes.byref(n), ctypes.byref(ms)), "tx_profile_read")
+    return int(n.value), float(ms.value)
+
+
+def tx_exchange_energy(ctx: Context, psi_occ, e_out=None, stream=None):
+    """E_x as a float64 device scalar."""
+    ctx._block(psi_occ, "psi_occ")
+    if e_out is None:
+        e_out = torch.empty((), dtype=torch.float64, device=psi_occ.device)
+    st = lib().tx_exchange_energy(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(e_out), _stream(stream))
+    _check(st, "tx_exchange_energy")
+    return e_out
+
+
+def tx_exchange_energy_grad(ctx: Context, psi_occ, grad=None, e_out=None, stream=None):
+    """(E_x, dE_x/dpsi)."""
+    ctx._block(psi_occ, "psi_occ")
+    if grad is None:
+        grad = torch.empty_like(psi_occ)
+    if e_out is None:
+        e_out = torch.empty((), dtype=torch.float64, device=psi_occ.device)
+    st = lib().tx_exchange_energy_grad(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(grad), _ptr(e_out),
+                                       _stream(stream))
+    _check(st, "tx_exchange_energy_grad")
+    return e_out, grad
+
+
+def tx_exchange_apply_vjp(ctx: Context, psi_occ, psi_tgt, grad_out, need_occ=True, need_tgt=True, stream=None):
+    """(grad_occ, grad_tgt) of sum(grad_out * K psi_tgt)."""
+    ctx._block(psi_occ, "psi_occ")
+    ctx._block(psi_tgt, "psi_tgt")
+    ctx._block(grad_out, "grad_out")
+    g_occ = torch.empty_like(psi_occ) if need_occ else None
+    g_tgt = torch.empty_like(psi_tgt) if need_tgt else None
+    st = lib().tx_exchange_apply_vjp(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(psi_tgt), psi_tgt.shape[0],
+                                     _ptr(grad_out), _ptr(g_occ), _ptr(g_tgt), _stream(stream))
+    _check(st, "tx_exchange_apply_vjp")
+    return g_occ, g_tgt
+
+
+def tx_launch_count() -> int:
+    return int(lib().tx_launch_count())
+
+
+def tx_reset_launch_count():
+    lib().tx_reset_launch_count()

@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs (float32 orbitals promoted to float64 on the oracle side)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from _helpers import E_TOL, W_TOL, max_row_rel, rel, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2401_04189_gb300 import build
+    build.build()
+
+
+def _P():
+    import paper_2401_04189_gb300 as P
+    return P
+
+
+def ragged_system(n=(20, 27, 33), r=(5, 7, 9), T=7, n_orb=5, seed=3):
+    """Different n and r per mode, none a multiple of a tile size."""
+    rng = np.random.default_rng(seed)
+    Ls = [0.22 * (k - 1) / 2 for k in n]
+    xs, ws = zip(*[W.uniform_grid(k, L) for k, L in zip(n, Ls)])
+    cen = rng.uniform(-1.5, 1.5, size=(n_orb, 3, 3))
+    exps = rng.uniform(0.4, 2.0, size=(n_orb, 3))
+    coefs = rng.standard_normal(size=(n_orb, 3))
+    psi = W.lowdin_orthonormalise(W.gaussian_sum_orbitals(xs, cen, exps, coefs), ws).astype(np.float32)
+    U = W.density_hosvd_basis(psi, r)
+    h = min(float(np.min(np.diff(v))) for v in xs)
+    theta, mu, ferr = W.exp_sum_inverse_r(T, h, math.sqrt(sum((2 * L) ** 2 for L in Ls)))
+    return W.System("ragged", list(xs), list(ws), U, theta, mu, psi, ferr)
+
+
+def gpu_apply(s, prec, tgt=None, occ_idx=None, limit=None):
+    P = _P()
+    ctx = P.Context.from_system(s, precision=prec)
+    if limit:
+        ctx.set_workspace_limit(limit)
+    occ = to_gpu(s.psi)
+    if isinstance(tgt, str):
+        out = P.tx_exchange_apply(ctx, occ)
+    elif isinstance(tgt, slice):
+        out = P.tx_exchange_apply(ctx, occ, occ[tgt])
+    else:
+        out = P.tx_exchange_apply(ctx, occ, to_gpu(tgt))
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_small_config_matches_oracle(prec):
+    s = W.config_small()
+    S = O.Setup.from_system(s)
+    ref = O.exchange_apply(s.psi, S)
+    got = gpu_apply(s, prec, "self")
+    assert rel(got, ref) < W_TOL[prec]
+    assert max_row_rel(got, ref) < 2 * W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_small_config_matches_oracle(prec):
+    P = _P()
+    s = W.config_small()
+    S = O.Setup.from_system(s)
+    ref = O.exchange_energy(s.psi, S)
+    ctx = P.Context.from_system(s, precision=prec)
+    e = float(P.tx_exchange_energy(ctx, to_gpu(s.psi)).item())
+    assert ref < 0
+    assert abs(e - ref) / abs(ref) < E_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("targets", ["self", "subset", "general"])
+def test_apply_ragged_shapes(prec, targets):
+    s = ragged_system()
+    S = O.Setup.from_system(s)
+    if targets == "self":
+        ref = O.exchange_apply(s.psi, S)
+        got = gpu_apply(s, prec, "self")
+    elif targets == "subset":
+        ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[1:4])
+        got = gpu_apply(s, prec, slice(1, 4))
+    else:
+        rng = np.random.default_rng(9)
+        tgt = (s.psi[:3] * 0.7 + 0.2 * rng.standard_normal(s.psi[:3].shape) * np.abs(s.psi[:3]).max()).astype(np.float32)
+        ref = O.exchange_apply(s.psi, S, psi_tgt=tgt)
+        got = gpu_apply(s, prec, tgt)
+    assert rel(got, ref) < W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pair_batching_does_not_change_the_result(prec):
+    s = ragged_system(n_orb=6)
+    one = gpu_apply(s, prec, "self")
+    many = gpu_apply(s, prec, "self", limit=1 << 20)     # forces one or two pairs per batch
+    assert rel(many, one) < 1e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_orbital_single_term(prec):
+    s = W.config_small(n=16, n_orb=1, rank=6, T=1, L=5.0)
+    S = O.Setup.from_system(s)
+    assert rel(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S)) < W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_rank_operator(prec):
+    s = W.config_small(n=16, n_orb=3, rank=16, T=6, L=5.0, full_rank=True)
+    S = O.Setup.from_system(s)
+    assert rel(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S)) < W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_gradient_matches_oracle(prec):
+    P = _P()
+    s = ragged_system(n=(14, 16, 18), r=(5, 6, 7), T=5, n_orb=3)
+    S = O.Setup.from_system(s)
+    E_ref, g_ref = O.exchange_energy_grad(s.psi, S)
+    ctx = P.Context.from_system(s, precision=prec)
+    e, g = P.tx_exchange_energy_grad(ctx, to_gpu(s.psi))
+    assert abs(float(e.item()) - E_ref) / abs(E_ref) < E_TOL[prec]
+    assert rel(g.cpu().numpy(), g_ref) < 5 * W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_vjp_matches_oracle(prec):
+    P = _P()
+    s = ragged_system(n=(14, 16, 18), r=(5, 6, 7), T=5, n_orb=3)
+    S = O.Setup.from_system(s)
+    rng = np.random.default_rng(4)
+    tgt = (s.psi[:2] + 0.1 * s.psi[1:3]).astype(np.float32)
+    cot = rng.standard_normal(tgt.shape).astype(np.float32)
+    go_ref, gt_ref = O.exchange_apply_vjp(s.psi, tgt, cot, S)
+    ctx = P.Context.from_system(s, precision=prec)
+    go, gt = P.tx_exchange_apply_vjp(ctx, to_gpu(s.psi), to_gpu(tgt), to_gpu(cot))
+    assert rel(go.cpu().numpy(), go_ref) < 5 * W_TOL[prec]
+    assert rel(gt.cpu().numpy(), gt_ref) < 5 * W_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pt_shaped_block_sampled_rows(prec):
+    """Full Pt-shaped size (96^3, 64 orbitals, rank 40, 40 terms); the oracle computes two
+    target rows against all 64 occupied orbitals."""
+    s = W.config_pt()
+    S = O.Setup.from_system(s)
+    got = gpu_apply(s, prec, "self")
+    for i in (0, 37):
+        ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[i:i + 1])
+        assert rel(got[i:i + 1], ref) < W_TOL[prec]
+
+
+def test_invalid_alignment_and_null_are_rejected():
+    P = _P()
+    import torch
+    s = W.config_small(n=12, n_orb=2, rank=4, T=2, L=4.0)
+    ctx = P.Context.from_system(s)
+    occ = to_gpu(s.psi)
+    buf = torch.zeros(occ.numel() + 1, dtype=torch.float32, device="cuda")
+    mis = buf[1:].view(occ.shape)                      # 4-byte offset: not 16-byte aligned
+    st = P.lib().tx_exchange_apply(ctx.handle, mis.data_ptr(), 2, None, 0, occ.data_ptr(), None)
+    assert st == -10
+    st = P.lib().tx_exchange_energy(ctx.handle, occ.data_ptr(), 2, None, None)
+    assert st == -1
