@@ -165,6 +165,16 @@ int tx_set_workspace_limit(tx_ctx* ctx, size_t bytes);
  * the context's last stream.  Returns TX_OK or TX_ERR_TIMEOUT. */
 int tx_check_device_error(tx_ctx* ctx);
 
+/*
+ * Self-check of the tensor-core GEMM building block used by every tensor-core precision (no
+ * counterpart in the paper): D[b][m][n] = sum_k A[b][m][k] B[b][n][k] for device float32
+ * A [batch][M][K], B [batch][N][K] (K a multiple of 8) rounded to the operand type of
+ * `precision` (split into hi + lo for the 3-pass precisions), D float32 [batch][M][N].
+ * Synchronises `stream`; allocates and frees its own scratch.
+ */
+int tx_selftest_gemm(int precision, int batch, int M, int N, int K, const float* A, const float* B, float* D,
+                     tx_stream_t stream);
+
 const char* tx_status_string(int status);
 const char* tx_last_error_message(void);
 

@@ -24,7 +24,7 @@ EXPORTED = [
     "tx_exchange_energy_grad", "tx_exchange_apply_vjp", "tx_workspace_bytes", "tx_set_workspace_limit",
     "tx_check_device_error", "tx_status_string", "tx_last_error_message", "tx_launch_count",
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
-    "tx_profile_read",
+    "tx_profile_read", "tx_selftest_gemm",
 ]
 
 
@@ -78,6 +78,8 @@ def lib():
     L.tx_profile_reset.restype = None
     L.tx_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
     L.tx_profile_read.restype = _I
+    L.tx_selftest_gemm.argtypes = [_I, _I, _I, _I, _I, _P, _P, _P, _P]
+    L.tx_selftest_gemm.restype = _I
     L.tx_exchange_energy.argtypes = [_P, _P, _I, _P, _P]
     L.tx_exchange_energy.restype = _I
     L.tx_exchange_energy_grad.argtypes = [_P, _P, _I, _P, _P, _P]
@@ -277,6 +279,17 @@ def tx_exchange_apply_vjp(ctx: Context, psi_occ, psi_tgt, grad_out, need_occ=Tru
                                      _ptr(grad_out), _ptr(g_occ), _ptr(g_tgt), _stream(stream))
     _check(st, "tx_exchange_apply_vjp")
     return g_occ, g_tgt
+
+
+def tx_selftest_gemm(precision, A, B, stream=None):
+    """D[b] = A[b] @ B[b]^T on the tensor cores (A [batch][M][K], B [batch][N][K] float32 CUDA)."""
+    batch, M, K = A.shape
+    N = B.shape[1]
+    D = torch.empty((batch, M, N), dtype=torch.float32, device=A.device)
+    st = lib().tx_selftest_gemm(int(Precision.parse(precision)), batch, M, N, K, _ptr(A.contiguous()),
+                                _ptr(B.contiguous()), _ptr(D), _stream(stream))
+    _check(st, "tx_selftest_gemm")
+    return D
 
 
 def tx_launch_count() -> int:

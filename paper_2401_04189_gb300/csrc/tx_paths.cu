@@ -124,7 +124,8 @@ int simt_batch(tx_ctx* c, const CallSpec& cs, const PairRec* recs, const PairRec
 int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     const long N3 = (long)c->n[0] * c->n[1] * c->n[2];
     const long P = pair_count(cs.mode, cs.n_occ, cs.n_tgt);
-    const bool tc = c->prec != TX_PREC_FP32;
+    // the tensor-core kernels cover the forward path; gradients run the float32 kernels
+    const bool tc = c->prec != TX_PREC_FP32 && (cs.kind == CALL_APPLY || cs.kind == CALL_ENERGY);
     const int ntables = cs.kind == CALL_VJP ? 2 : 1;
     const size_t recs_bytes = align_up(sizeof(PairRec) * (size_t)P, 256) * ntables;
     size_t per_pair;

@@ -1,38 +1,213 @@
-// Tensor-core (tcgen05 / TMEM / TMA) path.
+// Tensor-core path: operand preparation and the per-batch sequence of the forward hot path.
+//
+//   projection (Eq. TuckerDecompField, shared basis)
+//     S1[p][g][x][y] = sum_z rho_p[x][y][z] U3[z][g]        tc_project_mode3 (rho fused in)
+//     S2[p][g][b][x] = sum_y S1[p][g][x][y] U2[y][b]        tc_gemm
+//     G[p][g][b][a]  = sum_x S2[p][g][b][x] U1[x][a]        tc_gemm
+//   expansion (Eq. final)
+//     Z[p][t][x][g][b] = sum_a A_t1[x][a] G[p][g][b][a]     tc_gemm, every term t at once
+//     modes 2 and 3, the sum over t and the Hadamard/energy epilogue (Eq. hadam): tc_consume
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
 
 #include "tx_paths.h"
+#include "tx_tc_common.cuh"
+#include "tx_tc_ops.h"
 
 namespace tx {
 
+bool tc_consume_supported(const tx_ctx* c, bool tf32, bool split, std::string* why);
+
+namespace {
+
+// dst[r][c] (row stride ld) = operand(src[r * srs + c * scs]) for r < rows, c < cols
+__global__ void k_static_operand(const double* __restrict__ src, long rows, int cols, long srs, long scs, int ld,
+                                 int tf32, int split, void* dst, size_t lo_elems) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const long r = i / cols, c = i - r * cols;
+    const double v = src[r * srs + c * scs];
+    const long o = r * ld + c;
+    if (tf32) {
+        const float h = tc::tf32_hi((float)v);
+        ((float*)dst)[o] = h;
+        if (split) ((float*)dst)[o + lo_elems] = tc::tf32_hi((float)(v - (double)h));
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        ((__nv_bfloat16*)dst)[o] = h;
+        if (split) ((__nv_bfloat16*)dst)[o + lo_elems] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+    }
+}
+
+}  // namespace
+
+TcScratch tc_scratch(const tx_ctx* c) {
+    TcScratch s;
+    const size_t n1 = c->n[0], n2 = c->n[1], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2];
+    s.ld_y = pad8((int)n2);
+    s.ld_x = pad8((int)n1);
+    s.ld_a = pad8((int)r1);
+    s.ld_b = pad8((int)r2);
+    s.s1 = r3 * n1 * s.ld_y;
+    s.s2 = r3 * r2 * s.ld_x;
+    s.g = r3 * r2 * s.ld_a;
+    s.z = (size_t)c->T * n1 * r3 * s.ld_b;
+    return s;
+}
+
 bool tc_supported(const tx_ctx* c, std::string* why) {
-    (void)c;
-    if (why) *why = "tensor-core precisions are not built yet";
-    return false;
+    const bool tf32 = c->prec == TX_PREC_TF32 || c->prec == TX_PREC_TF32X3;
+    const bool split = c->prec == TX_PREC_TF32X3 || c->prec == TX_PREC_BF16X3;
+    if (c->n[2] % 4) {
+        if (why) *why = "tensor-core precisions need n3 % 4 == 0 (16-byte orbital rows for TMA)";
+        return false;
+    }
+    if (c->r[2] > 256) {
+        if (why) *why = "tensor-core precisions need r3 <= 256";
+        return false;
+    }
+    if ((long)c->T * c->n[0] > (1L << 30)) {
+        if (why) *why = "T * n1 too large";
+        return false;
+    }
+    return tc_consume_supported(c, tf32, split, why);
 }
+
+void tc_release(tx_ctx* c) {
+    if (!c->tc) return;
+    cudaFree(c->tc->buf);
+    delete c->tc;
+    c->tc = nullptr;
+}
+
 int tc_prepare(tx_ctx* c, cudaStream_t s) {
-    (void)c;
-    (void)s;
-    return fail(TX_ERR_UNSUPPORTED_PRECISION, "tensor-core precisions are not built yet");
+    tc_release(c);
+    TcOperands* op = new TcOperands();
+    op->prec = c->prec;
+    op->tf32 = c->prec == TX_PREC_TF32 || c->prec == TX_PREC_TF32X3;
+    op->split = c->prec == TX_PREC_TF32X3 || c->prec == TX_PREC_BF16X3;
+    op->esize = op->tf32 ? 4 : 2;
+    const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2], T = c->T;
+    const size_t e_u3 = (size_t)r3 * pad8(n3), e_u2 = (size_t)r2 * pad8(n2), e_u1 = (size_t)r1 * pad8(n1);
+    const size_t e_a1 = (size_t)T * n1 * pad8(r1), e_a2 = (size_t)T * n2 * pad8(r2), e_a3 = (size_t)T * n3 * pad8(r3);
+    auto al = [](size_t e) { return (e + 127) & ~(size_t)127; };   // 256-byte aligned pieces
+    const size_t tot = al(e_u3) + al(e_u2) + al(e_u1) + al(e_a1) + al(e_a2) + al(e_a3);
+    const size_t bytes = tot * op->esize * (op->split ? 2 : 1);
+    if (cudaMalloc(&op->buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete op;
+        return fail(TX_ERR_OOM, "tensor-core operand copies");
+    }
+    c->tc = op;
+    TX_TRY_CUDA(cudaMemsetAsync(op->buf, 0, bytes, s));
+    char* p = op->buf;
+    auto take = [&](size_t e) {
+        void* r = p;
+        p += al(e) * op->esize;
+        return r;
+    };
+    op->st.U3T = take(e_u3);
+    op->st.U2T = take(e_u2);
+    op->st.U1T = take(e_u1);
+    op->st.A1s = take(e_a1);
+    op->st.A2 = take(e_a2);
+    op->st.A3 = take(e_a3);
+    op->st.off_lo = tot * op->esize;
+    const size_t lo = tot;   // element offset of every lo copy
+    auto conv = [&](const double* src, long rows, int cols, long srs, long scs, int ld, void* dst) -> int {
+        const long n = rows * cols;
+        k_static_operand<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, rows, cols, srs, scs, ld, op->tf32 ? 1 : 0,
+                                                                    op->split ? 1 : 0, dst, lo);
+        TX_LAUNCHED();
+        return TX_OK;
+    };
+    // U_d^T: rows r_d, K = n_d  (U_d is [n_d][r_d])
+    TX_TRY(conv(c->d_U[2], r3, n3, 1, r3, pad8(n3), op->st.U3T));
+    TX_TRY(conv(c->d_U[1], r2, n2, 1, r2, pad8(n2), op->st.U2T));
+    TX_TRY(conv(c->d_U[0], r1, n1, 1, r1, pad8(n1), op->st.U1T));
+    // A_td: [T][n_d][r_d] -> rows (t, x), K = r_d
+    TX_TRY(conv(c->d_A64[0], (long)T * n1, r1, r1, 1, pad8(r1), op->st.A1s));
+    TX_TRY(conv(c->d_A64[1], (long)T * n2, r2, r2, 1, pad8(r2), op->st.A2));
+    TX_TRY(conv(c->d_A64[2], (long)T * n3, r3, r3, 1, pad8(r3), op->st.A3));
+    return TX_OK;
 }
-void tc_release(tx_ctx* c) { (void)c; }
+
 size_t tc_batch_bytes_per_pair(const tx_ctx* c, int kind) {
-    (void)c;
     (void)kind;
-    return 0;
+    const TcScratch sc = tc_scratch(c);
+    const TcOperands* op = c->tc;
+    return (sc.s1 + sc.s2 + sc.g + sc.z) * op->esize * (op->split ? 2 : 1) + 1024;
 }
-long tc_epart_per_pair(const tx_ctx* c) {
-    (void)c;
-    return 0;
-}
+
+long tc_epart_per_pair(const tx_ctx* c) { return tc_consume_blocks(c); }
+
 int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStream_t s) {
-    (void)c;
-    (void)cs;
-    (void)b;
-    (void)s;
-    return fail(TX_ERR_UNSUPPORTED_PRECISION, "tensor-core precisions are not built yet");
+    if (cs.kind != CALL_APPLY && cs.kind != CALL_ENERGY)
+        return fail(TX_ERR_UNSUPPORTED_PRECISION, "tensor-core batches run the forward path only");
+    const TcOperands* op = c->tc;
+    const TcScratch sc = tc_scratch(c);
+    const int np = b.np;
+    const int eb = op->esize, mult = op->split ? 2 : 1;
+    const int n1 = c->n[0], n2 = c->n[1], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2], T = c->T;
+    char* S1 = b.scratch;
+    char* S2 = S1 + (size_t)np * sc.s1 * eb * mult;
+    char* G = S2 + (size_t)np * sc.s2 * eb * mult;
+    char* Z = G + (size_t)np * sc.g * eb * mult;
+    const int out_type = op->tf32 ? (op->split ? TC_OUT_F32_SPLIT : TC_OUT_F32) : (op->split ? TC_OUT_BF16_SPLIT : TC_OUT_BF16);
+    const bool subset = cs.mode == PAIRS_SUBSET;
+    const float* SA = subset ? cs.occ : cs.tgt;
+    const int nA = subset ? cs.n_occ : cs.n_tgt;
+    auto lo_of = [&](const void* hi, size_t per_pair) -> const void* {
+        return op->split ? (const char*)hi + (size_t)np * per_pair * eb : nullptr;
+    };
+
+    // 1. S1 = rho x3 U3^T (rho = psi_a psi_b formed in the kernel)
+    TX_TRY(tc_project_mode3(c, b.recs, b.p0, np, SA, nA, cs.occ, cs.n_occ, 0, S1, s));
+
+    // 2. S2[p][g][b][x] = sum_y S1[p][(g,x)][y] U2T[b][y]
+    {
+        TcOperand A{S1, lo_of(S1, sc.s1), (uint64_t)n2, (uint64_t)r3 * n1, (uint64_t)np, (uint64_t)sc.ld_y, sc.s1};
+        TcOperand B{op->st.U2T, op->split ? (const char*)op->st.U2T + op->st.off_lo : nullptr, (uint64_t)n2,
+                    (uint64_t)r2, 1, (uint64_t)pad8(n2), 0};
+        TcGemmArgs g{};
+        g.M = r3 * n1; g.N = r2; g.K = n2; g.nb1 = np; g.nb2 = 1;
+        g.a_z1 = 1;
+        g.C = S2; g.rdiv = n1; g.c_mh = (long)r2 * sc.ld_x; g.c_m = 1; g.c_n = sc.ld_x; g.c_b1 = (long)sc.s2;
+        g.c_lo = (long)np * sc.s2; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj2", s));
+    }
+    // 3. G[p][(g,b)][a] = sum_x S2[p][(g,b)][x] U1T[a][x]
+    {
+        TcOperand A{S2, lo_of(S2, sc.s2), (uint64_t)n1, (uint64_t)r3 * r2, (uint64_t)np, (uint64_t)sc.ld_x, sc.s2};
+        TcOperand B{op->st.U1T, op->split ? (const char*)op->st.U1T + op->st.off_lo : nullptr, (uint64_t)n1,
+                    (uint64_t)r1, 1, (uint64_t)pad8(n1), 0};
+        TcGemmArgs g{};
+        g.M = r3 * r2; g.N = r1; g.K = n1; g.nb1 = np; g.nb2 = 1;
+        g.a_z1 = 1;
+        g.C = G; g.c_m = sc.ld_a; g.c_n = 1; g.c_b1 = (long)sc.g;
+        g.c_lo = (long)np * sc.g; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj1", s));
+    }
+    // 4. Z[p][(t,x)][(g,b)] = sum_a A1s[(t,x)][a] G[p][(g,b)][a]
+    {
+        TcOperand A{op->st.A1s, op->split ? (const char*)op->st.A1s + op->st.off_lo : nullptr, (uint64_t)r1,
+                    (uint64_t)T * n1, 1, (uint64_t)pad8(r1), 0};
+        TcOperand B{G, lo_of(G, sc.g), (uint64_t)r1, (uint64_t)r3 * r2, (uint64_t)np, (uint64_t)sc.ld_a, sc.g};
+        TcGemmArgs g{};
+        g.M = T * n1; g.N = r3 * r2; g.K = r1; g.nb1 = np; g.nb2 = 1;
+        g.b_z1 = 1;
+        g.C = Z; g.c_m = (long)r3 * sc.ld_b; g.cdiv = r2; g.c_nh = sc.ld_b; g.c_n = 1; g.c_b1 = (long)sc.z;
+        g.c_lo = (long)np * sc.z; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
+    }
+    // 5. modes 2 and 3 for every term, phi accumulated in TMEM, Hadamard / energy epilogue
+    int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
+    if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
+    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, flags, b.epart, s));
+    (void)r1;
+    return TX_OK;
 }
 
 }  // namespace tx

@@ -1,0 +1,388 @@
+// Generic batched tensor-core GEMM on tcgen05: D[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k]
+// with A and B K-major in global memory, loaded by TMA (128-byte swizzle) through a multi-
+// stage mbarrier pipeline, accumulated in TMEM by one issuing thread, and written back by
+// four epilogue warps with arbitrary output strides (float32 or bf16, optionally split into
+// hi + lo parts for the 3-pass precisions).
+//
+// Used for the small mode products of the hot path: the second and third modes of the
+// projection onto the Tucker core, the first mode of the expansion for every Gaussian term
+// (Eq. final) and the first mode of the adjoint.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "tx_internal.h"
+#include "tx_tc.h"
+#include "tx_tc_common.cuh"
+
+namespace tx {
+namespace tcg {
+
+using namespace tx::tc;
+
+constexpr int kMaxStages = 4;
+constexpr int kBM = 128;
+
+__device__ __forceinline__ void store_out(const TcGemmArgs& g, long o, float v) {
+    if (g.c_type == TC_OUT_F32) {
+        ((float*)g.C)[o] = v;
+    } else if (g.c_type == TC_OUT_BF16) {
+        ((__nv_bfloat16*)g.C)[o] = __float2bfloat16_rn(v);
+    } else if (g.c_type == TC_OUT_F32_SPLIT) {
+        const float hi = tf32_hi(v);
+        ((float*)g.C)[o] = hi;
+        ((float*)g.C)[o + g.c_lo] = tf32_hi(v - hi);
+    } else {   // TC_OUT_BF16_SPLIT
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        ((__nv_bfloat16*)g.C)[o] = hi;
+        ((__nv_bfloat16*)g.C)[o + g.c_lo] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+template <bool TF32, bool SPLIT>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+              const __grid_constant__ CUtensorMap mAlo, const __grid_constant__ CUtensorMap mBlo, TcGemmArgs g) {
+    constexpr int kAtomK = TF32 ? 32 : 64;      // elements per 128-byte row
+    constexpr int kMmaK = TF32 ? 8 : 16;        // K per instruction (32 bytes)
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
+    __shared__ uint32_t tmem_base;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int BN = g.BN;
+    const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)BN * 128;
+    const uint32_t stage_bytes = (SPLIT ? 2 : 1) * (a_bytes + b_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.z, b1 = b % g.nb1, b2 = b / g.nb1;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int nk = (g.K + kAtomK - 1) / kAtomK;
+    const int kStages = g.stages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 2) {
+        tmem_alloc(&tmem_base, g.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        const int arow = m0 + b1 * g.a_row1 + b2 * g.a_row2, az = b1 * g.a_z1 + b2 * g.a_z2;
+        const int brow = n0 + b1 * g.b_row1 + b2 * g.b_row2, bz = b1 * g.b_z1 + b2 * g.b_z2;
+        bool ok = true;
+        int issued = 0;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, g.err, 11)) { ok = false; break; }
+            issued = kb + 1;
+            uint8_t* st = smem + s * stage_bytes;
+            mbar_arrive_expect_tx(&full_bar[s], stage_bytes);
+            tma_load_3d(st, &mA, &full_bar[s], kb * kAtomK, arow, az);
+            tma_load_3d(st + a_bytes, &mB, &full_bar[s], kb * kAtomK, brow, bz);
+            if constexpr (SPLIT) {
+                tma_load_3d(st + a_bytes + b_bytes, &mAlo, &full_bar[s], kb * kAtomK, arow, az);
+                tma_load_3d(st + 2 * a_bytes + b_bytes, &mBlo, &full_bar[s], kb * kAtomK, brow, bz);
+            }
+        }
+        // do not leave the kernel with copies in flight
+        if (!ok)
+            for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+                mbar_drain(&full_bar[kb % kStages], (kb / kStages) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = TF32 ? idesc_tf32(kBM, BN) : idesc_bf16(kBM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(&full_bar[s], (kb / kStages) & 1, g.err, 13)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(smem + s * stage_bytes);
+            const uint32_t b_addr = a_addr + a_bytes;
+            const int krem = g.K - kb * kAtomK;
+            const int nsteps = (min(krem, kAtomK) + kMmaK - 1) / kMmaK;
+            for (int k = 0; k < nsteps; ++k) {
+                const uint64_t ad = sdesc_sw128(a_addr + k * 32), bd = sdesc_sw128(b_addr + k * 32);
+                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                mma_ss<TF32>(tmem, ad, bd, idesc, acc);
+                if constexpr (SPLIT) {
+                    const uint64_t alo = sdesc_sw128(a_addr + a_bytes + b_bytes + k * 32);
+                    const uint64_t blo = sdesc_sw128(a_addr + 2 * a_bytes + b_bytes + k * 32);
+                    mma_ss<TF32>(tmem, ad, blo, idesc, 1u);
+                    mma_ss<TF32>(tmem, alo, bd, idesc, 1u);
+                }
+            }
+            mma_commit(&empty_bar[s]);
+        }
+        (void)ok;
+        mma_commit(&done_bar);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: 4 warps, one TMEM lane (= output row) per thread ----------------
+    const bool ok = mbar_wait(&done_bar, 0, g.err, 14);
+    tc_fence_after();
+    const long boff = (long)b1 * g.c_b1 + (long)b2 * g.c_b2;
+    auto row_off = [&](int m) { return boff + (long)(m / g.rdiv) * g.c_mh + (long)(m % g.rdiv) * g.c_m; };
+    auto col_off = [&](int n) { return (long)(n / g.cdiv) * g.c_nh + (long)(n % g.cdiv) * g.c_n; };
+    if (ok && g.c_m == 1) {
+        // consecutive rows are adjacent in memory: lanes (= consecutive rows) already coalesce
+        const int m = m0 + warp * 32 + lane;
+        const long base = row_off(m);
+        int nq = n0 / g.cdiv, nr = n0 % g.cdiv;     // column split tracked incrementally
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c0 + j;
+                if (m < g.M && n < g.N)
+                    store_out(g, base + (long)nq * g.c_nh + (long)nr * g.c_n, g.alpha * __uint_as_float(r[j]));
+                if (++nr == g.cdiv) {
+                    nr = 0;
+                    ++nq;
+                }
+            }
+        }
+    } else if (ok) {
+        // columns are (mostly) contiguous: stage 32 rows x 64 columns per warp in the idle
+        // pipeline buffers, then write each row segment with the whole warp
+        float* stg = (float*)(smem + warp * (32 * 65 * 4));
+        // row offsets of this warp's 32 rows: one division each, shared through a shuffle
+        const int mrow = m0 + warp * 32 + lane;
+        const long my_row = row_off(mrow);
+        for (int cb = 0; cb < BN; cb += 64) {
+            const int nck = min(64, BN - cb) / 16;
+            uint32_t r[4][16];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nck) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb + 16 * c), r[c]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nck)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) stg[lane * 65 + 16 * c + j] = __uint_as_float(r[c][j]);
+            __syncwarp();
+            // this lane's two columns: offsets computed once per chunk
+            const int cc0 = lane, cc1 = 32 + lane;
+            const int n_0 = n0 + cb + cc0, n_1 = n0 + cb + cc1;
+            const bool v0 = cb + cc0 < BN && n_0 < g.N, v1 = cb + cc1 < BN && n_1 < g.N;
+            const long co0 = v0 ? col_off(n_0) : 0, co1 = v1 ? col_off(n_1) : 0;
+            for (int rr = 0; rr < 32; ++rr) {
+                const long base = __shfl_sync(0xffffffffu, my_row, rr);
+                if (m0 + warp * 32 + rr >= g.M) break;
+                if (v0) store_out(g, base + co0, g.alpha * stg[rr * 65 + cc0]);
+                if (v1) store_out(g, base + co1, g.alpha * stg[rr * 65 + cc1]);
+            }
+            __syncwarp();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(tmem, g.tmem_cols);
+}
+
+}  // namespace tcg
+
+// ======================================================================================
+// host side
+// ======================================================================================
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+int make_map(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent, uint64_t rows, uint64_t depth,
+             uint64_t row_stride_elems, uint64_t depth_stride_elems, uint32_t box_k, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (((uintptr_t)base & 15) || (row_stride_elems * elem_bytes) % 16 || (depth_stride_elems * elem_bytes) % 16)
+        return fail(TX_ERR_ALIGNMENT, "tensor map base / strides must be 16-byte multiples");
+    cuuint64_t dims[3] = {k_extent, rows, depth};
+    cuuint64_t strides[2] = {row_stride_elems * elem_bytes, depth_stride_elems * elem_bytes};
+    if (depth <= 1) strides[1] = strides[0] * rows;
+    if (strides[1] == 0) strides[1] = 16;
+    cuuint32_t box[3] = {box_k, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    return TX_OK;
+}
+
+int make_map_f32_plain(CUtensorMap* m, const void* base, uint64_t k_extent, uint64_t rows, uint64_t depth,
+                       uint32_t box_k, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (((uintptr_t)base & 15) || (k_extent * 4) % 16)
+        return fail(TX_ERR_UNSUPPORTED_SHAPE, "tensor-core path needs n3 % 4 == 0 and 16-byte aligned orbitals");
+    cuuint64_t dims[3] = {k_extent, rows, depth < 1 ? 1 : depth};
+    cuuint64_t strides[2] = {k_extent * 4, k_extent * 4 * rows};
+    cuuint32_t box[3] = {box_k, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled (float32 plain) failed (code " + std::to_string((int)r) + ")");
+    return TX_OK;
+}
+
+static uint32_t tmem_cols_for(int n) {
+    uint32_t c = 32;
+    while ((int)c < n) c <<= 1;
+    return c;
+}
+
+int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf32, bool split, const char* prof,
+                   cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return TX_OK;
+    if (g.rdiv <= 0) {
+        g.rdiv = 1 << 30;
+        g.c_mh = 0;
+    }
+    if (g.cdiv <= 0) {
+        g.cdiv = 1 << 30;
+        g.c_nh = 0;
+    }
+    if (g.BN <= 0) {
+        g.BN = 16;
+        while (g.BN < g.N && g.BN < 256) g.BN += 16;
+    }
+    if (g.BN % 16 || g.BN > 256) return fail(TX_ERR_INVALID_ARG, "tc_gemm: BN must be a multiple of 16 <= 256");
+    size_t stage = (size_t)(split ? 2 : 1) * (128 * 128 + (size_t)g.BN * 128);
+    const size_t budget = 225 * 1024;
+    while (g.BN > 16 && 2 * stage + 1024 > budget) {   // keep at least two stages in flight
+        g.BN -= 16;
+        stage = (size_t)(split ? 2 : 1) * (128 * 128 + (size_t)g.BN * 128);
+    }
+    g.tmem_cols = tmem_cols_for(g.BN);
+    g.stages = (int)std::min<size_t>(tcg::kMaxStages, (budget - 1024) / stage);
+    const size_t smem = stage * g.stages + 1024;
+    const int eb = tf32 ? 4 : 2;
+    const uint32_t atom_k = 128 / eb;
+    CUtensorMap mA, mB, mAlo, mBlo;
+    TX_TRY(make_map(&mA, A.hi, eb, A.k_extent, A.rows, A.depth, A.row_stride, A.depth_stride, atom_k, 128));
+    TX_TRY(make_map(&mB, B.hi, eb, B.k_extent, B.rows, B.depth, B.row_stride, B.depth_stride, atom_k, g.BN));
+    if (split) {
+        TX_TRY(make_map(&mAlo, A.lo, eb, A.k_extent, A.rows, A.depth, A.row_stride, A.depth_stride, atom_k, 128));
+        TX_TRY(make_map(&mBlo, B.lo, eb, B.k_extent, B.rows, B.depth, B.row_stride, B.depth_stride, atom_k, g.BN));
+    } else {
+        mAlo = mA;
+        mBlo = mB;
+    }
+    dim3 grid((g.N + g.BN - 1) / g.BN, (g.M + 127) / 128, g.nb1 * g.nb2);
+    if (grid.z > 65535) return fail(TX_ERR_INVALID_ARG, "tc_gemm: too many batches in one launch");
+    const int ps = prof_begin(prof ? prof : "tc_gemm", s);
+#define TCG_LAUNCH(TF, SP)                                                                                       \
+    do {                                                                                                         \
+        auto fn = tcg::k_tc_gemm<TF, SP>;                                                                        \
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                        \
+        fn<<<grid, 128, smem, s>>>(mA, mB, mAlo, mBlo, g);                                                       \
+    } while (0)
+    if (tf32) {
+        if (split) TCG_LAUNCH(true, true); else TCG_LAUNCH(true, false);
+    } else {
+        if (split) TCG_LAUNCH(false, true); else TCG_LAUNCH(false, false);
+    }
+#undef TCG_LAUNCH
+    prof_end(ps, s);
+    TX_LAUNCHED();
+    return TX_OK;
+}
+
+// ---- self-test of the building block ---------------------------------------------------
+namespace {
+__global__ void k_split_f32(const float* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i], h = tc::tf32_hi(v);
+    hi[i] = h;
+    lo[i] = v - h;
+}
+__global__ void k_split_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                             long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+}  // namespace
+
+}  // namespace tx
+
+using namespace tx;
+
+// D[b][m][n] = sum_k A[b][m][k] B[b][n][k], A [batch][M][K], B [batch][N][K] float32 row-major
+// (K a multiple of 8), D float32; the operands are rounded to the precision's operand type.
+extern "C" int tx_selftest_gemm(int precision, int batch, int M, int N, int K, const float* A, const float* B,
+                                float* D, tx_stream_t stream) {
+    if (!A || !B || !D || batch < 1 || M < 1 || N < 1 || K < 1 || K % 8)
+        return fail(TX_ERR_INVALID_ARG, "selftest_gemm: bad arguments");
+    if (precision == TX_PREC_FP32) return fail(TX_ERR_UNSUPPORTED_PRECISION, "selftest_gemm: tensor precisions only");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tf32 = precision == TX_PREC_TF32 || precision == TX_PREC_TF32X3;
+    const bool split = precision == TX_PREC_TF32X3 || precision == TX_PREC_BF16X3;
+    const int eb = tf32 ? 4 : 2;
+    const long na = (long)batch * M * K, nbb = (long)batch * N * K;
+    char* buf = nullptr;
+    TX_TRY_CUDA(cudaMalloc(&buf, (size_t)eb * 2 * (na + nbb) + 256));
+    char* ahi = buf;
+    char* alo = ahi + eb * na;
+    char* bhi = alo + eb * na;
+    char* blo = bhi + eb * nbb;
+    if (tf32) {
+        k_split_f32<<<(na + 255) / 256, 256, 0, s>>>(A, (float*)ahi, (float*)alo, na);
+        k_split_f32<<<(nbb + 255) / 256, 256, 0, s>>>(B, (float*)bhi, (float*)blo, nbb);
+    } else {
+        k_split_bf16<<<(na + 255) / 256, 256, 0, s>>>(A, (__nv_bfloat16*)ahi, (__nv_bfloat16*)alo, na);
+        k_split_bf16<<<(nbb + 255) / 256, 256, 0, s>>>(B, (__nv_bfloat16*)bhi, (__nv_bfloat16*)blo, nbb);
+    }
+    TcOperand oa{ahi, alo, (uint64_t)K, (uint64_t)M, (uint64_t)batch, (uint64_t)K, (uint64_t)M * K};
+    TcOperand ob{bhi, blo, (uint64_t)K, (uint64_t)N, (uint64_t)batch, (uint64_t)K, (uint64_t)N * K};
+    TcGemmArgs g{};
+    g.M = M; g.N = N; g.K = K; g.nb1 = batch; g.nb2 = 1;
+    g.a_z1 = 1; g.b_z1 = 1;
+    g.C = D; g.c_m = N; g.c_n = 1; g.c_b1 = (long)M * N; g.c_type = TC_OUT_F32; g.alpha = 1.f;
+    static int* d_err = nullptr;
+    if (!d_err) TX_TRY_CUDA(cudaMalloc(&d_err, 4 * sizeof(int)));
+    TX_TRY_CUDA(cudaMemsetAsync(d_err, 0, 4 * sizeof(int), s));
+    g.err = d_err;
+    int st = tc_gemm_launch(oa, ob, g, tf32, split, "selftest", s);
+    cudaStreamSynchronize(s);
+    int h[2] = {0, 0};
+    cudaMemcpy(h, d_err, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (st != TX_OK) return st;
+    if (h[0]) return fail(TX_ERR_TIMEOUT, "selftest_gemm: device wait gave up at site " + std::to_string(h[1]));
+    TX_TRY_CUDA(cudaGetLastError());
+    return TX_OK;
+}

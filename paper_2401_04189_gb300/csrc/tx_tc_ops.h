@@ -1,0 +1,46 @@
+// Tensor-core path: operand copies owned by the context and the per-pair scratch layout.
+#pragma once
+
+#include "tx_tc.h"
+
+namespace tx {
+
+inline int pad8(int v) { return (v + 7) & ~7; }
+inline int pad16(int v) { return (v + 15) & ~15; }
+
+// Static operands, K-major with 16-byte row strides, in the operand type of the precision
+// (bf16, or float32 holding TF32 values).  For the 3-pass precisions `lo` holds x - hi.
+struct TcStatic {
+    void* U3T;   // [r3][ld(n3)]     rows gamma, K = z        (projection, mode 3)
+    void* U2T;   // [r2][ld(n2)]     rows beta,  K = y        (projection, mode 2)
+    void* U1T;   // [r1][ld(n1)]     rows alpha, K = x        (projection, mode 1)
+    void* A1s;   // [T*n1][ld(r1)]   rows (t,x), K = alpha    (expansion, mode 1, every term)
+    void* A2;    // [T][n2][ld(r2)]  rows y, K = beta         (expansion, mode 2)
+    void* A3;    // [T][n3][ld(r3)]  rows z, K = gamma, mu_t folded in (expansion, mode 3)
+    size_t off_lo;   // byte offset from each hi array to its lo copy (3-pass precisions)
+};
+
+struct TcOperands {
+    int prec;
+    bool tf32, split;
+    int esize;            // bytes per operand element
+    char* buf;            // one allocation for every static operand (hi, then lo)
+    TcStatic st;
+    int bx;               // x planes per expansion CTA
+};
+
+// per-pair scratch (elements of the operand type; doubled for split precisions)
+struct TcScratch {
+    size_t s1, s2, g, z;  // element counts per pair
+    int ld_y, ld_x, ld_a, ld_b;
+};
+TcScratch tc_scratch(const tx_ctx* c);
+
+int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
+                     int nB, int flags, void* S1, cudaStream_t s);
+int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
+               const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
+               cudaStream_t s);
+long tc_consume_blocks(const tx_ctx* c);
+
+}  // namespace tx

@@ -1,0 +1,274 @@
+// Projection onto the shared Tucker basis, first contraction (mode 3), on tcgen05 with the
+// pair-density producer fused in (the pair product of the "Convolution operation" section,
+// then Eq. TuckerDecompField with a shared basis):
+//
+//   S1[p][gamma][x][y] = sum_z rho_p[x][y][z] U3[z][gamma],   rho_p = psi_a * psi_b (* w)
+//
+// One CTA owns 128 consecutive (x, y) rows of one pair.  TMA brings the float32 orbital tiles
+// of both factors into shared memory (double-buffered); four warps form rho in registers,
+// round it to the operand type and write it in the 128-byte swizzled K-major layout; one
+// thread issues the MMAs against U3^T; the accumulator lives in TMEM.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "tx_tc_common.cuh"
+#include "tx_tc_ops.h"
+
+namespace tx {
+namespace tcp {
+
+using namespace tx::tc;
+
+struct ProjArgs {
+    int n1, n2, n3, r3, ld_y;
+    int N3p;                 // r3 rounded up to 16 (MMA N)
+    int p0;
+    const PairRec* recs;
+    const float* w1;
+    const float* w2;
+    const float* w3;
+    int flags;
+    void* S1;                // [pair][r3][n1][ld_y]
+    size_t s1_pair;          // elements per pair
+    size_t s1_lo;            // element offset of the lo part
+    uint32_t tmem_cols;
+    int* err;
+};
+
+template <bool TF32, bool SPLIT>
+__global__ void __launch_bounds__(128, 1)
+    k_project3(const __grid_constant__ CUtensorMap mPsiA, const __grid_constant__ CUtensorMap mPsiB,
+               const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mUlo, ProjArgs a) {
+    constexpr int ZB = TF32 ? 32 : 64;          // z per 128-byte operand row
+    constexpr int kMmaK = TF32 ? 8 : 16;
+    constexpr uint32_t PSI_BYTES = 128 * ZB * 4; // one float32 orbital tile
+    constexpr uint32_t RHO_BYTES = 128 * 128;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[2], rho_free[2], done_bar, u_bar;
+    __shared__ uint32_t tmem_base;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t B_BYTES = (uint32_t)a.N3p * 128;
+    const int nk = (a.n3 + ZB - 1) / ZB;
+    // layout: [rho hi x2][rho lo x2][U3^T hi, every K atom][U3^T lo][psiA x2][psiB x2]
+    // U3^T is loaded once and stays: the MMAs read it asynchronously, so it must not share a
+    // buffer with the orbital tiles that are refilled while earlier MMAs may still run.
+    uint8_t* rho = smem;
+    uint8_t* rho_lo = rho + 2 * RHO_BYTES;
+    uint8_t* bt = rho + (SPLIT ? 4 : 2) * RHO_BYTES;
+    uint8_t* bt_lo = bt + nk * B_BYTES;
+    uint8_t* psa = bt + (SPLIT ? 2 : 1) * nk * B_BYTES;
+    uint8_t* psb = psa + 2 * PSI_BYTES;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * 128, pl = blockIdx.y;
+    const PairRec rec = a.recs[a.p0 + pl];
+    const uint32_t stage_tx = 2 * PSI_BYTES;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&rho_free[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        mbar_init(&u_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, a.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    auto issue_load = [&](int kb) {
+        const int s = kb & 1;
+        mbar_arrive_expect_tx(&full_bar[s], stage_tx);
+        tma_load_3d(psa + s * PSI_BYTES, &mPsiA, &full_bar[s], kb * ZB, m0, rec.ia);
+        tma_load_3d(psb + s * PSI_BYTES, &mPsiB, &full_bar[s], kb * ZB, m0, rec.ib);
+    };
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&u_bar, (SPLIT ? 2 : 1) * nk * B_BYTES);
+        for (int kb = 0; kb < nk; ++kb) {
+            tma_load_3d(bt + kb * B_BYTES, &mU, &u_bar, kb * ZB, 0, 0);
+            if constexpr (SPLIT) tma_load_3d(bt_lo + kb * B_BYTES, &mUlo, &u_bar, kb * ZB, 0, 0);
+        }
+        issue_load(0);
+        if (nk > 1) issue_load(1);
+    }
+
+    bool ok = true;
+    int issued = nk > 1 ? 2 : 1;
+    const uint32_t idesc = TF32 ? idesc_tf32(128, a.N3p) : idesc_bf16(128, a.N3p);
+    for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb & 1;
+        bool good = mbar_wait(&full_bar[s], (kb >> 1) & 1, a.err, 21);
+        if (good && kb >= 2) good = mbar_wait(&rho_free[s], ((kb - 2) >> 1) & 1, a.err, 22);
+        if (good && kb == 0) good = mbar_wait(&u_bar, 0, a.err, 25);
+        if (good) {
+            // rho = psi_a * psi_b (* w) -> operand tile (128-byte swizzle)
+            const float* A = (const float*)(psa + s * PSI_BYTES);
+            const float* B = (const float*)(psb + s * PSI_BYTES);
+            uint8_t* R = rho + s * RHO_BYTES;
+            uint8_t* Rl = rho_lo + s * RHO_BYTES;
+            for (int r = warp; r < 128; r += 4) {
+                float wr = 1.f;
+                if (a.flags & PROD_MULW) {
+                    const int m = m0 + r;
+                    const int x = m / a.n2, y = m - x * a.n2;
+                    wr = (x < a.n1) ? a.w1[x] * a.w2[y] : 0.f;
+                }
+                if constexpr (TF32) {
+                    const int zc = kb * ZB + lane;
+                    float v = A[r * ZB + lane] * B[r * ZB + lane];
+                    if (a.flags & PROD_MULW) v *= wr * (zc < a.n3 ? a.w3[zc] : 0.f);
+                    const float h = tf32_hi(v);
+                    const uint32_t off = sw128_offset(r, 4 * lane);
+                    *(float*)(R + off) = h;
+                    if constexpr (SPLIT) *(float*)(Rl + off) = tf32_hi(v - h);
+                } else {
+                    const float2 va = *(const float2*)(A + r * ZB + 2 * lane);
+                    const float2 vb = *(const float2*)(B + r * ZB + 2 * lane);
+                    float v0 = va.x * vb.x, v1 = va.y * vb.y;
+                    if (a.flags & PROD_MULW) {
+                        const int zc = kb * ZB + 2 * lane;
+                        v0 *= wr * (zc < a.n3 ? a.w3[zc] : 0.f);
+                        v1 *= wr * (zc + 1 < a.n3 ? a.w3[zc + 1] : 0.f);
+                    }
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    const uint32_t off = sw128_offset(r, 4 * lane);
+                    *(__nv_bfloat162*)(R + off) = h;
+                    if constexpr (SPLIT) {
+                        const float2 hf = __bfloat1622float2(h);
+                        *(__nv_bfloat162*)(Rl + off) = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                    }
+                }
+            }
+        }
+        fence_async_smem();
+        ok = __syncthreads_and(good) != 0;      // block-uniform: everyone stops together
+        if (!ok) break;
+        if (threadIdx.x == 0) {
+            if (kb + 2 < nk) {                   // buffer s is no longer read
+                issue_load(kb + 2);
+                ++issued;
+            }
+            tc_fence_after();
+            const uint32_t ra = smem_u32(rho + s * RHO_BYTES), rl = smem_u32(rho_lo + s * RHO_BYTES);
+            const uint32_t ba = smem_u32(bt + kb * B_BYTES), bl = smem_u32(bt_lo + kb * B_BYTES);
+            const int nsteps = (min(a.n3 - kb * ZB, ZB) + kMmaK - 1) / kMmaK;
+            for (int k = 0; k < nsteps; ++k) {
+                const uint64_t ad = sdesc_sw128(ra + 32 * k), bd = sdesc_sw128(ba + 32 * k);
+                mma_ss<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                if constexpr (SPLIT) {
+                    mma_ss<TF32>(tmem, ad, sdesc_sw128(bl + 32 * k), idesc, 1u);
+                    mma_ss<TF32>(tmem, sdesc_sw128(rl + 32 * k), bd, idesc, 1u);
+                }
+            }
+            mma_commit(&rho_free[s]);
+            if (kb == nk - 1) mma_commit(&done_bar);
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        mma_commit(&done_bar);
+        // do not exit with copies in flight: wait (bounded) for every issued stage
+        for (int kb = (issued > 2 ? issued - 2 : 0); kb < issued; ++kb) mbar_drain(&full_bar[kb & 1], (kb >> 1) & 1);
+        mbar_drain(&u_bar, 0);
+    }
+    __syncwarp();
+    // epilogue: S1[p][gamma][x][y]
+    const bool ok2 = mbar_wait(&done_bar, 0, a.err, 23);
+    tc_fence_after();
+    if (ok2 && ok) {
+        const int m = m0 + warp * 32 + lane;
+        const int x = m / a.n2, y = m - x * a.n2;
+        const bool valid = x < a.n1;
+        const size_t base = (size_t)pl * a.s1_pair + (size_t)x * a.ld_y + y;
+        const size_t gstride = (size_t)a.n1 * a.ld_y;
+        for (int c0 = 0; c0 < a.N3p; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            tmem_ld_wait();
+            if (!valid) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int g = c0 + j;
+                if (g >= a.r3) break;
+                const float v = __uint_as_float(r[j]);
+                const size_t o = base + (size_t)g * gstride;
+                if constexpr (TF32) {
+                    const float h = tf32_hi(v);
+                    ((float*)a.S1)[o] = h;
+                    if constexpr (SPLIT) ((float*)a.S1)[o + a.s1_lo] = tf32_hi(v - h);
+                } else {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    ((__nv_bfloat16*)a.S1)[o] = h;
+                    if constexpr (SPLIT) ((__nv_bfloat16*)a.S1)[o + a.s1_lo] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+}  // namespace tcp
+
+int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
+                     int nB, int flags, void* S1, cudaStream_t s) {
+    const TcOperands* op = c->tc;
+    const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r3 = c->r[2];
+    const TcScratch sc = tc_scratch(c);
+    tcp::ProjArgs a{};
+    a.n1 = n1; a.n2 = n2; a.n3 = n3; a.r3 = r3; a.ld_y = sc.ld_y;
+    a.N3p = pad16(r3);
+    a.p0 = p0; a.recs = recs;
+    a.w1 = c->f_w[0]; a.w2 = c->f_w[1]; a.w3 = c->f_w[2];
+    a.flags = flags;
+    a.S1 = S1;
+    a.s1_pair = sc.s1;
+    a.s1_lo = (size_t)np * sc.s1;          // lo part follows the batch's hi part
+    a.tmem_cols = a.N3p <= 32 ? 32 : (a.N3p <= 64 ? 64 : (a.N3p <= 128 ? 128 : 256));
+    a.err = c->d_err;
+    if (a.N3p > 256) return fail(TX_ERR_UNSUPPORTED_SHAPE, "tensor-core projection needs r3 <= 256");
+    const int ZB = op->tf32 ? 32 : 64;
+    const long nrows = (long)n1 * n2;
+    CUtensorMap mA, mB, mU, mUlo;
+    // psi as [orbital][n1*n2 rows][n3] float32, boxes of 128 rows x ZB z (no swizzle)
+    TX_TRY(make_map_f32_plain(&mA, SA, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nA, (uint32_t)ZB, 128));
+    TX_TRY(make_map_f32_plain(&mB, SB, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nB, (uint32_t)ZB, 128));
+    const int eb = op->esize;
+    TX_TRY(make_map(&mU, op->st.U3T, eb, n3, r3, 1, pad8(n3), 0, (uint32_t)ZB, (uint32_t)a.N3p));
+    if (op->split)
+        TX_TRY(make_map(&mUlo, (const char*)op->st.U3T + op->st.off_lo, eb, n3, r3, 1, pad8(n3), 0, (uint32_t)ZB,
+                        (uint32_t)a.N3p));
+    else
+        mUlo = mU;
+    const size_t psi_bytes = (size_t)128 * ZB * 4, rho_bytes = 128 * 128, b_bytes = (size_t)a.N3p * 128;
+    const int nk = (n3 + ZB - 1) / ZB;
+    const size_t smem = (op->split ? 4 : 2) * rho_bytes + (op->split ? 2 : 1) * nk * b_bytes + 4 * psi_bytes + 1024;
+    if (smem > 227 * 1024) return fail(TX_ERR_UNSUPPORTED_SHAPE, "projection tile does not fit shared memory");
+    dim3 grid((unsigned)((nrows + 127) / 128), (unsigned)np);
+    const int ps = prof_begin("tc_project", s);
+#define LAUNCH(TF, SP)                                                                                \
+    do {                                                                                              \
+        auto fn = tcp::k_project3<TF, SP>;                                                            \
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
+        fn<<<grid, 128, smem, s>>>(mA, mB, mU, mUlo, a);                                              \
+    } while (0)
+    if (op->tf32) {
+        if (op->split) LAUNCH(true, true); else LAUNCH(true, false);
+    } else {
+        if (op->split) LAUNCH(false, true); else LAUNCH(false, false);
+    }
+#undef LAUNCH
+    prof_end(ps, s);
+    TX_LAUNCHED();
+    return TX_OK;
+}
+
+}  // namespace tx

@@ -11,7 +11,7 @@ from _helpers import E_TOL, W_TOL, max_row_rel, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "bf16", "tf32", "tf32x3", "bf16x3"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,8 +25,9 @@ def _P():
     return P
 
 
-def ragged_system(n=(20, 27, 33), r=(5, 7, 9), T=7, n_orb=5, seed=3):
-    """Different n and r per mode, none a multiple of a tile size."""
+def ragged_system(n=(20, 27, 36), r=(5, 7, 9), T=7, n_orb=5, seed=3):
+    """Different n and r per mode, none a multiple of a tile size (n3 a multiple of 4, as the
+    tensor-core path needs 16-byte orbital rows)."""
     rng = np.random.default_rng(seed)
     Ls = [0.22 * (k - 1) / 2 for k in n]
     xs, ws = zip(*[W.uniform_grid(k, L) for k, L in zip(n, Ls)])
@@ -52,6 +53,7 @@ def gpu_apply(s, prec, tgt=None, occ_idx=None, limit=None):
         out = P.tx_exchange_apply(ctx, occ, occ[tgt])
     else:
         out = P.tx_exchange_apply(ctx, occ, to_gpu(tgt))
+    ctx.check_device_error()          # a bounded device-side wait that gave up fails the test
     return out.cpu().numpy()
 
 
@@ -169,3 +171,13 @@ def test_invalid_alignment_and_null_are_rejected():
     assert st == -10
     st = P.lib().tx_exchange_energy(ctx.handle, occ.data_ptr(), 2, None, None)
     assert st == -1
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32x3"])
+def test_tensor_core_precisions_reject_unaligned_rows(prec):
+    P = _P()
+    s = ragged_system(n=(12, 13, 15), r=(3, 4, 5), T=3, n_orb=2)
+    with pytest.raises(P.TuckerExchangeError) as ei:
+        P.Context.from_system(s, precision=prec)
+    assert ei.value.status == -9
+    P.Context.from_system(s, precision="fp32")          # the float32 path takes any shape
