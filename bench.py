@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orbitals", type=int, default=64,
+                    help="use only the first N orbitals of the block (smaller cases for profiling)")
     return ap.parse_args()
 
 
@@ -187,6 +189,8 @@ def main():
     if prec == "auto":
         prec = getattr(P, "DEFAULT_BENCH_PRECISION", "fp32")
     s = W.config_pt()
+    if args.orbitals != s.psi.shape[0]:
+        s.psi = s.psi[: args.orbitals].copy()
     n, r, T = s.n[0], s.r[0], s.T
     N = s.psi.shape[0]
     stream = torch.cuda.current_stream()
@@ -278,7 +282,7 @@ def main():
     # ---- accuracy of this run against the FP64 oracle (sampled target rows), rank 0 only
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and N == 64:
         with tempfile.TemporaryDirectory() as td:
             targets = [0, 37]
             res = run_oracle_sample(targets, os.path.join(td, "w.npy"))
@@ -295,7 +299,8 @@ def main():
         line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms_max, higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype=dtype_name(prec), data="synthetic",
-                    config=dict(WORKLOAD, precision=prec, l2="inputs larger than L2 (psi 226 MB, W 226 MB)",
+                    config=dict(WORKLOAD, orbitals=N, pairs_ordered=N * N, pairs_unique=N * (N + 1) // 2,
+                                precision=prec, l2="inputs larger than L2 (psi 226 MB, W 226 MB)",
                                 parallelism=f"replicas x{world}"),
                     unique_pair_potentials_per_s=world * (N * (N + 1) // 2) / (ms_max / 1000.0),
                     algorithmic_tflops=world * fl / (ms_max / 1000.0) / 1e12,
