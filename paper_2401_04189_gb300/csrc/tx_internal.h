@@ -6,7 +6,7 @@
 
 #include <string>
 
-#include "../../include/tuxc.h"
+#include "tuxc.h"   // the public C ABI (include/ is on the include path)
 
 namespace tx {
 

@@ -205,7 +205,8 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
     // 5. modes 2 and 3 for every term, phi accumulated in TMEM, Hadamard / energy epilogue
     int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
     if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
-    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, flags, b.epart, s));
+    // symmetric pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers
+    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, flags, b.epart, s, subset));
     (void)r1;
     return TX_OK;
 }

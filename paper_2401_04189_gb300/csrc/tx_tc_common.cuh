@@ -89,6 +89,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, uin
         : "memory");
 }
 
+// Asks the memory system to bring a box into L2 ahead of its load (no shared-memory write,
+// no barrier): used to start HBM reads of later Gaussian terms early.
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap* m, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"((uint64_t)m), "r"(c0), "r"(c1),
+                 "r"(c2)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------------------------------
 // TMEM
 // ---------------------------------------------------------------------------------------

@@ -44,6 +44,7 @@ struct ConsumeArgs {
     const float* w2;
     const float* w3;
     int flags;
+    int emul;                  // 1: SA == MUL1 and SB == MUL0 at the same orbital indices (symmetric pairs)
     double* epart;
     int* err;
 };
@@ -68,6 +69,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
     const int NS = a.nstage;
+    // Gaussian terms are accumulated from the largest exponent down (theta ascends with t):
+    // the narrow, local terms contribute least, and adding small terms first limits the
+    // rounding of the tensor core's float32 accumulator
+    auto term_of = [&](int t) { return a.nt - 1 - t; };
 
     // stage layout: [A2 (Z tile)][B2 (A_t2)][B3 (A_t3)][A3 (stage-3 operand)], each hi then lo
     auto A2s = [&](int s) { return smem + s * a.stage_bytes; };
@@ -113,8 +118,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int s = t % NS;
                 if (!mbar_wait(&empty_bar[s], ((t / NS) & 1) ^ 1, a.err, 31)) { ok = false; break; }
                 issued = t + 1;
+                // start the HBM reads of later Z tiles early (into L2 only): terms 1-3 at the
+                // start, then three terms ahead
+                for (int ahead = (t == 0 ? 1 : 3); ahead <= 3; ++ahead)
+                    if (t + ahead < a.nt)
+                        for (int k = 0; k < a.nk2; ++k)
+                            tma_prefetch_l2_3d(&mZ, k * AK, x0 * a.r3, pl * a.nt + term_of(t + ahead));
                 mbar_arrive_expect_tx(&full_bar[s], a.stage_tx);
-                const int zdep = pl * a.nt + t;
+                const int tt = term_of(t);
+                const int zdep = pl * a.nt + tt;
                 for (int k = 0; k < a.nk2; ++k)
                     for (int bb = 0; bb < a.nbox2; ++bb) {
                         const uint32_t off = k * a.nT2 * 16384u + bb * a.box_rows2 * 128u;
@@ -124,14 +136,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         x0 * a.r3 + bb * a.box_rows2, zdep);
                     }
                 for (int k = 0; k < a.nk2; ++k) {
-                    tma_load_3d(B2s(s) + k * a.n2p * 128u, &mA2, &full_bar[s], k * AK, 0, t);
+                    tma_load_3d(B2s(s) + k * a.n2p * 128u, &mA2, &full_bar[s], k * AK, 0, tt);
                     if constexpr (SPLIT)
-                        tma_load_3d(B2s(s) + a.b2_bytes + k * a.n2p * 128u, &mA2lo, &full_bar[s], k * AK, 0, t);
+                        tma_load_3d(B2s(s) + a.b2_bytes + k * a.n2p * 128u, &mA2lo, &full_bar[s], k * AK, 0, tt);
                 }
                 for (int k = 0; k < a.nk3; ++k) {
-                    tma_load_3d(B3s(s) + k * a.n3p * 128u, &mA3, &full_bar[s], k * AK, 0, t);
+                    tma_load_3d(B3s(s) + k * a.n3p * 128u, &mA3, &full_bar[s], k * AK, 0, tt);
                     if constexpr (SPLIT)
-                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 128u, &mA3lo, &full_bar[s], k * AK, 0, t);
+                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 128u, &mA3lo, &full_bar[s], k * AK, 0, tt);
                 }
             }
             if (!ok)
@@ -209,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // r3 even: lanes 2k and 2k+1 hold (x, g) and (x, g+1) of the same x, so after one
             // shuffle each lane stores a packed pair (g, g+1) for every other y
             const bool pack = (a.r3 & 1) == 0;
+            const bool fast = pack && (a.n2 % 16) == 0;
             for (int i = 0; i < a.nT2; ++i) {
                 const int m2 = i * 128 + q * 32 + lane;
                 const bool valid = m2 < a.R2;
@@ -216,6 +229,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int g0 = g & ~1;                       // first column of the packed pair
                 const int atom = g / AK, gin = (g % AK) * ES, gin0 = (g0 % AK) * ES;
                 const bool odd = lane & 1;
+                if (fast) {
+                    // 16-row groups of the stage-3 operand start on multiples of 16 (n2 % 16 == 0),
+                    // so the swizzled offsets of this lane's rows (2k + odd within each 8-row
+                    // group) are fixed: four of them, computed once per tile.
+                    const uint32_t cch = (uint32_t)gin0 >> 4, cin = (uint32_t)gin0 & 15u;
+                    uint32_t xo[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t rw = 2u * k + (odd ? 1u : 0u);
+                        xo[k] = rw * 128u + (((cch ^ rw) & 7u) << 4) + cin;
+                    }
+                    uint8_t* tile_a3 = a3 + atom * a.nT3 * 16384u;
+                    for (int cb = c2lo; cb < c2hi; cb += 64) {
+                        const int nck = min(64, c2hi - cb) / 16;
+                        uint32_t r[4][16];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (c < nck) tmem_ld16(tY + ((uint32_t)(q * 32) << 16) + i * a.n2p + cb + 16 * c, r[c]);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (c >= nck) break;
+                            const int m30 = xl * a.n2 + cb + 16 * c;               // multiple of 16
+                            uint8_t* base = tile_a3 + (m30 >> 7) * 16384u + (m30 & 127) * 128u;
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2) {
+                                const float v0 = __uint_as_float(r[c][j]), v1 = __uint_as_float(r[c][j + 1]);
+                                const float other = __shfl_xor_sync(0xffffffffu, odd ? v0 : v1, 1);
+                                const float lo_g = odd ? other : v0, hi_g = odd ? v1 : other;
+                                uint8_t* dst = base + ((j >> 3) << 10) + xo[(j >> 1) & 3];
+                                if (valid) {
+                                    if constexpr (TF32) {
+                                        const float h0 = tf32_hi(lo_g), h1 = tf32_hi(hi_g);
+                                        *(float2*)dst = make_float2(h0, h1);
+                                        if constexpr (SPLIT)
+                                            *(float2*)(dst + a.a3_bytes) = make_float2(tf32_hi(lo_g - h0), tf32_hi(hi_g - h1));
+                                    } else {
+                                        const __nv_bfloat162 hv = __floats2bfloat162_rn(lo_g, hi_g);
+                                        *(__nv_bfloat162*)dst = hv;
+                                        if constexpr (SPLIT) {
+                                            const float2 hf = __bfloat1622float2(hv);
+                                            *(__nv_bfloat162*)(dst + a.a3_bytes) =
+                                                __floats2bfloat162_rn(lo_g - hf.x, hi_g - hf.y);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    continue;
+                }
                 for (int cb = c2lo; cb < c2hi; cb += 64) {
                     const int nck = min(64, c2hi - cb) / 16;
                     uint32_t r[4][16];
@@ -338,18 +402,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
                         float4 f = phi;
                         if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
-                        if (a.flags & EPI_OUT) {
-                            if (out0) {
-                                const float4 m = *(const float4*)(mul0 + idx);
-                                atomicAdd((float4*)(out0 + idx), make_float4(-m.x * f.x, -m.y * f.y, -m.z * f.z, -m.w * f.w));
-                            }
-                            if (out1) {
-                                const float4 m = *(const float4*)(mul1 + idx);
-                                atomicAdd((float4*)(out1 + idx), make_float4(-m.x * f.x, -m.y * f.y, -m.z * f.z, -m.w * f.w));
-                            }
-                        }
-                        if (a.flags & EPI_ENERGY) {
-                            const float4 va = *(const float4*)(sa + idx), vb = *(const float4*)(sb + idx);
+                        // with symmetric pairs the energy factors (psi_a, psi_b) are the two
+                        // multipliers themselves: each orbital value is read once
+                        const bool en = (a.flags & EPI_ENERGY) != 0;
+                        const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
+                        float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
+                        if (o0 || (en && a.emul)) m0 = *(const float4*)(mul0 + idx);
+                        if (o1 || (en && a.emul)) m1 = *(const float4*)(mul1 + idx);
+                        if (o0) atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+                        if (o1) atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+                        if (en) {
+                            const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
+                            const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
                             e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
                                  (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
                         }
@@ -453,7 +517,7 @@ long tc_consume_blocks(const tx_ctx* c) {
 
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
                const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
-               cudaStream_t s) {
+               cudaStream_t s, bool emul) {
     const TcOperands* op = c->tc;
     ConsumePlan p;
     if (!choose_plan(c, op->tf32, op->split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
@@ -470,6 +534,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     a.SA = SA; a.SB = SB; a.MUL0 = MUL0; a.MUL1 = MUL1; a.OUT0 = OUT0; a.OUT1 = OUT1;
     a.w1 = c->f_w[0]; a.w2 = c->f_w[1]; a.w3 = c->f_w[2];
     a.flags = flags; a.epart = epart; a.err = c->d_err;
+    a.emul = (SA == MUL1 && SB == MUL0 && emul) ? 1 : 0;
     const int eb = op->esize;
     const uint32_t AK = op->tf32 ? 32 : 64;
     // Z of this batch: [pair][t][(x, g) rows][ld_b]; lo part after the batch's hi part

@@ -273,7 +273,7 @@ int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf
     }
     if (g.BN <= 0) {
         g.BN = 16;
-        while (g.BN < g.N && g.BN < 256) g.BN += 16;
+        while (g.BN < g.N && g.BN < 128) g.BN += 16;   // <= 128 keeps several CTAs per SM
     }
     if (g.BN % 16 || g.BN > 256) return fail(TX_ERR_INVALID_ARG, "tc_gemm: BN must be a multiple of 16 <= 256");
     size_t stage = (size_t)(split ? 2 : 1) * (128 * 128 + (size_t)g.BN * 128);
@@ -283,8 +283,10 @@ int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf
         stage = (size_t)(split ? 2 : 1) * (128 * 128 + (size_t)g.BN * 128);
     }
     g.tmem_cols = tmem_cols_for(g.BN);
-    g.stages = (int)std::min<size_t>(tcg::kMaxStages, (budget - 1024) / stage);
-    const size_t smem = stage * g.stages + 1024;
+    const int nk_atoms = (g.K + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64);
+    g.stages = (int)std::min<size_t>({(size_t)tcg::kMaxStages, (budget - 1024) / stage, (size_t)nk_atoms});
+    // the epilogue stages 4 warps x 32 rows x 65 floats in the (then idle) pipeline buffers
+    const size_t smem = std::max(stage * g.stages, (size_t)4 * 32 * 65 * 4) + 1024;
     const int eb = tf32 ? 4 : 2;
     const uint32_t atom_k = 128 / eb;
     CUtensorMap mA, mB, mAlo, mBlo;

@@ -40,7 +40,7 @@ int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const
                      int nB, int flags, void* S1, cudaStream_t s);
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
                const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
-               cudaStream_t s);
+               cudaStream_t s, bool emul = false);
 long tc_consume_blocks(const tx_ctx* c);
 
 }  // namespace tx
