@@ -155,6 +155,52 @@ int tx_exchange_apply_vjp(tx_ctx* ctx, const float* psi_occ, int n_occ,
                           const float* psi_tgt, int n_tgt, const float* grad_out,
                           float* grad_occ, float* grad_tgt, tx_stream_t stream);
 
+/*
+ * Batched application over many independent systems (grids, ranks and term counts may all
+ * differ; no counterpart in the paper, whose MPI task grid distributes pairs of one system).
+ * Each item is one tx_exchange_apply (e_dev NULL) or tx_exchange_apply_energy call (e_dev set,
+ * psi_tgt NULL).  Items that share a context share its workspace and run one after another;
+ * items with different contexts run concurrently on internal streams.
+ */
+typedef struct tx_batch_item {
+    tx_ctx* ctx;
+    const float* psi_occ;
+    int n_occ;
+    const float* psi_tgt;    /* NULL: targets are psi_occ */
+    int n_tgt;
+    float* out;              /* [n_tgt or n_occ][n1][n2][n3] */
+    double* e_dev;           /* optional energy (requires psi_tgt == NULL) */
+} tx_batch_item;
+typedef struct tx_plan tx_plan;
+
+/*
+ * tx_batch_plan -- validates the items, reserves every workspace, and picks the expansion tile
+ * plan of each distinct (n, r, T, precision).  tune_table: path of a text table of tuned plans
+ * (read if it exists; when `autotune` is non-zero, shapes missing from it are timed on the
+ * device with the items' own data and appended).  NULL: built-in heuristic only.  Runs one
+ * untimed launch of every item (so later launches allocate nothing and can be captured).
+ */
+int tx_batch_plan(tx_plan** plan, const tx_batch_item* items, int n_items, const char* tune_table, int autotune,
+                  tx_stream_t stream);
+
+/* Enqueues every item on `stream` (fork / join through internal streams and events). */
+int tx_batch_launch(tx_plan* plan, tx_stream_t stream);
+
+/* Captures one tx_batch_launch into a CUDA graph owned by the plan (replaces any earlier one). */
+int tx_batch_capture(tx_plan* plan, tx_stream_t stream);
+
+/* Replays the captured graph on `stream` (one cudaGraphLaunch). */
+int tx_batch_replay(tx_plan* plan, tx_stream_t stream);
+
+/* Number of items and the expansion tile plan chosen for item i (x planes per CTA, stages). */
+int tx_batch_item_plan(const tx_plan* plan, int i, int* bx, int* nstage);
+
+void tx_plan_destroy(tx_plan* plan);
+
+/* Forces the expansion tile plan of a context (x planes per CTA, pipeline stages); 0, 0 restores
+ * the built-in choice.  Returns TX_ERR_UNSUPPORTED_SHAPE if the plan does not fit. */
+int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
+
 /* Size in bytes of the device workspace the context currently holds. */
 size_t tx_workspace_bytes(const tx_ctx* ctx);
 

@@ -24,8 +24,15 @@ EXPORTED = [
     "tx_exchange_energy_grad", "tx_exchange_apply_vjp", "tx_workspace_bytes", "tx_set_workspace_limit",
     "tx_check_device_error", "tx_status_string", "tx_last_error_message", "tx_launch_count",
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
-    "tx_profile_read", "tx_selftest_gemm",
+    "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
+    "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan",
 ]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("psi_occ", ctypes.c_void_p), ("n_occ", ctypes.c_int),
+                ("psi_tgt", ctypes.c_void_p), ("n_tgt", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("e_dev", ctypes.c_void_p)]
 
 
 class Precision(enum.IntEnum):
@@ -78,6 +85,17 @@ def lib():
     L.tx_profile_reset.restype = None
     L.tx_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
     L.tx_profile_read.restype = _I
+    L.tx_batch_plan.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_BatchItem), _I, ctypes.c_char_p, _I, _P]
+    L.tx_batch_plan.restype = _I
+    for name in ("tx_batch_launch", "tx_batch_capture", "tx_batch_replay"):
+        getattr(L, name).argtypes = [_P, _P]
+        getattr(L, name).restype = _I
+    L.tx_batch_item_plan.argtypes = [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    L.tx_batch_item_plan.restype = _I
+    L.tx_plan_destroy.argtypes = [_P]
+    L.tx_plan_destroy.restype = None
+    L.tx_set_tile_plan.argtypes = [_P, _I, _I]
+    L.tx_set_tile_plan.restype = _I
     L.tx_selftest_gemm.argtypes = [_I, _I, _I, _I, _I, _P, _P, _P, _P]
     L.tx_selftest_gemm.restype = _I
     L.tx_exchange_energy.argtypes = [_P, _P, _I, _P, _P]
@@ -290,6 +308,73 @@ def tx_selftest_gemm(precision, A, B, stream=None):
                                 _ptr(B.contiguous()), _ptr(D), _stream(stream))
     _check(st, "tx_selftest_gemm")
     return D
+
+
+class BatchPlan:
+    """tx_batch_plan over a list of items: dict(ctx=Context, psi_occ=tensor, psi_tgt=None|tensor,
+    out=None|tensor, energy=False).  Outputs (and energies) are allocated here when absent."""
+
+    def __init__(self, items, tune_table=None, autotune=False, stream=None):
+        self.items = []
+        arr = (_BatchItem * len(items))()
+        for k, it in enumerate(items):
+            ctx = it["ctx"]
+            occ = ctx._block(it["psi_occ"], "psi_occ")
+            tgt = it.get("psi_tgt")
+            if tgt is not None:
+                ctx._block(tgt, "psi_tgt")
+            n_tgt = occ.shape[0] if tgt is None else tgt.shape[0]
+            out = it.get("out")
+            if out is None:
+                out = torch.empty((n_tgt, *ctx.n), dtype=torch.float32, device=occ.device)
+            e = torch.empty((), dtype=torch.float64, device=occ.device) if it.get("energy") else None
+            self.items.append(dict(ctx=ctx, psi_occ=occ, psi_tgt=tgt, out=out, e=e))
+            arr[k] = _BatchItem(ctx.handle.value, occ.data_ptr(), occ.shape[0], 0 if tgt is None else tgt.data_ptr(),
+                                0 if tgt is None else n_tgt, out.data_ptr(), 0 if e is None else e.data_ptr())
+        self._arr = arr
+        h = _P()
+        st = lib().tx_batch_plan(ctypes.byref(h), arr, len(items),
+                                 None if tune_table is None else str(tune_table).encode(), 1 if autotune else 0,
+                                 _stream(stream))
+        _check(st, "tx_batch_plan")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().tx_batch_launch(self._h, _stream(stream)), "tx_batch_launch")
+
+    def capture(self, stream):
+        _check(lib().tx_batch_capture(self._h, _stream(stream)), "tx_batch_capture")
+
+    def replay(self, stream=None):
+        _check(lib().tx_batch_replay(self._h, _stream(stream)), "tx_batch_replay")
+
+    def item_plan(self, i):
+        bx, ns = _I(), _I()
+        st = lib().tx_batch_item_plan(self._h, i, ctypes.byref(bx), ctypes.byref(ns))
+        if st < 0:
+            _check(st, "tx_batch_item_plan")
+        return bx.value, ns.value
+
+    def outputs(self):
+        return [it["out"] for it in self.items]
+
+    def energies(self):
+        return [it["e"] for it in self.items]
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tx_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def tx_set_tile_plan(ctx, bx, nstage):
+    _check(lib().tx_set_tile_plan(ctx.handle, int(bx), int(nstage)), "tx_set_tile_plan")
 
 
 def tx_launch_count() -> int:

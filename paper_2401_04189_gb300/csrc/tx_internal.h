@@ -106,6 +106,7 @@ struct tx_ctx {
     double* d_ebatch;    // per-batch energy partial sums
     int ebatch_cap;
     cudaStream_t last_stream;
+    int tile_bx, tile_nstage;   // forced expansion tile plan (0 = built-in choice)
 };
 
 namespace tx {

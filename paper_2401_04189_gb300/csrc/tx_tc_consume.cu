@@ -482,6 +482,7 @@ static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nstage,
 }
 
 static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* best) {
+    if (c->tile_bx > 0 && plan_for(c, tf32, split, c->tile_bx, c->tile_nstage, best)) return true;
     // prefer two stages, then the slab with the least padding per useful row
     double best_score = -1;
     for (int ns = 2; ns >= 1; --ns)
@@ -497,6 +498,39 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
             }
         }
     return best_score > 0;
+}
+
+// every (bx, nstage) that fits, for the autotuner; returns the count written (<= cap)
+int tc_feasible_plans(const tx_ctx* c, int* bx, int* ns, int cap) {
+    const TcOperands* op = c->tc;
+    if (!op) return 0;
+    int k = 0;
+    for (int s = 2; s >= 1; --s)
+        for (int b = 1; b <= 16 && k < cap; ++b) {
+            ConsumePlan p;
+            if (plan_for(c, op->tf32, op->split, b, s, &p)) {
+                bx[k] = b;
+                ns[k] = s;
+                ++k;
+            }
+        }
+    return k;
+}
+
+// the plan the next launch will use
+bool tc_current_plan(const tx_ctx* c, int* bx, int* ns) {
+    const TcOperands* op = c->tc;
+    ConsumePlan p;
+    if (!op || !choose_plan(c, op->tf32, op->split, &p)) return false;
+    *bx = p.bx;
+    *ns = p.nstage;
+    return true;
+}
+
+bool tc_plan_fits(const tx_ctx* c, int bx, int ns) {
+    const TcOperands* op = c->tc;
+    ConsumePlan p;
+    return op && plan_for(c, op->tf32, op->split, bx, ns, &p);
 }
 
 bool tc_consume_supported(const tx_ctx* c, bool tf32, bool split, std::string* why) {

@@ -123,7 +123,7 @@ def test_full_rank_operator(prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_energy_gradient_matches_oracle(prec):
     P = _P()
-    s = ragged_system(n=(14, 16, 18), r=(5, 6, 7), T=5, n_orb=3)
+    s = ragged_system(n=(14, 17, 20), r=(5, 6, 7), T=5, n_orb=3)
     S = O.Setup.from_system(s)
     E_ref, g_ref = O.exchange_energy_grad(s.psi, S)
     ctx = P.Context.from_system(s, precision=prec)
@@ -135,7 +135,7 @@ def test_energy_gradient_matches_oracle(prec):
 @pytest.mark.parametrize("prec", PRECS)
 def test_apply_vjp_matches_oracle(prec):
     P = _P()
-    s = ragged_system(n=(14, 16, 18), r=(5, 6, 7), T=5, n_orb=3)
+    s = ragged_system(n=(14, 17, 20), r=(5, 6, 7), T=5, n_orb=3)
     S = O.Setup.from_system(s)
     rng = np.random.default_rng(4)
     tgt = (s.psi[:2] + 0.1 * s.psi[1:3]).astype(np.float32)
