@@ -201,6 +201,27 @@ void tx_plan_destroy(tx_plan* plan);
  * the built-in choice.  Returns TX_ERR_UNSUPPORTED_SHAPE if the plan does not fit. */
 int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
 
+/*
+ * tx_exchange_apply_static -- out = K psi_occ (targets = the occupied block), like
+ * tx_exchange_apply with psi_tgt NULL, for callers that cannot let a library allocate device
+ * memory: code that gives all device memory to its own arena or pool allocator, or loops that
+ * cannot afford the device-wide synchronisation cudaMalloc / cudaFree may cause.  The paper has
+ * no counterpart; this is an interface of this library.
+ *   - Allocates nothing (no cudaMalloc / cudaFree, no allocating library routine).  All scratch
+ *     (pair table, projection and expansion intermediates) lives in one fixed 32 MiB array in
+ *     the library's device memory, reserved on every device that loads the library until the
+ *     process exits.  Sizes whose scratch for a single pair exceeds it are rejected with
+ *     TX_ERR_UNSUPPORTED_SHAPE and a message giving the bytes needed.
+ *   - Always runs the float32 kernels, whatever the context's precision.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; nothing in it is read before
+ *     the same call writes it.  Calls whose GPU work overlaps (different streams, or different
+ *     host threads on one device) race on the array: order them.
+ *   psi_occ / out: device float32 [n_occ][n1][n2][n3]; out is overwritten.
+ */
+int tx_exchange_apply_static(tx_ctx* ctx, const float* psi_occ, int n_occ, float* out, tx_stream_t stream);
+
 /* Size in bytes of the device workspace the context currently holds. */
 size_t tx_workspace_bytes(const tx_ctx* ctx);
 

@@ -25,7 +25,7 @@ EXPORTED = [
     "tx_check_device_error", "tx_status_string", "tx_last_error_message", "tx_launch_count",
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
-    "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan",
+    "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_exchange_apply_static",
 ]
 
 
@@ -94,6 +94,8 @@ def lib():
     L.tx_batch_item_plan.restype = _I
     L.tx_plan_destroy.argtypes = [_P]
     L.tx_plan_destroy.restype = None
+    L.tx_exchange_apply_static.argtypes = [_P, _P, _I, _P, _P]
+    L.tx_exchange_apply_static.restype = _I
     L.tx_set_tile_plan.argtypes = [_P, _I, _I]
     L.tx_set_tile_plan.restype = _I
     L.tx_selftest_gemm.argtypes = [_I, _I, _I, _I, _I, _P, _P, _P, _P]
