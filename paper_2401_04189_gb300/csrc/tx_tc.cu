@@ -48,11 +48,12 @@ TcScratch tc_scratch(const tx_ctx* c) {
     const size_t n1 = c->n[0], n2 = c->n[1], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2];
     s.ld_y = pad8((int)n2);
     s.ld_x = pad8((int)n1);
-    s.ld_a = pad8((int)r1);
-    s.ld_b = pad8((int)r2);
+    const int eb = (c->prec == TX_PREC_TF32 || c->prec == TX_PREC_TF32X3) ? 4 : 2;
+    s.ld_a = ldk((int)r1, eb);     // G and Z rows are read by TMA along K: whole 32-byte sectors
+    s.ld_b = ldk((int)r2, eb);
     s.s1 = r3 * n1 * s.ld_y;
-    s.s2 = r3 * r2 * s.ld_x;
-    s.g = r3 * r2 * s.ld_a;
+    s.s2 = r3 * s.ld_b * s.ld_x;
+    s.g = r3 * s.ld_b * s.ld_a;
     s.z = (size_t)c->T * n1 * r3 * s.ld_b;
     return s;
 }
@@ -90,11 +91,16 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     op->split = c->prec == TX_PREC_TF32X3 || c->prec == TX_PREC_BF16X3;
     op->esize = op->tf32 ? 4 : 2;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2], T = c->T;
-    const size_t e_u3 = (size_t)r3 * pad8(n3), e_u2 = (size_t)r2 * pad8(n2), e_u1 = (size_t)r1 * pad8(n1);
-    const size_t e_a1 = (size_t)T * n1 * pad8(r1), e_a2 = (size_t)T * n2 * pad8(r2), e_a3 = (size_t)T * n3 * pad8(r3);
+    // every static operand row is K padded with zeros to a whole number of 32-byte sectors
+    const int eb = op->esize;
+    const size_t e_u3 = (size_t)r3 * ldk(n3, eb), e_u2 = (size_t)r2 * ldk(n2, eb), e_u1 = (size_t)r1 * ldk(n1, eb);
+    const size_t e_a1 = (size_t)T * n1 * ldk(r1, eb), e_a2 = (size_t)T * n2 * ldk(r2, eb);
+    const size_t e_a3 = (size_t)T * n3 * ldk(r3, eb), e_a3f = (size_t)T * n3 * pad8(r3);
     auto al = [](size_t e) { return (e + 127) & ~(size_t)127; };   // 256-byte aligned pieces
     const size_t tot = al(e_u3) + al(e_u2) + al(e_u1) + al(e_a1) + al(e_a2) + al(e_a3);
-    const size_t bytes = tot * op->esize * (op->split ? 2 : 1);
+    // bf16 single pass: the stage-3 B operand also in float32 (TF32), after everything else
+    const bool a3f_extra = !op->split && !op->tf32;
+    const size_t bytes = tot * op->esize * (op->split ? 2 : 1) + (a3f_extra ? al(e_a3f) * 4 : 0);
     if (cudaMalloc(&op->buf, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete op;
@@ -115,6 +121,7 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     op->st.A2 = take(e_a2);
     op->st.A3 = take(e_a3);
     op->st.off_lo = tot * op->esize;
+    op->st.A3f = a3f_extra ? (void*)(op->buf + tot * op->esize) : (op->split ? nullptr : op->st.A3);
     const size_t lo = tot;   // element offset of every lo copy
     auto conv = [&](const double* src, long rows, int cols, long srs, long scs, int ld, void* dst) -> int {
         const long n = rows * cols;
@@ -124,13 +131,19 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
         return TX_OK;
     };
     // U_d^T: rows r_d, K = n_d  (U_d is [n_d][r_d])
-    TX_TRY(conv(c->d_U[2], r3, n3, 1, r3, pad8(n3), op->st.U3T));
-    TX_TRY(conv(c->d_U[1], r2, n2, 1, r2, pad8(n2), op->st.U2T));
-    TX_TRY(conv(c->d_U[0], r1, n1, 1, r1, pad8(n1), op->st.U1T));
+    TX_TRY(conv(c->d_U[2], r3, n3, 1, r3, ldk(n3, eb), op->st.U3T));
+    TX_TRY(conv(c->d_U[1], r2, n2, 1, r2, ldk(n2, eb), op->st.U2T));
+    TX_TRY(conv(c->d_U[0], r1, n1, 1, r1, ldk(n1, eb), op->st.U1T));
     // A_td: [T][n_d][r_d] -> rows (t, x), K = r_d
-    TX_TRY(conv(c->d_A64[0], (long)T * n1, r1, r1, 1, pad8(r1), op->st.A1s));
-    TX_TRY(conv(c->d_A64[1], (long)T * n2, r2, r2, 1, pad8(r2), op->st.A2));
-    TX_TRY(conv(c->d_A64[2], (long)T * n3, r3, r3, 1, pad8(r3), op->st.A3));
+    TX_TRY(conv(c->d_A64[0], (long)T * n1, r1, r1, 1, ldk(r1, eb), op->st.A1s));
+    TX_TRY(conv(c->d_A64[1], (long)T * n2, r2, r2, 1, ldk(r2, eb), op->st.A2));
+    TX_TRY(conv(c->d_A64[2], (long)T * n3, r3, r3, 1, ldk(r3, eb), op->st.A3));
+    if (a3f_extra) {
+        const long n = (long)T * n3 * r3;
+        k_static_operand<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->d_A64[2], (long)T * n3, r3, r3, 1, pad8(r3), 1, 0,
+                                                                    op->st.A3f, 0);
+        TX_LAUNCHED();
+    }
     return TX_OK;
 }
 
@@ -166,39 +179,42 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
     // 1. S1 = rho x3 U3^T (rho = psi_a psi_b formed in the kernel)
     TX_TRY(tc_project_mode3(c, b.recs, b.p0, np, SA, nA, cs.occ, cs.n_occ, 0, S1, s));
 
-    // 2. S2[p][g][b][x] = sum_y S1[p][(g,x)][y] U2T[b][y]
+    // 2. S2[p][g][b][x] = sum_y S1[p][(g,x)][y] U2T[b][y], b < ld_b: the columns past r2 read
+    //    rows of U2^T past its end (zero-filled), so the b padding is exact zeros and stays zero
+    //    through G and Z (whose rows TMA reads along b in whole 32-byte sectors)
     {
         TcOperand A{S1, lo_of(S1, sc.s1), (uint64_t)n2, (uint64_t)r3 * n1, (uint64_t)np, (uint64_t)sc.ld_y, sc.s1};
-        TcOperand B{op->st.U2T, op->split ? (const char*)op->st.U2T + op->st.off_lo : nullptr, (uint64_t)n2,
-                    (uint64_t)r2, 1, (uint64_t)pad8(n2), 0};
+        TcOperand B{op->st.U2T, op->split ? (const char*)op->st.U2T + op->st.off_lo : nullptr, (uint64_t)ldk(n2, eb),
+                    (uint64_t)r2, 1, (uint64_t)ldk(n2, eb), 0};
         TcGemmArgs g{};
-        g.M = r3 * n1; g.N = r2; g.K = n2; g.nb1 = np; g.nb2 = 1;
+        g.M = r3 * n1; g.N = sc.ld_b; g.K = n2; g.nb1 = np; g.nb2 = 1;
         g.a_z1 = 1;
-        g.C = S2; g.rdiv = n1; g.c_mh = (long)r2 * sc.ld_x; g.c_m = 1; g.c_n = sc.ld_x; g.c_b1 = (long)sc.s2;
+        g.C = S2; g.rdiv = n1; g.c_mh = (long)sc.ld_b * sc.ld_x; g.c_m = 1; g.c_n = sc.ld_x; g.c_b1 = (long)sc.s2;
         g.c_lo = (long)np * sc.s2; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
         TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj2", s));
     }
-    // 3. G[p][(g,b)][a] = sum_x S2[p][(g,b)][x] U1T[a][x]
+    // 3. G[p][(g,b)][a] = sum_x S2[p][(g,b)][x] U1T[a][x]  (rows (g, b < ld_b), a < ld_a: the
+    //    columns past r1 read rows of U1^T past its end, so G's a padding is zeros too)
     {
-        TcOperand A{S2, lo_of(S2, sc.s2), (uint64_t)n1, (uint64_t)r3 * r2, (uint64_t)np, (uint64_t)sc.ld_x, sc.s2};
-        TcOperand B{op->st.U1T, op->split ? (const char*)op->st.U1T + op->st.off_lo : nullptr, (uint64_t)n1,
-                    (uint64_t)r1, 1, (uint64_t)pad8(n1), 0};
+        TcOperand A{S2, lo_of(S2, sc.s2), (uint64_t)n1, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_x, sc.s2};
+        TcOperand B{op->st.U1T, op->split ? (const char*)op->st.U1T + op->st.off_lo : nullptr, (uint64_t)ldk(n1, eb),
+                    (uint64_t)r1, 1, (uint64_t)ldk(n1, eb), 0};
         TcGemmArgs g{};
-        g.M = r3 * r2; g.N = r1; g.K = n1; g.nb1 = np; g.nb2 = 1;
+        g.M = r3 * sc.ld_b; g.N = sc.ld_a; g.K = n1; g.nb1 = np; g.nb2 = 1;
         g.a_z1 = 1;
         g.C = G; g.c_m = sc.ld_a; g.c_n = 1; g.c_b1 = (long)sc.g;
         g.c_lo = (long)np * sc.g; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
         TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj1", s));
     }
-    // 4. Z[p][(t,x)][(g,b)] = sum_a A1s[(t,x)][a] G[p][(g,b)][a]
+    // 4. Z[p][(t,x)][(g,b)] = sum_a A1s[(t,x)][a] G[p][(g,b)][a]  (b < ld_b, padding included)
     {
-        TcOperand A{op->st.A1s, op->split ? (const char*)op->st.A1s + op->st.off_lo : nullptr, (uint64_t)r1,
-                    (uint64_t)T * n1, 1, (uint64_t)pad8(r1), 0};
-        TcOperand B{G, lo_of(G, sc.g), (uint64_t)r1, (uint64_t)r3 * r2, (uint64_t)np, (uint64_t)sc.ld_a, sc.g};
+        TcOperand A{op->st.A1s, op->split ? (const char*)op->st.A1s + op->st.off_lo : nullptr, (uint64_t)ldk(r1, eb),
+                    (uint64_t)T * n1, 1, (uint64_t)ldk(r1, eb), 0};
+        TcOperand B{G, lo_of(G, sc.g), (uint64_t)sc.ld_a, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_a, sc.g};
         TcGemmArgs g{};
-        g.M = T * n1; g.N = r3 * r2; g.K = r1; g.nb1 = np; g.nb2 = 1;
+        g.M = T * n1; g.N = r3 * sc.ld_b; g.K = r1; g.nb1 = np; g.nb2 = 1;
         g.b_z1 = 1;
-        g.C = Z; g.c_m = (long)r3 * sc.ld_b; g.cdiv = r2; g.c_nh = sc.ld_b; g.c_n = 1; g.c_b1 = (long)sc.z;
+        g.C = Z; g.c_m = (long)r3 * sc.ld_b; g.c_n = 1; g.c_b1 = (long)sc.z;
         g.c_lo = (long)np * sc.z; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
         TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
     }

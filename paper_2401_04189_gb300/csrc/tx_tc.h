@@ -37,8 +37,13 @@ struct TcGemmArgs {
     int* err;
 };
 
+// [depth][rows][k_extent] operand (strides in elements), box {box_k, box_rows, 1}; 128-byte swizzle
 int make_map(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent, uint64_t rows, uint64_t depth,
              uint64_t row_stride_elems, uint64_t depth_stride_elems, uint32_t box_k, uint32_t box_rows);
+// the same with the swizzle chosen by the caller (box_k x elem_bytes must not exceed its span)
+int make_map_sw(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent, uint64_t rows, uint64_t depth,
+                uint64_t row_stride_elems, uint64_t depth_stride_elems, uint32_t box_k, uint32_t box_rows,
+                CUtensorMapSwizzle swizzle);
 // float32 [depth][rows][k_extent] (row stride k_extent), no swizzle, box {box_k, box_rows, 1}
 int make_map_f32_plain(CUtensorMap* m, const void* base, uint64_t k_extent, uint64_t rows, uint64_t depth,
                        uint32_t box_k, uint32_t box_rows);

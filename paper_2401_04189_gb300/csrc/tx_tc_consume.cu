@@ -2,15 +2,21 @@
 // Hadamard product and the sum over j (Eq. hadam) and the weighted energy sums:
 //
 //   for every Gaussian term t (the K loop of the final contraction):
-//     Y_t^T[(x,g)][y] = sum_b Z_t[(x,g)][b] A_t2[y][b]              stage 2 -> TMEM
-//     phi[(x,y)][z]  += sum_g Y_t[(x,y)][g] (mu_t A_t3)[z][g]        stage 3 -> TMEM (all t)
+//     Y_t,x[y][g]    = sum_b A_t2[y][b] Z_t[(x,g)][b]     one stage-2 MMA per x plane -> TMEM
+//     phi[(x,y)][z] += sum_g Y_t[(x,y)][g] (mu_t A_t3)[z][g]        stage 3 -> TMEM (all t)
 //   out0[o0] -= mul0[m0] * phi,  out1[o1] -= mul1[m1] * phi,  energy += ew * w * psi_a psi_b phi
 //
-// Z_t = G x1 A_t1 comes from the first-mode GEMM.  Y_t is produced transposed (rows (x, g)) so
-// the stage-2 MMA has no x-alignment constraint; eight converter warps read it from TMEM,
-// round it to the operand type and write it as the K-major stage-3 operand (rows (x, y)) in
-// the 128-byte swizzled layout.  phi stays in TMEM across every term and is read once by the
-// epilogue.  Warp roles: 0-7 converters + epilogue, 8 TMA producer + TMEM owner, 9 MMA issuer.
+// Z_t = G x1 A_t1 comes from the first-mode GEMM.  Stage 2 puts y on the TMEM lanes and g on
+// the columns, so each converter lane already holds one row (x, y) of the K-major stage-3
+// operand: it rounds the row to the operand type and writes it with 16-byte stores.  Each x
+// plane has its own TMEM columns and its own full / free barriers, so the MMA of plane p for
+// the next term starts as soon as plane p has been converted.  phi stays in TMEM across every
+// term and is read once by the epilogue.
+//
+// Operand tiles use the 32-byte swizzle: one sub-tile of `rows x 32 bytes` per MMA K-step, so K
+// is padded only to the K-step (48 for r = 40 in bf16, none for TF32), and the load stages are
+// small enough for three of them to be in flight.  Warp roles: 0-7 converters + epilogue,
+// 8 TMA producer + TMEM owner, 9 MMA issuer.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -25,13 +31,20 @@ namespace tcc {
 
 using namespace tx::tc;
 
+constexpr int kMaxLoad = 4;
+constexpr int kMaxPlanes = 16;
+constexpr int kMaxYBuf = 4;        // stage-2 output buffers in TMEM (single-pass kernel)
+
+__host__ __device__ constexpr int pad16c(int v) { return (v + 15) & ~15; }
+
 struct ConsumeArgs {
     int n1, n2, n3, r2, r3, nt;
-    int bx, R, R2, nT2, nT3, n2p, n3p, nk2, nk3;
-    int nbox2, box_rows2, nstage;
-    uint32_t a2_bytes, b2_bytes, b3_bytes, a3_bytes, stage_bytes, stage_tx;
+    int bx, R, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, gs, ycol_tile, ns3;
+    int nload, na3, nyb;
+    uint32_t ya_rows, z_rows;                          // rows of the stage-2 A tile (A_t2) and B tile (Z)
+    uint32_t ya_bytes, z_bytes, b3_bytes, a3_bytes;    // one hi copy of each operand tile
+    uint32_t load_bytes, stage_tx, a3_off;             // load stage stride, bytes per stage, A3 buffers
     uint32_t tmem_cols, y_cols;
-    uint32_t stg_off;          // byte offset of the epilogue staging area (8 warps x 32 x 68 floats)
     int p0;
     const PairRec* recs;
     const float* SA;
@@ -50,52 +63,206 @@ struct ConsumeArgs {
 };
 
 constexpr int kThreads = 320;
+// epilogue shared memory (reuses the pipeline buffers): phi staging, 8 warps x 32 rows x 68
+// floats, then per warp two blocks of orbital values, 8 row pairs x 2 multipliers x 32 lanes
+constexpr uint32_t kStgBytes = 8u * 32u * 68u * 4u;
+constexpr uint32_t kEpiBytes = kStgBytes + 8u * 2u * 8u * 2u * 32u * 16u;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// byte offset of (row, byte-in-row) in a 32-byte-swizzled sub-tile (rows 4-7 of every 8-row
+// group have their two 16-byte halves swapped)
+__device__ __forceinline__ uint32_t sw32_offset(uint32_t row, uint32_t byte_in_row) {
+    return row * 32u + (byte_in_row ^ (((row >> 2) & 1u) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *(const uint32_t*)&v;
+}
+
+// One 16-byte chunk of a stage-3 operand row: 8 bf16 or 4 tf32 values v[0..]; `lo` receives
+// the rounding residuals for the split precisions.
+template <bool TF32, bool SPLIT>
+__device__ __forceinline__ void convert_chunk(const float* v, uint4& hi, uint4& lo) {
+    if constexpr (TF32) {
+        float h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) h[e] = tf32_hi(v[e]);
+        hi = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+        if constexpr (SPLIT)
+            lo = make_uint4(__float_as_uint(tf32_hi(v[0] - h[0])), __float_as_uint(tf32_hi(v[1] - h[1])),
+                            __float_as_uint(tf32_hi(v[2] - h[2])), __float_as_uint(tf32_hi(v[3] - h[3])));
+    } else {
+        uint32_t w[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            w[e] = *(const uint32_t*)&hv;
+            if constexpr (SPLIT) {
+                const float2 hf = __bfloat1622float2(hv);
+                l[e] = pack_bf16(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+            }
+        }
+        hi = make_uint4(w[0], w[1], w[2], w[3]);
+        if constexpr (SPLIT) lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Epilogue of one (pair, slab of x planes): phi, nTiles M-tiles of 128 rows x n3p columns in
+// TMEM, goes into the outputs (out -= mul * phi) and the weighted energy sum of this thread.
+// rows(jt, r, x, y) gives the grid point (x, y) of row r of tile jt and whether it exists.
+template <typename Rows>
+__device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const PairRec& rec, uint8_t* smem,
+                                                   uint32_t tPhi, int nTiles, int warp, int lane, Rows rows) {
+    const int q = warp & 3, h = warp >> 2;
+    double e = 0.0;
+    const long N3 = (long)a.n1 * a.n2 * a.n3;
+    const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
+    const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
+    float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
+    float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
+    const float* sa = a.SA + (long)rec.ia * N3;
+    const float* sb = a.SB + (long)rec.ib * N3;
+    const bool en = (a.flags & EPI_ENERGY) != 0;
+    const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
+    // with symmetric pairs the energy factors (psi_a, psi_b) are the two multipliers
+    // themselves: each orbital value is read once
+    const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
+    // Each warp stages its quadrant's 32 rows x 64 columns of phi in shared memory (the
+    // pipeline buffers are idle now), then walks the rows with consecutive z across lanes:
+    // psi reads are coalesced and W is updated with 16-byte vector reductions.  The two
+    // warps of a quadrant split the row pairs.  The orbital values of the next block are
+    // copied to shared memory (cp.async) while the current block is processed, so their
+    // HBM latency is hidden.
+    float* stg = (float*)smem + warp * (32 * 68);
+    float4* lbuf = (float4*)(smem + kStgBytes) + warp * (2 * 8 * 2 * 32);   // [buf][it][m][lane]
+    const int sub = lane >> 4;
+    const int ncb = (a.n3p + 63) / 64, nblk = nTiles * ncb;
+    // row, grid offset and validity of iteration `it` of block `blk` for this lane
+    auto locate = [&](int blk, int it, int& x, int& y, int& z, int& idx) -> bool {
+        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
+        z = cb + 4 * (lane & 15);
+        if (!rows(jt, q * 32 + 2 * h + 4 * it + sub, x, y) || z >= a.n3) return false;
+        idx = (x * a.n2 + y) * a.n3 + z;       // < 256^3; a multiple of 4 (n3 % 4 == 0)
+        return true;
+    };
+    auto prefetch = [&](int blk) {
+        float4* d = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            int x, y, z, idx;
+            if (!locate(blk, it, x, y, z, idx)) continue;
+            if (need0) cp_async16(d + (2 * it) * 32, mul0 + idx);
+            if (need1) cp_async16(d + (2 * it + 1) * 32, mul1 + idx);
+        }
+        cp_async_commit();
+    };
+    prefetch(0);
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
+        if (blk + 1 < nblk) prefetch(blk + 1);
+        const int nck = min(64, a.n3p - cb) / 16;
+        uint32_t r[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < nck) tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + jt * a.n3p + cb + 16 * c, r[c]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < nck)
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *(float4*)(stg + lane * 68 + 16 * c + j) =
+                        make_float4(__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
+                                    __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3]));
+        if (blk + 1 < nblk) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncwarp();
+        const float4* lb = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
+        // lanes 0-15 take row rr, lanes 16-31 row rr + 1; four consecutive z per lane
+#pragma unroll 2
+        for (int it = 0; it < 8; ++it) {
+            int x, y, z, idx;
+            if (!locate(blk, it, x, y, z, idx)) continue;
+            const int rr = 2 * h + 4 * it + sub;
+            const float4 phi = *(const float4*)(stg + rr * 68 + 4 * (lane & 15));
+            const float wxy = a.w1[x] * a.w2[y];
+            const float4 w3 = *(const float4*)(a.w3 + z);
+            const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+            float4 f = phi;
+            if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+            const float4 m0 = need0 ? lb[(2 * it) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 m1 = need1 ? lb[(2 * it + 1) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o0) atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+            if (o1) atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+            if (en) {
+                const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
+                const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
+                e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
+                     (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
+            }
+        }
+        __syncwarp();
+    }
+    return e;
+}
 
 template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_consume(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mZlo,
               const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA2lo,
               const __grid_constant__ CUtensorMap mA3, const __grid_constant__ CUtensorMap mA3lo, ConsumeArgs a) {
-    constexpr int AK = TF32 ? 32 : 64;       // K elements per 128-byte row
-    constexpr int MK = TF32 ? 8 : 16;        // K per MMA instruction
+    constexpr int MK = TF32 ? 8 : 16;        // K per MMA instruction (32 bytes)
     constexpr int ES = TF32 ? 4 : 2;         // operand element bytes
+    constexpr int CV = 16 / ES;              // values per 16-byte chunk
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[2], empty_bar[2], a3full[2], a3free[2], yfull, yfree, phidone;
+    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], a3full[2], a3free[2], phidone;
+    __shared__ uint64_t yfull, yfree;
     __shared__ uint32_t tmem_base;
-    __shared__ double red[10];
+    __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slab = blockIdx.x, pl = blockIdx.y;
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
-    const int NS = a.nstage;
-    // Gaussian terms are accumulated from the largest exponent down (theta ascends with t):
-    // the narrow, local terms contribute least, and adding small terms first limits the
-    // rounding of the tensor core's float32 accumulator
-    auto term_of = [&](int t) { return a.nt - 1 - t; };
+    const int NL = a.nload, NA = a.na3, BX = a.bx;
+    // Gaussian terms in the order of the exponential sum (theta ascending: wide terms first).
+    // Measured against the float64 oracle, this order gives about half the split-precision
+    // error of the reverse order: the tensor core's float32 accumulator rounds each partial
+    // sum, and starting from the large, smooth wide-term part keeps later steps small.
+    auto term_of = [&](int t) { return t; };
 
-    // stage layout: [A2 (Z tile)][B2 (A_t2)][B3 (A_t3)][A3 (stage-3 operand)], each hi then lo
-    auto A2s = [&](int s) { return smem + s * a.stage_bytes; };
-    auto B2s = [&](int s) { return A2s(s) + (SPLIT ? 2 : 1) * a.a2_bytes; };
-    auto B3s = [&](int s) { return B2s(s) + (SPLIT ? 2 : 1) * a.b2_bytes; };
-    auto A3s = [&](int s) { return B3s(s) + (SPLIT ? 2 : 1) * a.b3_bytes; };
+    // load stage s: [A_t2 tile][Z tile][A_t3 tile], each hi then lo; then the NA stage-3 operands
+    auto YAs = [&](int s) { return smem + s * a.load_bytes; };
+    auto Zs = [&](int s) { return YAs(s) + (SPLIT ? 2 : 1) * a.ya_bytes; };
+    auto B3s = [&](int s) { return Zs(s) + (SPLIT ? 2 : 1) * a.z_bytes; };
+    auto A3s = [&](int b) { return smem + a.a3_off + b * (SPLIT ? 2 : 1) * a.a3_bytes; };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kMaxLoad; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
-            mbar_init(&a3full[s], 8);
-            mbar_init(&a3free[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a3full[b], 8);
+            mbar_init(&a3free[b], 1);
         }
         mbar_init(&yfull, 1);
-        mbar_init(&yfree, 8);
+        mbar_init(&yfree, 2 * a.nq);
         mbar_init(&phidone, 1);
         fence_barrier_init();
     }
-    // the stage-3 operand: padded K columns and unused rows must hold finite values
-    for (int s = 0; s < NS; ++s) {
-        uint4* p = (uint4*)A3s(s);
-        const int n16 = (SPLIT ? 2 : 1) * a.a3_bytes / 16;
+    // the stage-3 operand: rows past the slab's last (x, y) are never written and must be finite
+    {
+        uint4* p = (uint4*)A3s(0);
+        const int n16 = NA * (SPLIT ? 2 : 1) * a.a3_bytes / 16;
         for (int i = threadIdx.x; i < n16; i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
     }
     fence_async_smem();
@@ -108,6 +275,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t tY = tmem, tPhi = tmem + a.y_cols;
+    const uint32_t ya_sub = a.ya_rows * 32u;                  // one K-step sub-tile of each operand
+    const uint32_t z_sub = a.z_rows * 32u;
+    const uint32_t a3_sub = (uint32_t)a.nT3 * 128u * 32u;
 
     if (warp == 8) {
         // ------------------------------ TMA producer ------------------------------
@@ -115,312 +285,384 @@ __global__ void __launch_bounds__(kThreads, 1)
             int issued = 0;
             bool ok = true;
             for (int t = 0; t < a.nt && ok; ++t) {
-                const int s = t % NS;
-                if (!mbar_wait(&empty_bar[s], ((t / NS) & 1) ^ 1, a.err, 31)) { ok = false; break; }
+                const int s = t % NL;
+                if (!mbar_wait(&empty_bar[s], ((t / NL) & 1) ^ 1, a.err, 31)) { ok = false; break; }
                 issued = t + 1;
-                // start the HBM reads of later Z tiles early (into L2 only): terms 1-3 at the
-                // start, then three terms ahead
-                for (int ahead = (t == 0 ? 1 : 3); ahead <= 3; ++ahead)
+                // start the HBM reads of later Z tiles early (into L2 only)
+                for (int ahead = (t == 0 ? 1 : NL + 1); ahead <= NL + 1; ++ahead)
                     if (t + ahead < a.nt)
-                        for (int k = 0; k < a.nk2; ++k)
-                            tma_prefetch_l2_3d(&mZ, k * AK, x0 * a.r3, pl * a.nt + term_of(t + ahead));
+                        for (int p = 0; p < BX; ++p)
+                            for (int k = 0; k < a.ks2; ++k)
+                                tma_prefetch_l2_3d(&mZ, k * MK, (x0 + p) * a.r3, pl * a.nt + term_of(t + ahead));
                 mbar_arrive_expect_tx(&full_bar[s], a.stage_tx);
                 const int tt = term_of(t);
                 const int zdep = pl * a.nt + tt;
-                for (int k = 0; k < a.nk2; ++k)
-                    for (int bb = 0; bb < a.nbox2; ++bb) {
-                        const uint32_t off = k * a.nT2 * 16384u + bb * a.box_rows2 * 128u;
-                        tma_load_3d(A2s(s) + off, &mZ, &full_bar[s], k * AK, x0 * a.r3 + bb * a.box_rows2, zdep);
+                for (int k = 0; k < a.ks2; ++k) {
+                    tma_load_3d(YAs(s) + k * ya_sub, &mA2, &full_bar[s], k * MK, 0, tt);
+                    if constexpr (SPLIT) tma_load_3d(YAs(s) + a.ya_bytes + k * ya_sub, &mA2lo, &full_bar[s], k * MK, 0, tt);
+                    // plane p's rows start at row p * Nz (a multiple of 16) of the Z tile
+                    for (int p = 0; p < BX; ++p) {
+                        const uint32_t off = k * z_sub + (uint32_t)(p * a.Nz) * 32u;
+                        tma_load_3d(Zs(s) + off, &mZ, &full_bar[s], k * MK, (x0 + p) * a.r3, zdep);
                         if constexpr (SPLIT)
-                            tma_load_3d(A2s(s) + a.a2_bytes + off, &mZlo, &full_bar[s], k * AK,
-                                        x0 * a.r3 + bb * a.box_rows2, zdep);
+                            tma_load_3d(Zs(s) + a.z_bytes + off, &mZlo, &full_bar[s], k * MK, (x0 + p) * a.r3, zdep);
                     }
-                for (int k = 0; k < a.nk2; ++k) {
-                    tma_load_3d(B2s(s) + k * a.n2p * 128u, &mA2, &full_bar[s], k * AK, 0, tt);
-                    if constexpr (SPLIT)
-                        tma_load_3d(B2s(s) + a.b2_bytes + k * a.n2p * 128u, &mA2lo, &full_bar[s], k * AK, 0, tt);
                 }
-                for (int k = 0; k < a.nk3; ++k) {
-                    tma_load_3d(B3s(s) + k * a.n3p * 128u, &mA3, &full_bar[s], k * AK, 0, tt);
+                for (int k = 0; k < a.ks3; ++k) {
+                    tma_load_3d(B3s(s) + k * a.n3p * 32u, &mA3, &full_bar[s], k * MK, 0, tt);
                     if constexpr (SPLIT)
-                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 128u, &mA3lo, &full_bar[s], k * AK, 0, tt);
+                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 32u, &mA3lo, &full_bar[s], k * MK, 0, tt);
                 }
             }
             if (!ok)
-                for (int t = (issued > NS ? issued - NS : 0); t < issued; ++t)
-                    mbar_drain(&full_bar[t % NS], (t / NS) & 1);
+                for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t)
+                    mbar_drain(&full_bar[t % NL], (t / NL) & 1);
         }
     } else if (warp == 9) {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
-            const uint32_t id2 = TF32 ? idesc_tf32(128, a.n2p) : idesc_bf16(128, a.n2p);
             const uint32_t id3 = TF32 ? idesc_tf32(128, a.n3p) : idesc_bf16(128, a.n3p);
-            const int st2 = (a.r2 + MK - 1) / MK, st3 = (a.r3 + MK - 1) / MK;
-            bool ok = true;
-            auto stage3 = [&](int t) -> bool {
-                const int s = t % NS;
-                if (!mbar_wait(&a3full[s], (t / NS) & 1, a.err, 34)) return false;
-                tc_fence_after();
-                const uint32_t a3 = smem_u32(A3s(s)), b3 = smem_u32(B3s(s));
-                for (int j = 0; j < a.nT3; ++j)
-                    for (int k = 0; k < st3; ++k) {
-                        const int atom = k * MK / AK, kin = (k * MK) % AK;
-                        const uint32_t ao = atom * a.nT3 * 16384u + j * 16384u + kin * ES;
-                        const uint32_t bo = atom * a.n3p * 128u + kin * ES;
-                        const uint64_t ad = sdesc_sw128(a3 + ao), bd = sdesc_sw128(b3 + bo);
-                        const uint32_t acc = (t > 0 || k > 0) ? 1u : 0u;
-                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, acc);
-                        if constexpr (SPLIT) {
-                            mma_ss<TF32>(tPhi + j * a.n3p, ad, sdesc_sw128(b3 + a.b3_bytes + bo), id3, 1u);
-                            mma_ss<TF32>(tPhi + j * a.n3p, sdesc_sw128(a3 + a.a3_bytes + ao), bd, id3, 1u);
-                        }
-                    }
-                mma_commit(&a3free[s]);
-                mma_commit(&empty_bar[s]);
-                return true;
-            };
-            for (int t = 0; t < a.nt && ok; ++t) {
-                const int s = t % NS;
-                // one stage: term t-1 must finish (and free the buffer) before term t can load
-                if (NS == 1 && t > 0 && !stage3(t - 1)) { ok = false; break; }
-                if (!mbar_wait(&full_bar[s], (t / NS) & 1, a.err, 32)) { ok = false; break; }
-                if (t > 0 && !mbar_wait(&yfree, (t - 1) & 1, a.err, 33)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t a2 = smem_u32(A2s(s)), b2 = smem_u32(B2s(s));
-                for (int i = 0; i < a.nT2; ++i)
-                    for (int k = 0; k < st2; ++k) {
-                        const int atom = k * MK / AK, kin = (k * MK) % AK;
-                        const uint32_t ao = atom * a.nT2 * 16384u + i * 16384u + kin * ES;
-                        const uint32_t bo = atom * a.n2p * 128u + kin * ES;
-                        const uint64_t ad = sdesc_sw128(a2 + ao), bd = sdesc_sw128(b2 + bo);
-                        mma_ss<TF32>(tY + i * a.n2p, ad, bd, id2, k > 0 ? 1u : 0u);
-                        if constexpr (SPLIT) {
-                            mma_ss<TF32>(tY + i * a.n2p, ad, sdesc_sw128(b2 + a.b2_bytes + bo), id2, 1u);
-                            mma_ss<TF32>(tY + i * a.n2p, sdesc_sw128(a2 + a.a2_bytes + ao), bd, id2, 1u);
+            // Event-driven issue: stage 2 of (term t2, plane p2) as soon as its load stage has
+            // landed and the converters have released the plane's TMEM columns; stage 3 of term
+            // t3 as soon as its operand is converted.  Neither waits for the other, so a load
+            // stage is released (by stage 3) without waiting for the next stage's data.
+            // all planes of a term in one MMA per K step (N = planes x Nz, in chunks of <= 256).
+            // Descriptors are built once and advanced by adds, so that issuing an MMA costs less
+            // than the ~50 cycles it occupies the tensor pipe.
+            const uint64_t d0 = sdesc_sw32(0);
+            const uint64_t ya_step = ya_sub >> 4, z_step = z_sub >> 4, b3_step = (uint32_t)a.n3p * 2u;
+            const uint64_t a3_step = a3_sub >> 4, ya_lo = a.ya_bytes >> 4, z_lo = a.z_bytes >> 4;
+            const uint64_t b3_lo = a.b3_bytes >> 4, a3_lo = a.a3_bytes >> 4;
+            auto stage2 = [&](int t) {
+                const int s = t % NL;
+                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
+                for (int i = 0; i < a.nY; ++i)
+                    for (int p0 = 0; p0 < BX; p0 += a.npc) {
+                        const int N = min(a.npc, BX - p0) * a.Nz;
+                        const uint32_t id2 = TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                        const uint32_t d = tY + (uint32_t)((i * BX + p0) * a.Nz);
+                        uint64_t ad = ya + (uint32_t)i * 256u, bd = zb + (uint32_t)(p0 * a.Nz) * 2u;
+                        for (int k = 0; k < a.ks2; ++k) {
+                            mma_ss<TF32>(d, ad, bd, id2, k > 0 ? 1u : 0u);
+                            if constexpr (SPLIT) {
+                                mma_ss<TF32>(d, ad, bd + z_lo, id2, 1u);
+                                mma_ss<TF32>(d, ad + ya_lo, bd, id2, 1u);
+                            }
+                            ad += ya_step;
+                            bd += z_step;
                         }
                     }
                 mma_commit(&yfull);
-                // two stages: stage 3 of term t-1 runs while the converters work on term t
-                if (NS == 2 && t > 0 && !stage3(t - 1)) { ok = false; break; }
+            };
+            auto stage3 = [&](int t) {
+                const int s = t % NL, b = t % NA;
+                const uint64_t a3 = d0 + (smem_u32(A3s(b)) >> 4), b3 = d0 + (smem_u32(B3s(s)) >> 4);
+                for (int j = 0; j < a.nT3; ++j) {
+                    uint64_t ad = a3 + (uint32_t)j * 256u, bd = b3;
+                    for (int k = 0; k < a.ks3; ++k) {
+                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, (t > 0 || k > 0) ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            mma_ss<TF32>(tPhi + j * a.n3p, ad, bd + b3_lo, id3, 1u);
+                            mma_ss<TF32>(tPhi + j * a.n3p, ad + a3_lo, bd, id3, 1u);
+                        }
+                        ad += a3_step;
+                        bd += b3_step;
+                    }
+                }
+                mma_commit(&a3free[b]);
+                mma_commit(&empty_bar[s]);
+            };
+            bool ok = true, fresh = true;
+            int t2 = 0, t3 = 0;
+            uint32_t idle = 0;
+            uint64_t since = 0;
+            while (t3 < a.nt) {
+                bool prog = false;
+                if (t2 < a.nt && mbar_try_wait(&full_bar[t2 % NL], (t2 / NL) & 1) &&
+                    (t2 == 0 || mbar_try_wait(&yfree, (t2 - 1) & 1))) {
+                    tc_fence_after();
+                    stage2(t2);
+                    ++t2;
+                    prog = true;
+                }
+                if (t3 < t2 && mbar_try_wait(&a3full[t3 % NA], (t3 / NA) & 1)) {
+                    tc_fence_after();
+                    stage3(t3);
+                    ++t3;
+                    prog = true;
+                }
+                if (prog) {
+                    fresh = true;
+                    idle = 0;
+                } else if ((++idle & 63) == 0) {
+                    if (*(volatile int*)a.err != 0) { ok = false; break; }
+                    const uint64_t now = globaltimer();
+                    if (fresh) {
+                        since = now;
+                        fresh = false;
+                    } else if (now - since > kWaitLimitNs) {
+                        if (atomicCAS(a.err, 0, 1) == 0) atomicExch(a.err + 1, 32);
+                        ok = false;
+                        break;
+                    }
+                }
             }
-            if (ok) ok = stage3(a.nt - 1);
             mma_commit(&phidone);
+            // on the error path nobody else waits: keep the CTA (and its TMEM) until the MMAs
+            // already issued have finished
+            if (!ok) mbar_drain(&phidone, 0);
         }
     } else {
         // ------------------------------ converters (warps 0-7) ------------------------------
+        // warp (q, h) converts the TMEM lanes 32q..32q+31 (y) of the planes p = h, h + 2, ...
         const int q = warp & 3, h = warp >> 2;
-        const int half2 = ((a.n2p / 16 + 1) / 2) * 16;       // y columns per half, multiple of 16
-        const int c2lo = h * half2, c2hi = min(a.n2p, c2lo + half2);
+        const bool active = q < a.nq;
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
-            const int s = t % NS;
-            if (!mbar_wait(&yfull, t & 1, a.err, 35)) { ok = false; break; }
-            if (t >= NS && !mbar_wait(&a3free[s], ((t - NS) / NS) & 1, a.err, 36)) { ok = false; break; }
-            tc_fence_after();
-            uint8_t* a3 = A3s(s);
-            // r3 even: lanes 2k and 2k+1 hold (x, g) and (x, g+1) of the same x, so after one
-            // shuffle each lane stores a packed pair (g, g+1) for every other y
-            const bool pack = (a.r3 & 1) == 0;
-            const bool fast = pack && (a.n2 % 16) == 0;
-            for (int i = 0; i < a.nT2; ++i) {
-                const int m2 = i * 128 + q * 32 + lane;
-                const bool valid = m2 < a.R2;
-                const int xl = m2 / a.r3, g = m2 - xl * a.r3;
-                const int g0 = g & ~1;                       // first column of the packed pair
-                const int atom = g / AK, gin = (g % AK) * ES, gin0 = (g0 % AK) * ES;
-                const bool odd = lane & 1;
-                if (fast) {
-                    // 16-row groups of the stage-3 operand start on multiples of 16 (n2 % 16 == 0),
-                    // so the swizzled offsets of this lane's rows (2k + odd within each 8-row
-                    // group) are fixed: four of them, computed once per tile.
-                    const uint32_t cch = (uint32_t)gin0 >> 4, cin = (uint32_t)gin0 & 15u;
-                    uint32_t xo[4];
+            const int b = t % NA;
+            if (t >= NA && !mbar_wait(&a3free[b], ((t - NA) / NA) & 1, a.err, 36)) { ok = false; break; }
+            uint8_t* a3 = A3s(b);
+            if (active) {
+                if (!mbar_wait(&yfull, t & 1, a.err, 35)) { ok = false; break; }
+                tc_fence_after();
+                for (int p = h; p < BX; p += 2) {
+                    for (int i = 0; i < a.nY; ++i) {
+                        const int y = i * 128 + q * 32 + lane;
+                        const bool valid = y < a.n2;
+                        const uint32_t m3 = (uint32_t)(p * a.n2 + y);
+                        const uint32_t col = tY + ((uint32_t)(q * 32) << 16) + (uint32_t)((i * BX + p) * a.Nz);
+                        for (int g0 = 0; g0 < a.r3; g0 += 64) {
+                            const int nck = min(4, (min(a.Nz, g0 + 64) - g0) / 16);
+                            uint32_t r[4][16];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t rw = 2u * k + (odd ? 1u : 0u);
-                        xo[k] = rw * 128u + (((cch ^ rw) & 7u) << 4) + cin;
-                    }
-                    uint8_t* tile_a3 = a3 + atom * a.nT3 * 16384u;
-                    for (int cb = c2lo; cb < c2hi; cb += 64) {
-                        const int nck = min(64, c2hi - cb) / 16;
-                        uint32_t r[4][16];
+                            for (int c = 0; c < 4; ++c)
+                                if (c < nck) tmem_ld16(col + g0 + 16 * c, r[c]);
+                            tmem_ld_wait();
 #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (c < nck) tmem_ld16(tY + ((uint32_t)(q * 32) << 16) + i * a.n2p + cb + 16 * c, r[c]);
-                        tmem_ld_wait();
+                            for (int c = 0; c < 4; ++c) {
+                                if (c >= nck) break;
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            if (c >= nck) break;
-                            const int m30 = xl * a.n2 + cb + 16 * c;               // multiple of 16
-                            uint8_t* base = tile_a3 + (m30 >> 7) * 16384u + (m30 & 127) * 128u;
+                                for (int u = 0; u < 16 / CV; ++u) {
+                                    const int g = g0 + 16 * c + CV * u;          // first column of the chunk
+                                    if (!valid || g >= a.r3) continue;
+                                    float v[CV];
 #pragma unroll
-                            for (int j = 0; j < 16; j += 2) {
-                                const float v0 = __uint_as_float(r[c][j]), v1 = __uint_as_float(r[c][j + 1]);
-                                const float other = __shfl_xor_sync(0xffffffffu, odd ? v0 : v1, 1);
-                                const float lo_g = odd ? other : v0, hi_g = odd ? v1 : other;
-                                uint8_t* dst = base + ((j >> 3) << 10) + xo[(j >> 1) & 3];
-                                if (valid) {
-                                    if constexpr (TF32) {
-                                        const float h0 = tf32_hi(lo_g), h1 = tf32_hi(hi_g);
-                                        *(float2*)dst = make_float2(h0, h1);
-                                        if constexpr (SPLIT)
-                                            *(float2*)(dst + a.a3_bytes) = make_float2(tf32_hi(lo_g - h0), tf32_hi(hi_g - h1));
-                                    } else {
-                                        const __nv_bfloat162 hv = __floats2bfloat162_rn(lo_g, hi_g);
-                                        *(__nv_bfloat162*)dst = hv;
-                                        if constexpr (SPLIT) {
-                                            const float2 hf = __bfloat1622float2(hv);
-                                            *(__nv_bfloat162*)(dst + a.a3_bytes) =
-                                                __floats2bfloat162_rn(lo_g - hf.x, hi_g - hf.y);
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    continue;
-                }
-                for (int cb = c2lo; cb < c2hi; cb += 64) {
-                    const int nck = min(64, c2hi - cb) / 16;
-                    uint32_t r[4][16];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (c < nck) tmem_ld16(tY + ((uint32_t)(q * 32) << 16) + i * a.n2p + cb + 16 * c, r[c]);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (c >= nck) break;
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            const int y = cb + 16 * c + j;
-                            const float v0 = __uint_as_float(r[c][j]), v1 = __uint_as_float(r[c][j + 1]);
-                            if (pack) {
-                                // even lane keeps column y, odd lane keeps y + 1
-                                const float mine = odd ? v0 : v1;             // what the partner needs
-                                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                                const int yy = odd ? y + 1 : y;
-                                const float lo_g = odd ? other : v0;          // value at column g0
-                                const float hi_g = odd ? v1 : other;          // value at column g0 + 1
-                                if (!valid || yy >= a.n2) continue;
-                                const int m3 = xl * a.n2 + yy;
-                                const uint32_t off = atom * a.nT3 * 16384u + (m3 >> 7) * 16384u +
-                                                     sw128_offset(m3 & 127, gin0);
-                                if constexpr (TF32) {
-                                    const float h0 = tf32_hi(lo_g), h1 = tf32_hi(hi_g);
-                                    *(float2*)(a3 + off) = make_float2(h0, h1);
-                                    if constexpr (SPLIT)
-                                        *(float2*)(a3 + a.a3_bytes + off) =
-                                            make_float2(tf32_hi(lo_g - h0), tf32_hi(hi_g - h1));
-                                } else {
-                                    const __nv_bfloat162 hv = __floats2bfloat162_rn(lo_g, hi_g);
-                                    *(__nv_bfloat162*)(a3 + off) = hv;
-                                    if constexpr (SPLIT) {
-                                        const float2 hf = __bfloat1622float2(hv);
-                                        *(__nv_bfloat162*)(a3 + a.a3_bytes + off) =
-                                            __floats2bfloat162_rn(lo_g - hf.x, hi_g - hf.y);
-                                    }
-                                }
-                            } else {
-                                if (!valid) continue;
-#pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    const int yy = y + u;
-                                    if (yy >= a.n2) break;
-                                    const float v = u ? v1 : v0;
-                                    const int m3 = xl * a.n2 + yy;
-                                    const uint32_t off = atom * a.nT3 * 16384u + (m3 >> 7) * 16384u +
-                                                         sw128_offset(m3 & 127, gin);
-                                    if constexpr (TF32) {
-                                        const float hv = tf32_hi(v);
-                                        *(float*)(a3 + off) = hv;
-                                        if constexpr (SPLIT) *(float*)(a3 + a.a3_bytes + off) = tf32_hi(v - hv);
-                                    } else {
-                                        const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-                                        *(__nv_bfloat16*)(a3 + off) = hv;
-                                        if constexpr (SPLIT)
-                                            *(__nv_bfloat16*)(a3 + a.a3_bytes + off) =
-                                                __float2bfloat16_rn(v - __bfloat162float(hv));
-                                    }
+                                    for (int e = 0; e < CV; ++e)
+                                        v[e] = (g + e < a.r3) ? __uint_as_float(r[c][CV * u + e]) : 0.f;
+                                    uint4 hi, lo;
+                                    convert_chunk<TF32, SPLIT>(v, hi, lo);
+                                    const uint32_t ks = (uint32_t)(g / MK), bin = (uint32_t)((g % MK) * ES);
+                                    uint8_t* dst = a3 + ks * a3_sub + sw32_offset(m3, bin);
+                                    *(uint4*)dst = hi;
+                                    if constexpr (SPLIT) *(uint4*)(dst + a.a3_bytes) = lo;
                                 }
                             }
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&yfree);
             }
-            tc_fence_before();
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&yfree);
-                mbar_arrive(&a3full[s]);
-            }
+            if (lane == 0) mbar_arrive(&a3full[b]);
         }
         // ------------------------------ epilogue ------------------------------
         double e = 0.0;
-        if (ok && mbar_wait(&phidone, 0, a.err, 37) && *(volatile int*)a.err == 0) {
+        if (ok && mbar_wait_idle(&phidone, 0, a.err, 37) && *(volatile int*)a.err == 0) {
             tc_fence_after();
-            const long N3 = (long)a.n1 * a.n2 * a.n3;
-            const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
-            const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
-            float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
-            float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
-            const float* sa = a.SA + (long)rec.ia * N3;
-            const float* sb = a.SB + (long)rec.ib * N3;
-            // Each warp stages its quadrant's 32 rows x 64 columns of phi in shared memory (the
-            // pipeline buffers are idle now), then walks the rows with consecutive z across lanes:
-            // psi reads are coalesced and W is updated with 8-byte vector reductions.  The two
-            // warps of a quadrant split the rows (even / odd).
-            float* stg = (float*)(smem + a.stg_off) + warp * (32 * 68);
-            for (int jt = 0; jt < a.nT3; ++jt) {
-                for (int cb = 0; cb < a.n3p; cb += 64) {
-                    const int nck = min(64, a.n3p - cb) / 16;
-                    uint32_t r[4][16];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (c < nck) tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + jt * a.n3p + cb + 16 * c, r[c]);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (c < nck)
-#pragma unroll
-                            for (int j = 0; j < 16; j += 4)
-                                *(float4*)(stg + lane * 68 + 16 * c + j) =
-                                    make_float4(__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
-                                                __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3]));
-                    __syncwarp();
-                    // lanes 0-15 take row rr, lanes 16-31 row rr + 1; four consecutive z per lane
-                    const int sub = lane >> 4, z = cb + 4 * (lane & 15);
-                    for (int rp = 2 * h; rp < 32; rp += 4) {
-                        const int rr = rp + sub;
-                        const int m3 = jt * 128 + q * 32 + rr;
-                        const int xl = m3 / a.n2, y = m3 - xl * a.n2, x = x0 + xl;
-                        if (m3 >= a.R || x >= a.n1 || z >= a.n3) continue;
-                        const long idx = ((long)x * a.n2 + y) * a.n3 + z;   // multiple of 4: n3 % 4 == 0
-                        const float4 phi = *(const float4*)(stg + rr * 68 + 4 * (lane & 15));
-                        const float wxy = a.w1[x] * a.w2[y];
-                        const float4 w3 = *(const float4*)(a.w3 + z);
-                        const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
-                        float4 f = phi;
-                        if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
-                        // with symmetric pairs the energy factors (psi_a, psi_b) are the two
-                        // multipliers themselves: each orbital value is read once
-                        const bool en = (a.flags & EPI_ENERGY) != 0;
-                        const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
-                        float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
-                        if (o0 || (en && a.emul)) m0 = *(const float4*)(mul0 + idx);
-                        if (o1 || (en && a.emul)) m1 = *(const float4*)(mul1 + idx);
-                        if (o0) atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
-                        if (o1) atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
-                        if (en) {
-                            const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
-                            const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
-                            e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
-                                 (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
-                        }
-                    }
-                    __syncwarp();
-                }
+            e = consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, [&](int jt, int r, int& x, int& y) {
+                const int m3 = jt * 128 + r;
+                const int xl = m3 / a.n2;
+                y = m3 - xl * a.n2;
+                x = x0 + xl;
+                return m3 < a.R && x < a.n1;
+            });
+        }
+        if (a.flags & EPI_ENERGY) {
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+            if (lane == 0) red[warp] = e * rec.ew;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if ((a.flags & EPI_ENERGY) && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        a.epart[(long)pl * gridDim.x + slab] = s;
+    }
+    if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// Variant for the single-pass precisions: stage 3 runs as kind::tf32 with its A operand read
+// straight from TMEM.  Stage 2 leaves Y_t,x[y][g] in TMEM with y on the lanes and g on the
+// columns, which is exactly the K-major layout of an A operand whose rows are the y of one x
+// plane; so stage 3 is one 128-row MMA tile per plane, and no warp touches Y.
+//
+// Schedule.  Warp 9 issues stage 2 of every term into nyb rotating Y buffers; warps 0..ns3-1
+// issue stage 3, one x plane each, as soon as the term's stage 2 has finished.  A warp needs
+// more time to issue a tcgen05.mma than the tensor pipe needs to run one of these small
+// tiles, so the stage-3 streams are issued in parallel.  Operand tiles use the 128-byte
+// swizzle (one 128-byte row per TMA request).
+template <bool S2TF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_consume_ts(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mA2,
+                 const __grid_constant__ CUtensorMap mA3f, ConsumeArgs a) {
+    constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ double red[8];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slab = blockIdx.x, pl = blockIdx.y;
+    const int x0 = slab * a.bx;
+    const PairRec rec = a.recs[a.p0 + pl];
+    const int NL = a.nload, NYB = a.nyb, BX = a.bx;
+    auto term_of = [&](int t) { return t; };     // theta ascending, as in the split-precision kernel
+
+    // load stage s: [A_t2 tile][Z tile][mu_t A_t3 tile (tf32)], each [atom][rows][128 bytes]
+    auto YAs = [&](int s) { return smem + s * a.load_bytes; };
+    auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
+    auto B3s = [&](int s) { return Zs(s) + a.z_bytes; };
+
+    if (threadIdx.x == 0) {
+        // stage-3 commits (ybar, empty, phidone) come from each of the ns3 plane warps
+        for (int s = 0; s < kMaxLoad; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], a.ns3);
+        }
+        for (int b = 0; b < kMaxYBuf; ++b) {
+            mbar_init(&s2bar[b], 1);
+            mbar_init(&ybar[b], a.ns3);
+        }
+        mbar_init(&phidone, a.ns3);
+        mbar_init(&s2fin, 1);
+        fence_barrier_init();
+    }
+    // Z tile rows that no copy writes (rows r3..gs-1 of each plane, the tail up to the MMA's N)
+    // feed Y columns that stage 3 multiplies by zeros: they must hold finite values
+    for (int s = 0; s < NL; ++s) {
+        uint4* z = (uint4*)Zs(s);
+        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    fence_async_smem();
+    if (warp == 8) {
+        tmem_alloc(&tmem_base, a.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
+    const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
+
+    // The producer and MMA roles run on whole warps with uniform control flow; one elected lane
+    // issues each TMA / tcgen05 instruction (see the _w helpers).
+    if (warp == 8) {
+        // ------------------------------ TMA producer ------------------------------
+        const int na2 = (a.ks2 + 3) / 4, na3 = (a.ks3 + 3) / 4;   // 128-byte atoms along K
+        int issued = 0;
+        bool ok = true;
+        for (int t = 0; t < a.nt && ok; ++t) {
+            const int s = t % NL;
+            ok = mbar_wait(&empty_bar[s], ((t / NL) & 1) ^ 1, a.err, 41);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            issued = t + 1;
+            for (int ahead = (t == 0 ? 1 : NL + 1); ahead <= NL + 1; ++ahead)
+                if (t + ahead < a.nt)
+                    for (int p = 0; p < BX; ++p)
+                        for (int k = 0; k < na2; ++k)
+                            tma_prefetch_l2_3d_w(&mZ, k * AK2, (x0 + p) * a.r3, pl * a.nt + term_of(t + ahead));
+            mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
+            const int tt = term_of(t);
+            const int zdep = pl * a.nt + tt;
+            for (int k = 0; k < na2; ++k) {
+                tma_load_3d_w(YAs(s) + k * ya_atom, &mA2, &full_bar[s], k * AK2, 0, tt);
+                // plane p's rows start at row p * gs (a multiple of 8) of the Z tile
+                for (int p = 0; p < BX; ++p)
+                    tma_load_3d_w(Zs(s) + k * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s], k * AK2,
+                                  (x0 + p) * a.r3, zdep);
             }
+            for (int k = 0; k < na3; ++k) tma_load_3d_w(B3s(s) + k * b3_atom, &mA3f, &full_bar[s], k * 32, 0, tt);
+        }
+        if (!ok)
+            for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
+    } else if (warp == 9) {
+        // ------------------------------ stage-2 MMA issuer ------------------------------
+        // descriptors are built once and advanced by adds: +32 bytes (2 units of the
+        // address / 16 field) per K step inside a 128-byte atom, one atom stride every 4 steps
+        const uint64_t d0 = sdesc_sw128(0);
+        bool ok = true;
+        for (int t = 0; t < a.nt && ok; ++t) {
+            bool w = mbar_wait(&full_bar[t % NL], (t / NL) & 1, a.err, 42);
+            // Y buffer t % nyb was last read by stage 3 of term t - nyb (every plane warp)
+            if (w && t >= NYB) w = mbar_wait(&ybar[t % NYB], ((t - NYB) / NYB) & 1, a.err, 43);
+            if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+            tc_fence_after();
+            const int s = t % NL;
+            const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
+            const uint32_t tY = tmem + (uint32_t)(t % NYB) * a.y_cols;
+            for (int i = 0; i < a.nY; ++i)
+                for (int p0 = 0; p0 < BX; p0 += a.npc) {
+                    const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                    const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                    const uint32_t d = tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs);
+                    const uint64_t ad0 = ya + (uint32_t)i * 1024u, bd0 = zb + (uint32_t)(p0 * a.gs) * 8u;
+                    for (int k = 0; k < a.ks2; ++k)
+                        mma_ss_w<S2TF32>(d, ad0 + (uint32_t)(k >> 2) * (ya_atom >> 4) + (uint32_t)(k & 3) * 2u,
+                                         bd0 + (uint32_t)(k >> 2) * (z_atom >> 4) + (uint32_t)(k & 3) * 2u, id2,
+                                         k > 0 ? 1u : 0u);
+                }
+            mma_commit_w(&s2bar[t % NYB]);
+        }
+        // the CTA must not release TMEM while these MMAs run
+        mma_commit_w(&s2fin);
+        mbar_drain(&s2fin, 0);
+    } else {
+        // ---------------- stage-3 MMA issuers (warps 0..nS3-1), then the epilogue ----------------
+        // Issuing one tcgen05.mma costs a warp more time than the tensor pipe needs to run it at
+        // these sizes, so stage 3 is issued by one warp per x plane in parallel (each plane
+        // accumulates into its own TMEM columns) while warp 9 issues stage 2.
+        double e = 0.0;
+        bool ok = true;
+        if (warp < a.ns3) {
+            const uint32_t id3 = idesc_tf32(128, a.n3p);
+            const uint64_t d0 = sdesc_sw128(0);
+            for (int t = 0; t < a.nt && ok; ++t) {
+                const bool w = mbar_wait(&s2bar[t % NYB], (t / NYB) & 1, a.err, 44);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                tc_fence_after();
+                const int s = t % NL;
+                const uint64_t b3 = d0 + (smem_u32(B3s(s)) >> 4);
+                const uint32_t tY = tmem + (uint32_t)(t % NYB) * a.y_cols;
+                const uint32_t acc0 = t > 0 ? 1u : 0u;
+                for (int p = warp; p < BX; p += a.ns3)
+                    for (int i = 0; i < a.nY; ++i) {
+                        const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
+                        const uint32_t d = tPhi + (uint32_t)((p * a.nY + i) * a.n3p);
+                        for (int k = 0; k < a.ks3; ++k)
+                            mma_ts_tf32_w(d, aT + 8u * k, b3 + (uint32_t)(k >> 2) * (b3_atom >> 4) + (uint32_t)(k & 3) * 2u,
+                                          id3, k > 0 ? 1u : acc0);
+                    }
+                mma_commit_w(&ybar[t % NYB]);
+                mma_commit_w(&empty_bar[s]);
+            }
+            mma_commit_w(&phidone);
+        }
+        if (ok && mbar_wait_idle(&phidone, 0, a.err, 45) && *(volatile int*)a.err == 0) {
+            tc_fence_after();
+            e = consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, [&](int jt, int r, int& x, int& y) {
+                const int p = jt / a.nY, i = jt - p * a.nY;
+                y = i * 128 + r;
+                x = x0 + p;
+                return y < a.n2 && x < a.n1;
+            });
+        } else if (warp < a.ns3) {
+            mbar_drain(&phidone, 0);
         }
         if (a.flags & EPI_ENERGY) {
             for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -443,55 +685,144 @@ __global__ void __launch_bounds__(kThreads, 1)
 // host side: tile plan and launch
 // ======================================================================================
 struct ConsumePlan {
-    int bx, nT2, nT3, n2p, n3p, nk2, nk3, nstage, nbox2, box_rows2;
-    uint32_t a2, b2, b3, a3, stage, tmem_cols, y_cols, stg_off;
+    bool ts;                 // single-pass kernel (stage 3 from TMEM) instead of the converter kernel
+    int bx, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, nload, na3, nyb, gs, ycol_tile;
+    uint32_t ya_rows, z_rows, ya, zb, b3, a3, load, a3_off, tmem_cols, y_cols;
     size_t smem;
 };
 
-static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nstage, ConsumePlan* p) {
-    const int AK = tf32 ? 32 : 64;
+// Single-pass plan: bx planes, nload load stages, 4 (else 3, 2) stage-2 output buffers in TMEM
+static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* p) {
+    const int MK2 = tf32 ? 8 : 16;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
-    if (bx < 1 || bx > n1) return false;
+    if (bx < 1 || bx > n1 || bx > tcc::kMaxPlanes || nload < 2 || nload > tcc::kMaxLoad) return false;
+    *p = ConsumePlan{};
+    p->ts = true;
     p->bx = bx;
     p->n2p = pad16(n2);
     p->n3p = pad16(n3);
-    if (p->n2p > 256 || p->n3p > 256) return false;
-    const int R2 = bx * r3, R = bx * n2;
-    p->nT2 = (R2 + 127) / 128;
-    p->nT3 = (R + 127) / 128;
-    p->nk2 = (r2 + AK - 1) / AK;
-    p->nk3 = (r3 + AK - 1) / AK;
-    if (R2 > 256) return false;                 // one TMA box per K atom fills the stage-2 tile
-    p->box_rows2 = R2;
-    p->nbox2 = 1;
-    p->y_cols = (uint32_t)(p->nT2 * p->n2p);
+    p->gs = pad8(r3);                          // TMEM columns (and Z tile rows) per plane
+    if (p->n2p > 256 || p->n3p > 256 || p->gs > 256) return false;
+    p->nY = (n2 + 127) / 128;
+    p->npc = std::min(bx, 256 / p->gs);
+    p->ks2 = (r2 + MK2 - 1) / MK2;
+    p->ks3 = (r3 + 7) / 8;
+    // columns of one y tile of Y: each plane chunk writes pad16(planes * gs) columns from p0 * gs
+    p->ycol_tile = 0;
+    for (int p0 = 0; p0 < bx; p0 += p->npc)
+        p->ycol_tile = std::max(p->ycol_tile, p0 * p->gs + pad16(std::min(p->npc, bx - p0) * p->gs));
+    p->y_cols = (uint32_t)(p->nY * p->ycol_tile);
+    p->nT3 = bx * p->nY;
+    const uint32_t phi = (uint32_t)(p->nT3 * p->n3p);
+    p->nyb = tcc::kMaxYBuf;
+    while (p->nyb > 2 && p->nyb * p->y_cols + phi > 512) --p->nyb;
+    const uint32_t cols = p->nyb * p->y_cols + phi;
+    if (cols > 512) return false;
+    p->tmem_cols = 32;
+    while (p->tmem_cols < cols) p->tmem_cols <<= 1;
+    const int na2 = (p->ks2 + 3) / 4, na3 = (p->ks3 + 3) / 4;   // 128-byte atoms along K
+    p->ya_rows = (uint32_t)(p->nY * 128);
+    p->z_rows = (uint32_t)p->ycol_tile;         // rows every stage-2 MMA may read
+    p->ya = (uint32_t)na2 * p->ya_rows * 128u;
+    p->zb = (uint32_t)na2 * p->z_rows * 128u;
+    p->b3 = (uint32_t)na3 * p->n3p * 128u;
+    p->load = (p->ya + p->zb + p->b3 + 1023) & ~1023u;
+    p->nload = nload;
+    p->smem = std::max((size_t)p->load * nload, (size_t)tcc::kEpiBytes) + 1024;
+    return p->smem <= 226 * 1024;
+}
+
+// tensor-pipe cycles per plane and term of a single-pass plan (one MMA costs max(50, N / 2))
+static double ts_cost(const ConsumePlan& p) {
+    double s2 = 0;
+    for (int p0 = 0; p0 < p.bx; p0 += p.npc) s2 += std::max(50.0, pad16(std::min(p.npc, p.bx - p0) * p.gs) / 2.0);
+    const double s3 = p.bx * std::max(50.0, p.n3p / 2.0);
+    return (p.nY * p.ks2 * s2 + p.nY * p.ks3 * s3) / p.bx;
+}
+
+static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p);
+
+// single-pass shapes that fit no TMEM plan (large n with large r) use the converter kernel
+static bool ts_possible(const tx_ctx* c, bool tf32) {
+    ConsumePlan p;
+    for (int nl = 2; nl <= tcc::kMaxLoad; ++nl)
+        if (plan_ts(c, tf32, 1, nl, &p)) return true;
+    return false;
+}
+
+static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p) {
+    if (!split && ts_possible(c, tf32)) return plan_ts(c, tf32, bx, nload, p);
+    return plan_cv(c, tf32, split, bx, nload, na3, p);
+}
+
+// Converter plan (split precisions)
+static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p) {
+    const int MK = tf32 ? 8 : 16;
+    const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
+    if (bx < 1 || bx > n1 || bx > tcc::kMaxPlanes || nload < 1 || nload > tcc::kMaxLoad || na3 < 1 || na3 > 2)
+        return false;
+    *p = ConsumePlan{};
+    p->bx = bx;
+    p->n2p = pad16(n2);
+    p->n3p = pad16(n3);
+    p->Nz = pad16(r3);
+    if (p->n2p > 256 || p->n3p > 256 || p->Nz > 256) return false;
+    p->nY = (n2 + 127) / 128;
+    p->nq = std::min(4, (n2 + 31) / 32);
+    p->npc = std::min(bx, 256 / p->Nz);                  // planes per stage-2 MMA (N <= 256)
+    p->nT3 = (bx * n2 + 127) / 128;
+    p->ks2 = (r2 + MK - 1) / MK;
+    p->ks3 = (r3 + MK - 1) / MK;
+    p->y_cols = (uint32_t)(bx * p->nY * p->Nz);
     const uint32_t cols = p->y_cols + (uint32_t)(p->nT3 * p->n3p);
     if (cols > 512) return false;
     p->tmem_cols = 32;
     while (p->tmem_cols < cols) p->tmem_cols <<= 1;
-    p->a2 = (uint32_t)(p->nk2 * p->nT2 * 16384);
-    p->b2 = (uint32_t)(p->nk2 * p->n2p * 128);
-    p->b3 = (uint32_t)(p->nk3 * p->n3p * 128);
-    p->a3 = (uint32_t)(p->nk3 * p->nT3 * 16384);
-    p->stage = (split ? 2 : 1) * (p->a2 + p->b2 + p->b3 + p->a3);
-    p->nstage = nstage;
-    p->stg_off = 0;                                    // staging reuses the idle pipeline buffers
-    const size_t stg = (size_t)8 * 32 * 68 * 4;
-    p->smem = std::max((size_t)p->stage * nstage, stg) + 1024;
+    const int m = split ? 2 : 1;
+    p->ya_rows = (uint32_t)(p->nY * 128);
+    p->z_rows = (uint32_t)(bx * p->Nz);                   // plane p at rows p * Nz
+    p->ya = (uint32_t)p->ks2 * p->ya_rows * 32u;
+    p->zb = (uint32_t)p->ks2 * p->z_rows * 32u;
+    p->b3 = (uint32_t)(p->ks3 * p->n3p * 32);
+    p->a3 = (uint32_t)(p->ks3 * p->nT3 * 128 * 32);
+    p->load = (uint32_t)(m * (p->ya + p->zb + p->b3));
+    p->load = (p->load + 1023) & ~1023u;
+    p->nload = nload;
+    p->na3 = na3;
+    p->a3_off = p->load * nload;
+    const size_t total = (size_t)p->a3_off + (size_t)na3 * m * p->a3;
+    p->smem = std::max(total, (size_t)tcc::kEpiBytes) + 1024;   // the epilogue reuses the front
     return p->smem <= 226 * 1024;
 }
 
 static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* best) {
-    if (c->tile_bx > 0 && plan_for(c, tf32, split, c->tile_bx, c->tile_nstage, best)) return true;
-    // prefer two stages, then the slab with the least padding per useful row
+    if (c->tile_bx > 0) {
+        const int nl = c->tile_nstage;
+        if (plan_for(c, tf32, split, c->tile_bx, nl, nl > 1 ? 2 : 1, best)) return true;
+    }
     double best_score = -1;
-    for (int ns = 2; ns >= 1; --ns)
-        for (int bx = 1; bx <= 16; ++bx) {
+    if (!split && ts_possible(c, tf32)) {
+        // least tensor-pipe time per plane and term, then the deepest load pipeline
+        for (int nl = tcc::kMaxLoad; nl >= 2; --nl)
+            for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx) {
+                ConsumePlan p;
+                if (!plan_ts(c, tf32, bx, nl, &p)) continue;
+                const double score = 1.0 / ts_cost(p) * (p.nyb >= 3 ? 1.0 : 0.85) * (nl >= 3 ? 1.0 : 0.9);
+                if (score > best_score * 1.0001) {
+                    best_score = score;
+                    *best = p;
+                }
+            }
+        return best_score > 0;
+    }
+    // deepest load pipeline first, then the slab with the least padding per useful row
+    for (int nl = tcc::kMaxLoad; nl >= 1; --nl)
+        for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx) {
             ConsumePlan p;
-            if (!plan_for(c, tf32, split, bx, ns, &p)) continue;
+            if (!plan_for(c, tf32, split, bx, nl, nl > 1 ? 2 : 1, &p)) continue;
             const double use3 = (double)(bx * c->n[1]) / (p.nT3 * 128.0);
-            const double use2 = (double)(bx * c->r[2]) / (p.nT2 * 128.0);
-            const double score = (ns == 2 ? 1.0 : 0.6) * (0.7 * use3 + 0.3 * use2) * (1.0 + 0.02 * bx);
+            const double depth = nl >= 4 ? 1.0 : (nl == 3 ? 0.95 : (nl == 2 ? 0.8 : 0.5));
+            const double score = depth * use3 * (1.0 + 0.03 * std::min(bx, 8));
             if (score > best_score) {
                 best_score = score;
                 *best = p;
@@ -500,15 +831,15 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
     return best_score > 0;
 }
 
-// every (bx, nstage) that fits, for the autotuner; returns the count written (<= cap)
+// every (bx, stages) that fits, for the autotuner; returns the count written (<= cap)
 int tc_feasible_plans(const tx_ctx* c, int* bx, int* ns, int cap) {
     const TcOperands* op = c->tc;
     if (!op) return 0;
     int k = 0;
-    for (int s = 2; s >= 1; --s)
-        for (int b = 1; b <= 16 && k < cap; ++b) {
+    for (int s = tcc::kMaxLoad; s >= 1; --s)
+        for (int b = 1; b <= tcc::kMaxPlanes && k < cap; ++b) {
             ConsumePlan p;
-            if (plan_for(c, op->tf32, op->split, b, s, &p)) {
+            if (plan_for(c, op->tf32, op->split, b, s, s > 1 ? 2 : 1, &p)) {
                 bx[k] = b;
                 ns[k] = s;
                 ++k;
@@ -523,14 +854,14 @@ bool tc_current_plan(const tx_ctx* c, int* bx, int* ns) {
     ConsumePlan p;
     if (!op || !choose_plan(c, op->tf32, op->split, &p)) return false;
     *bx = p.bx;
-    *ns = p.nstage;
+    *ns = p.nload;
     return true;
 }
 
 bool tc_plan_fits(const tx_ctx* c, int bx, int ns) {
     const TcOperands* op = c->tc;
     ConsumePlan p;
-    return op && plan_for(c, op->tf32, op->split, bx, ns, &p);
+    return op && plan_for(c, op->tf32, op->split, bx, ns, ns > 1 ? 2 : 1, &p);
 }
 
 bool tc_consume_supported(const tx_ctx* c, bool tf32, bool split, std::string* why) {
@@ -557,40 +888,72 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     if (!choose_plan(c, op->tf32, op->split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T;
     const TcScratch sc = tc_scratch(c);
+    const int m = op->split ? 2 : 1;
     tcc::ConsumeArgs a{};
     a.n1 = n1; a.n2 = n2; a.n3 = n3; a.r2 = r2; a.r3 = r3; a.nt = T;
-    a.bx = p.bx; a.R = p.bx * n2; a.R2 = p.bx * r3; a.nT2 = p.nT2; a.nT3 = p.nT3; a.n2p = p.n2p; a.n3p = p.n3p;
-    a.nk2 = p.nk2; a.nk3 = p.nk3; a.nbox2 = p.nbox2; a.box_rows2 = p.box_rows2; a.nstage = p.nstage;
-    a.a2_bytes = p.a2; a.b2_bytes = p.b2; a.b3_bytes = p.b3; a.a3_bytes = p.a3; a.stage_bytes = p.stage;
-    a.stage_tx = (op->split ? 2 : 1) * (uint32_t)(p.nk2 * p.nbox2 * p.box_rows2 * 128 + p.b2 + p.b3);
-    a.tmem_cols = p.tmem_cols; a.y_cols = p.y_cols; a.stg_off = p.stg_off;
+    a.bx = p.bx; a.R = p.bx * n2; a.nY = p.nY; a.Nz = p.Nz; a.npc = p.npc; a.nT3 = p.nT3;
+    a.n2p = p.n2p; a.n3p = p.n3p; a.ks2 = p.ks2; a.ks3 = p.ks3; a.nq = p.nq;
+    a.nload = p.nload; a.na3 = p.na3; a.nyb = p.nyb;
+    a.ya_rows = p.ya_rows; a.z_rows = p.z_rows;
+    a.ya_bytes = p.ya; a.z_bytes = p.zb; a.b3_bytes = p.b3; a.a3_bytes = p.a3;
+    a.load_bytes = p.load; a.a3_off = p.a3_off;
+    // bytes the TMA delivers per stage (out-of-range rows and columns count: they are zero-filled)
+    a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * p.n2p + p.ks2 * p.bx * r3 + p.ks3 * p.n3p));
+    a.tmem_cols = p.tmem_cols; a.y_cols = p.y_cols;
     a.p0 = p0; a.recs = recs;
     a.SA = SA; a.SB = SB; a.MUL0 = MUL0; a.MUL1 = MUL1; a.OUT0 = OUT0; a.OUT1 = OUT1;
     a.w1 = c->f_w[0]; a.w2 = c->f_w[1]; a.w3 = c->f_w[2];
     a.flags = flags; a.epart = epart; a.err = c->d_err;
     a.emul = (SA == MUL1 && SB == MUL0 && emul) ? 1 : 0;
     const int eb = op->esize;
-    const uint32_t AK = op->tf32 ? 32 : 64;
+    const uint32_t MK = op->tf32 ? 8 : 16;
+    dim3 grid((unsigned)((n1 + p.bx - 1) / p.bx), (unsigned)np);
+    if (p.ts) {
+        a.gs = p.gs; a.ycol_tile = p.ycol_tile; a.ns3 = std::min(p.bx, 8);
+        // bytes per stage (128-byte rows; zero-filled parts count): A_t2, Z planes, mu_t A_t3
+        const int na2 = (p.ks2 + 3) / 4, na3 = (p.ks3 + 3) / 4;
+        a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3 + na3 * p.n3p));
+        CUtensorMap mZ, mA2, mA3f;
+        const uint32_t AK2 = op->tf32 ? 32 : 64;   // elements per 128-byte box row
+        // K extents are the zero-padded row lengths (whole 32-byte sectors)
+        const int l2 = ldk(r2, eb);
+        TX_TRY(make_map(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b,
+                        AK2, (uint32_t)r3));
+        TX_TRY(make_map(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, AK2, (uint32_t)p.n2p));
+        TX_TRY(make_map(&mA3f, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 32, (uint32_t)p.n3p));
+        const int ps = prof_begin("tc_consume", s);
+        if (op->tf32) {
+            cudaFuncSetAttribute(tcc::k_consume_ts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, a);
+        } else {
+            cudaFuncSetAttribute(tcc::k_consume_ts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, a);
+        }
+        prof_end(ps, s);
+        TX_LAUNCHED();
+        return TX_OK;
+    }
     // Z of this batch: [pair][t][(x, g) rows][ld_b]; lo part after the batch's hi part
     const size_t zlo = (size_t)np * sc.z * eb;
     CUtensorMap mZ, mZlo, mA2, mA2lo, mA3, mA3lo;
-    TX_TRY(make_map(&mZ, Z, eb, r2, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b, AK,
-                    (uint32_t)p.box_rows2));
-    TX_TRY(make_map(&mA2, op->st.A2, eb, r2, n2, T, pad8(r2), (uint64_t)n2 * pad8(r2), AK, (uint32_t)p.n2p));
-    TX_TRY(make_map(&mA3, op->st.A3, eb, r3, n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), AK, (uint32_t)p.n3p));
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_32B;
+    const int l2 = ldk(r2, eb), l3 = ldk(r3, eb);
+    TX_TRY(make_map_sw(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b, MK,
+                       (uint32_t)r3, sw));
+    TX_TRY(make_map_sw(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, MK, (uint32_t)p.n2p, sw));
+    TX_TRY(make_map_sw(&mA3, op->st.A3, eb, l3, n3, T, l3, (uint64_t)n3 * l3, MK, (uint32_t)p.n3p, sw));
     if (op->split) {
-        TX_TRY(make_map(&mZlo, (const char*)Z + zlo, eb, r2, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b,
-                        (uint64_t)n1 * r3 * sc.ld_b, AK, (uint32_t)p.box_rows2));
-        TX_TRY(make_map(&mA2lo, (const char*)op->st.A2 + op->st.off_lo, eb, r2, n2, T, pad8(r2),
-                        (uint64_t)n2 * pad8(r2), AK, (uint32_t)p.n2p));
-        TX_TRY(make_map(&mA3lo, (const char*)op->st.A3 + op->st.off_lo, eb, r3, n3, T, pad8(r3),
-                        (uint64_t)n3 * pad8(r3), AK, (uint32_t)p.n3p));
+        TX_TRY(make_map_sw(&mZlo, (const char*)Z + zlo, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b,
+                           (uint64_t)n1 * r3 * sc.ld_b, MK, (uint32_t)r3, sw));
+        TX_TRY(make_map_sw(&mA2lo, (const char*)op->st.A2 + op->st.off_lo, eb, l2, n2, T, l2, (uint64_t)n2 * l2, MK,
+                           (uint32_t)p.n2p, sw));
+        TX_TRY(make_map_sw(&mA3lo, (const char*)op->st.A3 + op->st.off_lo, eb, l3, n3, T, l3, (uint64_t)n3 * l3, MK,
+                           (uint32_t)p.n3p, sw));
     } else {
         mZlo = mZ;
         mA2lo = mA2;
         mA3lo = mA3;
     }
-    dim3 grid((unsigned)((n1 + p.bx - 1) / p.bx), (unsigned)np);
     const int ps = prof_begin("tc_consume", s);
 #define LAUNCH(TF, SP)                                                                                       \
     do {                                                                                                     \

@@ -114,16 +114,18 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t b_addr = a_addr + a_bytes;
             const int krem = g.K - kb * kAtomK;
             const int nsteps = (min(krem, kAtomK) + kMmaK - 1) / kMmaK;
+            // descriptors advance by adds (32 bytes per K step = 2 in the address / 16 field)
+            // (each lo copy sits a_bytes + b_bytes after its hi copy)
+            uint64_t ad = sdesc_sw128(a_addr), bd = sdesc_sw128(b_addr);
+            const uint64_t lo = (uint64_t)((a_bytes + b_bytes) >> 4);
             for (int k = 0; k < nsteps; ++k) {
-                const uint64_t ad = sdesc_sw128(a_addr + k * 32), bd = sdesc_sw128(b_addr + k * 32);
-                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                mma_ss<TF32>(tmem, ad, bd, idesc, acc);
+                mma_ss<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                 if constexpr (SPLIT) {
-                    const uint64_t alo = sdesc_sw128(a_addr + a_bytes + b_bytes + k * 32);
-                    const uint64_t blo = sdesc_sw128(a_addr + 2 * a_bytes + b_bytes + k * 32);
-                    mma_ss<TF32>(tmem, ad, blo, idesc, 1u);
-                    mma_ss<TF32>(tmem, alo, bd, idesc, 1u);
+                    mma_ss<TF32>(tmem, ad, bd + lo, idesc, 1u);
+                    mma_ss<TF32>(tmem, ad + lo, bd, idesc, 1u);
                 }
+                ad += 2;
+                bd += 2;
             }
             mma_commit(&empty_bar[s]);
         }
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
 
     // ---------------- epilogue: 4 warps, one TMEM lane (= output row) per thread ----------------
-    const bool ok = mbar_wait(&done_bar, 0, g.err, 14);
+    const bool ok = mbar_wait_idle(&done_bar, 0, g.err, 14);
     tc_fence_after();
     const long boff = (long)b1 * g.c_b1 + (long)b2 * g.c_b2;
     auto row_off = [&](int m) { return boff + (long)(m / g.rdiv) * g.c_mh + (long)(m % g.rdiv) * g.c_m; };
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(128, 1)
                 if (m0 + warp * 32 + rr >= g.M) break;
                 if (v0) store_out(g, base + co0, g.alpha * stg[rr * 65 + cc0]);
                 if (v1) store_out(g, base + co1, g.alpha * stg[rr * 65 + cc1]);
+
             }
             __syncwarp();
         }
@@ -218,6 +221,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int make_map(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent, uint64_t rows, uint64_t depth,
              uint64_t row_stride_elems, uint64_t depth_stride_elems, uint32_t box_k, uint32_t box_rows) {
+    return make_map_sw(m, base, elem_bytes, k_extent, rows, depth, row_stride_elems, depth_stride_elems, box_k, box_rows,
+                       CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int make_map_sw(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent, uint64_t rows, uint64_t depth,
+                uint64_t row_stride_elems, uint64_t depth_stride_elems, uint32_t box_k, uint32_t box_rows,
+                CUtensorMapSwizzle swizzle) {
     auto fn = encode_fn();
     if (!fn) return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     if (((uintptr_t)base & 15) || (row_stride_elems * elem_bytes) % 16 || (depth_stride_elems * elem_bytes) % 16)
@@ -230,7 +240,7 @@ int make_map(CUtensorMap* m, const void* base, int elem_bytes, uint64_t k_extent
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(TX_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
     return TX_OK;

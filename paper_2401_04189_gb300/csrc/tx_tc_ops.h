@@ -7,6 +7,11 @@ namespace tx {
 
 inline int pad8(int v) { return (v + 7) & ~7; }
 inline int pad16(int v) { return (v + 15) & ~15; }
+// row length (elements) of a tensor-core operand in memory: K padded with zeros to a multiple of
+// 32 bytes.  A TMA box row that ends inside a 32-byte sector of its tensor takes a slow path
+// (measured: about a quarter of the full-row rate), so every map's K extent is a whole number
+// of sectors and the padding is read as zeros.
+inline int ldk(int k, int elem_bytes) { return elem_bytes == 2 ? pad16(k) : pad8(k); }
 
 // Static operands, K-major with 16-byte row strides, in the operand type of the precision
 // (bf16, or float32 holding TF32 values).  For the 3-pass precisions `lo` holds x - hi.
@@ -17,6 +22,7 @@ struct TcStatic {
     void* A1s;   // [T*n1][ld(r1)]   rows (t,x), K = alpha    (expansion, mode 1, every term)
     void* A2;    // [T][n2][ld(r2)]  rows y, K = beta         (expansion, mode 2)
     void* A3;    // [T][n3][ld(r3)]  rows z, K = gamma, mu_t folded in (expansion, mode 3)
+    void* A3f;   // the same in float32 rounded to TF32 (single-pass precisions; == A3 for tf32)
     size_t off_lo;   // byte offset from each hi array to its lo copy (3-pass precisions)
 };
 

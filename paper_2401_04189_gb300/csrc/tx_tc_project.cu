@@ -160,13 +160,18 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t ra = smem_u32(rho + s * RHO_BYTES), rl = smem_u32(rho_lo + s * RHO_BYTES);
             const uint32_t ba = smem_u32(bt + kb * B_BYTES), bl = smem_u32(bt_lo + kb * B_BYTES);
             const int nsteps = (min(a.n3 - kb * ZB, ZB) + kMmaK - 1) / kMmaK;
+            // descriptors advance by adds (32 bytes per K step = 2 in the address / 16 field)
+            uint64_t ad = sdesc_sw128(ra), bd = sdesc_sw128(ba), al = sdesc_sw128(rl), bdl = sdesc_sw128(bl);
             for (int k = 0; k < nsteps; ++k) {
-                const uint64_t ad = sdesc_sw128(ra + 32 * k), bd = sdesc_sw128(ba + 32 * k);
                 mma_ss<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                 if constexpr (SPLIT) {
-                    mma_ss<TF32>(tmem, ad, sdesc_sw128(bl + 32 * k), idesc, 1u);
-                    mma_ss<TF32>(tmem, sdesc_sw128(rl + 32 * k), bd, idesc, 1u);
+                    mma_ss<TF32>(tmem, ad, bdl, idesc, 1u);
+                    mma_ss<TF32>(tmem, al, bd, idesc, 1u);
                 }
+                ad += 2;
+                bd += 2;
+                al += 2;
+                bdl += 2;
             }
             mma_commit(&rho_free[s]);
             if (kb == nk - 1) mma_commit(&done_bar);
@@ -242,9 +247,9 @@ int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const
     TX_TRY(make_map_f32_plain(&mA, SA, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nA, (uint32_t)ZB, 128));
     TX_TRY(make_map_f32_plain(&mB, SB, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nB, (uint32_t)ZB, 128));
     const int eb = op->esize;
-    TX_TRY(make_map(&mU, op->st.U3T, eb, n3, r3, 1, pad8(n3), 0, (uint32_t)ZB, (uint32_t)a.N3p));
+    TX_TRY(make_map(&mU, op->st.U3T, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB, (uint32_t)a.N3p));
     if (op->split)
-        TX_TRY(make_map(&mUlo, (const char*)op->st.U3T + op->st.off_lo, eb, n3, r3, 1, pad8(n3), 0, (uint32_t)ZB,
+        TX_TRY(make_map(&mUlo, (const char*)op->st.U3T + op->st.off_lo, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB,
                         (uint32_t)a.N3p));
     else
         mUlo = mU;
