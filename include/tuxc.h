@@ -198,7 +198,7 @@ int tx_batch_item_plan(const tx_plan* plan, int i, int* bx, int* nstage);
 void tx_plan_destroy(tx_plan* plan);
 
 /* Forces the expansion tile plan of a context: bx x planes per CTA (1..16) and nstage operand
- * load stages (1..4); 0, 0 restores the built-in choice.  Returns TX_ERR_INVALID_ARG outside
+ * load stages (1..6); 0, 0 restores the built-in choice.  Returns TX_ERR_INVALID_ARG outside
  * those ranges and TX_ERR_UNSUPPORTED_SHAPE if the plan does not fit SMEM / TMEM. */
 int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
 

@@ -106,7 +106,7 @@ extern "C" int tx_set_tile_plan(tx_ctx* c, int bx, int nstage) {
         c->tile_bx = c->tile_nstage = 0;
         return TX_OK;
     }
-    if (bx < 1 || nstage < 1 || nstage > 4) return fail(TX_ERR_INVALID_ARG, "bx >= 1 and nstage in 1..4");
+    if (bx < 1 || nstage < 1 || nstage > 6) return fail(TX_ERR_INVALID_ARG, "bx >= 1 and nstage in 1..6");
     if (c->prec == TX_PREC_FP32) return fail(TX_ERR_UNSUPPORTED_PRECISION, "tile plans apply to tensor-core precisions");
     if (!tc_plan_fits(c, bx, nstage)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "tile plan does not fit SMEM / TMEM");
     c->tile_bx = bx;

@@ -65,6 +65,48 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     }
 }
 
+// Non-blocking probe of a phase (mbarrier.test_wait never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for a phase that is expected within microseconds, by spinning on test_wait: a thread
+// suspended in try_wait can take a long time to resume after the phase completes, which
+// costs the latency-critical hand-offs between the MMA issuing warps.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity, int* err, int site) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+#pragma unroll 1
+        for (int i = 0; i < 64; ++i)
+            if (mbar_test_wait(bar, parity)) return true;
+        if (*(volatile int*)err != 0) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) {
+            if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
+            return false;
+        }
+    }
+}
+
+// Wait by a whole warp that issues on the phase: lane 0 spins on test_wait (32 lanes probing
+// one mbarrier serialize in the shared-memory pipe; a lane suspended in try_wait resumes
+// late), the result is broadcast and __syncwarp orders the other lanes after the phase.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int* err, int site) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait_spin(bar, parity, err, site);
+    ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+    __syncwarp();
+    return ok;
+}
+
 // For long waits by warps that have nothing else to do (an epilogue waiting for the whole
 // main loop): each probe suspends the thread for up to `hint_ns` unless the phase completes
 // first, so idle warps do not keep the shared-memory pipe busy with polls.

@@ -31,7 +31,7 @@ namespace tcc {
 
 using namespace tx::tc;
 
-constexpr int kMaxLoad = 4;
+constexpr int kMaxLoad = 6;
 constexpr int kMaxPlanes = 16;
 constexpr int kMaxYBuf = 4;        // stage-2 output buffers in TMEM (single-pass kernel)
 
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <bool S2TF32>
 __global__ void __launch_bounds__(kThreads, 1)
     k_consume_ts(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mA2,
-                 const __grid_constant__ CUtensorMap mA3f, ConsumeArgs a) {
+                 const __grid_constant__ CUtensorMap mA3f, const __grid_constant__ CUtensorMap mA3t, ConsumeArgs a) {
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto B3s = [&](int s) { return Zs(s) + a.z_bytes; };
 
     if (threadIdx.x == 0) {
-        // stage-3 commits (ybar, empty, phidone) come from each of the ns3 plane warps
+        // stage-3 commits (empty, phidone) come from each of the ns3 plane warps
         for (int s = 0; s < kMaxLoad; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], a.ns3);
@@ -558,12 +558,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = tmem_base;
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
+    // mu_t A_t3: na3f full 128-byte atoms (32 K each), then kt single K steps of 32-byte rows
+    // (the K tail, so that no box row is mostly zero fill)
+    const int na3f = a.ks3 / 4, kt = a.ks3 % 4;
 
     // The producer and MMA roles run on whole warps with uniform control flow; one elected lane
     // issues each TMA / tcgen05 instruction (see the _w helpers).
     if (warp == 8) {
         // ------------------------------ TMA producer ------------------------------
-        const int na2 = (a.ks2 + 3) / 4, na3 = (a.ks3 + 3) / 4;   // 128-byte atoms along K
+        const int na2 = (a.ks2 + 3) / 4;   // 128-byte atoms along K
         int issued = 0;
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
@@ -587,7 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tma_load_3d_w(Zs(s) + k * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s], k * AK2,
                                   (x0 + p) * a.r3, zdep);
             }
-            for (int k = 0; k < na3; ++k) tma_load_3d_w(B3s(s) + k * b3_atom, &mA3f, &full_bar[s], k * 32, 0, tt);
+            for (int k = 0; k < na3f; ++k) tma_load_3d_w(B3s(s) + k * b3_atom, &mA3f, &full_bar[s], k * 32, 0, tt);
+            for (int j = 0; j < kt; ++j)
+                tma_load_3d_w(B3s(s) + na3f * b3_atom + (uint32_t)j * a.n3p * 32u, &mA3t, &full_bar[s], na3f * 32 + 8 * j, 0,
+                              tt);
         }
         if (!ok)
             for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
@@ -599,8 +605,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
             bool w = mbar_wait(&full_bar[t % NL], (t / NL) & 1, a.err, 42);
-            // Y buffer t % nyb was last read by stage 3 of term t - nyb (every plane warp)
-            if (w && t >= NYB) w = mbar_wait(&ybar[t % NYB], ((t - NYB) / NYB) & 1, a.err, 43);
+            // Y buffer t % nyb was last read by stage 3 of term t - nyb.  With nyb == nload that
+            // is the stage-3 term whose completion freed this load stage, which the producer
+            // waited for before loading term t: the full barrier already covers it.
+            if (w && NYB != NL && t >= NYB) w = mbar_wait(&ybar[t % NYB], ((t - NYB) / NYB) & 1, a.err, 43);
             if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
             tc_fence_after();
             const int s = t % NL;
@@ -638,17 +646,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const int s = t % NL;
                 const uint64_t b3 = d0 + (smem_u32(B3s(s)) >> 4);
+                const uint64_t b3t = sdesc_sw32(0) + (smem_u32(B3s(s) + na3f * b3_atom) >> 4);
                 const uint32_t tY = tmem + (uint32_t)(t % NYB) * a.y_cols;
                 const uint32_t acc0 = t > 0 ? 1u : 0u;
                 for (int p = warp; p < BX; p += a.ns3)
                     for (int i = 0; i < a.nY; ++i) {
                         const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
                         const uint32_t d = tPhi + (uint32_t)((p * a.nY + i) * a.n3p);
-                        for (int k = 0; k < a.ks3; ++k)
+                        for (int k = 0; k < 4 * na3f; ++k)
                             mma_ts_tf32_w(d, aT + 8u * k, b3 + (uint32_t)(k >> 2) * (b3_atom >> 4) + (uint32_t)(k & 3) * 2u,
                                           id3, k > 0 ? 1u : acc0);
+                        for (int j = 0; j < kt; ++j)
+                            mma_ts_tf32_w(d, aT + 8u * (4 * na3f + j), b3t + (uint32_t)j * (uint32_t)a.n3p * 2u, id3,
+                                          (na3f > 0 || j > 0) ? 1u : acc0);
                     }
-                mma_commit_w(&ybar[t % NYB]);
+                if (NYB != NL) mma_commit_w(&ybar[t % NYB]);
                 mma_commit_w(&empty_bar[s]);
             }
             mma_commit_w(&phidone);
@@ -691,7 +703,7 @@ struct ConsumePlan {
     size_t smem;
 };
 
-// Single-pass plan: bx planes, nload load stages, 4 (else 3, 2) stage-2 output buffers in TMEM
+// Single-pass plan: bx planes, nload load stages and as many stage-2 output buffers in TMEM
 static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* p) {
     const int MK2 = tf32 ? 8 : 16;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
@@ -714,21 +726,25 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->y_cols = (uint32_t)(p->nY * p->ycol_tile);
     p->nT3 = bx * p->nY;
     const uint32_t phi = (uint32_t)(p->nT3 * p->n3p);
-    p->nyb = tcc::kMaxYBuf;
+    // one Y buffer per load stage when TMEM allows (the kernel then needs no Y-buffer barrier)
+    p->nyb = std::min(nload, tcc::kMaxYBuf);
     while (p->nyb > 2 && p->nyb * p->y_cols + phi > 512) --p->nyb;
     const uint32_t cols = p->nyb * p->y_cols + phi;
     if (cols > 512) return false;
     p->tmem_cols = 32;
     while (p->tmem_cols < cols) p->tmem_cols <<= 1;
-    const int na2 = (p->ks2 + 3) / 4, na3 = (p->ks3 + 3) / 4;   // 128-byte atoms along K
-    p->ya_rows = (uint32_t)(p->nY * 128);
+    const int na2 = (p->ks2 + 3) / 4;          // 128-byte atoms along K
+    // The A_t2 tile holds the n2p loaded rows; a 128-row MMA tile reads past them into the Z tile
+    // that follows (garbage rows only reach TMEM lanes that are never read), and the smem
+    // allocation keeps 16 KB spare after the last stage for the same reason.
+    p->ya_rows = (uint32_t)p->n2p;
     p->z_rows = (uint32_t)p->ycol_tile;         // rows every stage-2 MMA may read
     p->ya = (uint32_t)na2 * p->ya_rows * 128u;
     p->zb = (uint32_t)na2 * p->z_rows * 128u;
-    p->b3 = (uint32_t)na3 * p->n3p * 128u;
+    p->b3 = (uint32_t)(p->ks3 / 4) * p->n3p * 128u + (uint32_t)(p->ks3 % 4) * p->n3p * 32u;
     p->load = (p->ya + p->zb + p->b3 + 1023) & ~1023u;
     p->nload = nload;
-    p->smem = std::max((size_t)p->load * nload, (size_t)tcc::kEpiBytes) + 1024;
+    p->smem = std::max((size_t)p->load * nload + 16384, (size_t)tcc::kEpiBytes) + 1024;
     return p->smem <= 226 * 1024;
 }
 
@@ -807,7 +823,7 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
             for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx) {
                 ConsumePlan p;
                 if (!plan_ts(c, tf32, bx, nl, &p)) continue;
-                const double score = 1.0 / ts_cost(p) * (p.nyb >= 3 ? 1.0 : 0.85) * (nl >= 3 ? 1.0 : 0.9);
+                const double score = 1.0 / ts_cost(p) * (0.8 + 0.05 * nl);
                 if (score > best_score * 1.0001) {
                     best_score = score;
                     *best = p;
@@ -911,9 +927,9 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     if (p.ts) {
         a.gs = p.gs; a.ycol_tile = p.ycol_tile; a.ns3 = std::min(p.bx, 8);
         // bytes per stage (128-byte rows; zero-filled parts count): A_t2, Z planes, mu_t A_t3
-        const int na2 = (p.ks2 + 3) / 4, na3 = (p.ks3 + 3) / 4;
-        a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3 + na3 * p.n3p));
-        CUtensorMap mZ, mA2, mA3f;
+        const int na2 = (p.ks2 + 3) / 4;
+        a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3 + (p.ks3 / 4) * p.n3p) + 32 * (p.ks3 % 4) * p.n3p);
+        CUtensorMap mZ, mA2, mA3f, mA3t;
         const uint32_t AK2 = op->tf32 ? 32 : 64;   // elements per 128-byte box row
         // K extents are the zero-padded row lengths (whole 32-byte sectors)
         const int l2 = ldk(r2, eb);
@@ -921,13 +937,15 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
                         AK2, (uint32_t)r3));
         TX_TRY(make_map(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, AK2, (uint32_t)p.n2p));
         TX_TRY(make_map(&mA3f, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 32, (uint32_t)p.n3p));
+        TX_TRY(make_map_sw(&mA3t, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 8, (uint32_t)p.n3p,
+                           CU_TENSOR_MAP_SWIZZLE_32B));
         const int ps = prof_begin("tc_consume", s);
         if (op->tf32) {
             cudaFuncSetAttribute(tcc::k_consume_ts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, a);
+            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, mA3t, a);
         } else {
             cudaFuncSetAttribute(tcc::k_consume_ts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, a);
+            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, mA3t, a);
         }
         prof_end(ps, s);
         TX_LAUNCHED();

@@ -49,7 +49,7 @@ def test_batch_equals_individual_calls_and_graph_replay(prec, tmp_path):
     assert table.exists() and len(table.read_text().splitlines()) >= 1
     for i in range(len(systems)):
         bx, ns = plan.item_plan(i)
-        assert bx >= 1 and 1 <= ns <= 4
+        assert bx >= 1 and 1 <= ns <= 6
     for o in plan.outputs():
         o.zero_()
     plan.launch()
@@ -100,7 +100,7 @@ def test_forced_tile_plans_agree():
     base = P.tx_exchange_apply(ctx, psi).cpu().numpy()
     tried = 0
     for bx in (1, 2, 3, 5, 8, 13):
-        for ns in (1, 2, 3, 4):
+        for ns in (1, 2, 3, 4, 5, 6):
             try:
                 P.tx_set_tile_plan(ctx, bx, ns)
             except P.TuckerExchangeError as e:
