@@ -202,6 +202,13 @@ void tx_plan_destroy(tx_plan* plan);
  * those ranges and TX_ERR_UNSUPPORTED_SHAPE if the plan does not fit SMEM / TMEM. */
 int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
 
+/* Split precisions (TF32x3, BF16x3): phi = sum_t mu_t G x_d A_td (final contraction of the
+ * expansion) is accumulated on the tensor core in chunks of `terms` Gaussian terms, each chunk
+ * folded into the outputs in float32.  The tensor core rounds its float32 accumulator at every
+ * MMA, so shorter chunks give a smaller error and cost one extra fold pass per chunk.  0 restores
+ * the default (5 terms).  No effect on the single-pass precisions.  TX_ERR_INVALID_ARG if < 0. */
+int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
+
 /*
  * tx_exchange_apply_static -- out = K psi_occ (targets = the occupied block), like
  * tx_exchange_apply with psi_tgt NULL, for callers that cannot let a library allocate device

@@ -100,6 +100,13 @@ static void plan_free(tx_plan* p) {
     delete p;
 }
 
+extern "C" int tx_set_accumulation_chunk(tx_ctx* c, int terms) {
+    if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
+    if (terms < 0) return fail(TX_ERR_INVALID_ARG, "terms must be >= 0");
+    c->acc_chunk = terms;
+    return TX_OK;
+}
+
 extern "C" int tx_set_tile_plan(tx_ctx* c, int bx, int nstage) {
     if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
     if (bx == 0 && nstage == 0) {

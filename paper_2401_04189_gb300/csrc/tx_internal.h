@@ -107,6 +107,7 @@ struct tx_ctx {
     int ebatch_cap;
     cudaStream_t last_stream;
     int tile_bx, tile_nstage;   // forced expansion tile plan (0 = built-in choice)
+    int acc_chunk;              // split precisions: Gaussian terms per phi accumulation chunk (0 = default)
 };
 
 namespace tx {

@@ -33,6 +33,7 @@ struct TcGemmArgs {
     int c_type;
     float alpha;
     uint32_t tmem_cols;
+    int nacc;                // TMEM accumulators, one per K atom in turn (summed in float32)
     int stages;
     int* err;
 };

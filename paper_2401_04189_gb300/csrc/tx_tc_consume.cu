@@ -41,6 +41,7 @@ struct ConsumeArgs {
     int n1, n2, n3, r2, r3, nt;
     int bx, R, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, gs, ycol_tile, ns3;
     int nload, na3, nyb;
+    int chunk;                 // split kernel: Gaussian terms per TMEM accumulation chunk
     uint32_t ya_rows, z_rows;                          // rows of the stage-2 A tile (A_t2) and B tile (Z)
     uint32_t ya_bytes, z_bytes, b3_bytes, a3_bytes;    // one hi copy of each operand tile
     uint32_t load_bytes, stage_tx, a3_off;             // load stage stride, bytes per stage, A3 buffers
@@ -214,6 +215,63 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
     return e;
 }
 
+// Fold of phi into the outputs and the energy sum without shared memory (the pipeline
+// buffers are still in use): each thread takes its TMEM lane, i.e. one grid row (x, y), and
+// 16 z columns per load; the two warps of a lane quadrant take alternate column blocks.
+template <typename Rows>
+__device__ __forceinline__ double consume_fold_direct(const ConsumeArgs& a, const PairRec& rec, uint32_t tPhi,
+                                                      int nTiles, int warp, int lane, Rows rows) {
+    const int q = warp & 3, h = warp >> 2;
+    const long N3 = (long)a.n1 * a.n2 * a.n3;
+    const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
+    const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
+    float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
+    float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
+    const float* sa = a.SA + (long)rec.ia * N3;
+    const float* sb = a.SB + (long)rec.ib * N3;
+    const bool en = (a.flags & EPI_ENERGY) != 0;
+    const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
+    double e = 0.0;
+    for (int jt = 0; jt < nTiles; ++jt) {
+        int x = 0, y = 0;
+        const bool in = rows(jt, q * 32 + lane, x, y);
+        const float wxy = in ? a.w1[x] * a.w2[y] : 0.f;
+        const int rowbase = in ? (x * a.n2 + y) * a.n3 : 0;
+        for (int c = h; c < a.n3p / 16; c += 2) {
+            uint32_t r[16];
+            tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + 16 * c), r);
+            tmem_ld_wait();
+            if (!in) continue;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+                const int z = 16 * c + j;
+                if (z >= a.n3) break;                   // n3 % 4 == 0
+                const int idx = rowbase + z;
+                const float4 phi = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                const float4 w3 = *(const float4*)(a.w3 + z);
+                const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+                float4 f = phi;
+                if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+                if (o0) {
+                    const float4 m0 = __ldg((const float4*)(mul0 + idx));
+                    atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+                }
+                if (o1) {
+                    const float4 m1 = __ldg((const float4*)(mul1 + idx));
+                    atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+                }
+                if (en) {
+                    const float4 va = __ldg((const float4*)(sa + idx)), vb = __ldg((const float4*)(sb + idx));
+                    e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
+                         (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
+                }
+            }
+        }
+    }
+    return e;
+}
+
 template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_consume(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mZlo,
@@ -224,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int CV = 16 / ES;              // values per 16-byte chunk
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], a3full[2], a3free[2], phidone;
-    __shared__ uint64_t yfull, yfree;
+    __shared__ uint64_t yfull, yfree, chunkdone, phifree;
     __shared__ uint32_t tmem_base;
     __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -233,6 +291,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
     const int NL = a.nload, NA = a.na3, BX = a.bx;
+    // phi is accumulated in TMEM over chunks of C terms and folded into the outputs after each
+    // chunk: the tensor core rounds its float32 accumulator at every MMA, and restarting it
+    // bounds that error by the chunk length (the folds add in float32, rounding to nearest)
+    const int C = a.chunk > 0 ? a.chunk : a.nt;
     // Gaussian terms in the order of the exponential sum (theta ascending: wide terms first).
     // Measured against the float64 oracle, this order gives about half the split-precision
     // error of the reverse order: the tensor core's float32 accumulator rounds each partial
@@ -257,6 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&yfull, 1);
         mbar_init(&yfree, 2 * a.nq);
         mbar_init(&phidone, 1);
+        mbar_init(&chunkdone, 1);
+        mbar_init(&phifree, 8);
         fence_barrier_init();
     }
     // the stage-3 operand: rows past the slab's last (x, y) are never written and must be finite
@@ -360,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < a.nT3; ++j) {
                     uint64_t ad = a3 + (uint32_t)j * 256u, bd = b3;
                     for (int k = 0; k < a.ks3; ++k) {
-                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, (t > 0 || k > 0) ? 1u : 0u);
+                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, (t % C > 0 || k > 0) ? 1u : 0u);
                         if constexpr (SPLIT) {
                             mma_ss<TF32>(tPhi + j * a.n3p, ad, bd + b3_lo, id3, 1u);
                             mma_ss<TF32>(tPhi + j * a.n3p, ad + a3_lo, bd, id3, 1u);
@@ -385,9 +449,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ++t2;
                     prog = true;
                 }
-                if (t3 < t2 && mbar_try_wait(&a3full[t3 % NA], (t3 / NA) & 1)) {
+                // a new accumulation chunk starts once the previous one has been folded out of TMEM
+                if (t3 < t2 && mbar_try_wait(&a3full[t3 % NA], (t3 / NA) & 1) &&
+                    (t3 % C != 0 || t3 == 0 || mbar_try_wait(&phifree, (t3 / C - 1) & 1))) {
                     tc_fence_after();
                     stage3(t3);
+                    if ((t3 + 1) % C == 0 && t3 + 1 < a.nt) mma_commit(&chunkdone);
                     ++t3;
                     prog = true;
                 }
@@ -418,6 +485,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3, h = warp >> 2;
         const bool active = q < a.nq;
         bool ok = true;
+        double e = 0.0;
+        auto rows_of = [&](int jt, int r, int& x, int& y) {
+            const int m3 = jt * 128 + r;
+            const int xl = m3 / a.n2;
+            y = m3 - xl * a.n2;
+            x = x0 + xl;
+            return m3 < a.R && x < a.n1;
+        };
         for (int t = 0; t < a.nt && ok; ++t) {
             const int b = t % NA;
             if (t >= NA && !mbar_wait(&a3free[b], ((t - NA) / NA) & 1, a.err, 36)) { ok = false; break; }
@@ -467,18 +542,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&a3full[b]);
+            // end of an accumulation chunk: fold phi into the outputs, then free the accumulator
+            if ((t + 1) % C == 0 && t + 1 < a.nt) {
+                if (!mbar_wait(&chunkdone, (t / C) & 1, a.err, 38)) { ok = false; break; }
+                tc_fence_after();
+                e += consume_fold_direct(a, rec, tPhi, a.nT3, warp, lane, rows_of);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&phifree);
+            }
         }
         // ------------------------------ epilogue ------------------------------
-        double e = 0.0;
         if (ok && mbar_wait_idle(&phidone, 0, a.err, 37) && *(volatile int*)a.err == 0) {
             tc_fence_after();
-            e = consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, [&](int jt, int r, int& x, int& y) {
-                const int m3 = jt * 128 + r;
-                const int xl = m3 / a.n2;
-                y = m3 - xl * a.n2;
-                x = x0 + xl;
-                return m3 < a.R && x < a.n1;
-            });
+            e += consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, rows_of);
         }
         if (a.flags & EPI_ENERGY) {
             for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -696,6 +773,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ======================================================================================
 // host side: tile plan and launch
 // ======================================================================================
+// Gaussian terms per phi accumulation chunk of the split precisions (see k_consume)
+constexpr int kDefaultSplitChunk = 5;
+
 struct ConsumePlan {
     bool ts;                 // single-pass kernel (stage 3 from TMEM) instead of the converter kernel
     int bx, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, nload, na3, nyb, gs, ycol_tile;
@@ -920,6 +1000,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     a.SA = SA; a.SB = SB; a.MUL0 = MUL0; a.MUL1 = MUL1; a.OUT0 = OUT0; a.OUT1 = OUT1;
     a.w1 = c->f_w[0]; a.w2 = c->f_w[1]; a.w3 = c->f_w[2];
     a.flags = flags; a.epart = epart; a.err = c->d_err;
+    a.chunk = c->acc_chunk > 0 ? c->acc_chunk : (op->split ? kDefaultSplitChunk : T);
     a.emul = (SA == MUL1 && SB == MUL0 && emul) ? 1 : 0;
     const int eb = op->esize;
     const uint32_t MK = op->tf32 ? 8 : 16;

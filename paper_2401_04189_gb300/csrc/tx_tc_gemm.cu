@@ -118,11 +118,15 @@ __global__ void __launch_bounds__(128, 1)
             // (each lo copy sits a_bytes + b_bytes after its hi copy)
             uint64_t ad = sdesc_sw128(a_addr), bd = sdesc_sw128(b_addr);
             const uint64_t lo = (uint64_t)((a_bytes + b_bytes) >> 4);
+            // K atom kb accumulates into accumulator kb % nacc: the tensor core rounds its float32
+            // accumulator at every MMA, so split precisions spread K over several accumulators
+            // and the epilogue adds them in float32
+            const uint32_t dacc = tmem + (uint32_t)((kb % g.nacc) * BN);
             for (int k = 0; k < nsteps; ++k) {
-                mma_ss<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_ss<TF32>(dacc, ad, bd, idesc, (kb >= g.nacc || k > 0) ? 1u : 0u);
                 if constexpr (SPLIT) {
-                    mma_ss<TF32>(tmem, ad, bd + lo, idesc, 1u);
-                    mma_ss<TF32>(tmem, ad + lo, bd, idesc, 1u);
+                    mma_ss<TF32>(dacc, ad, bd + lo, idesc, 1u);
+                    mma_ss<TF32>(dacc, ad + lo, bd, idesc, 1u);
                 }
                 ad += 2;
                 bd += 2;
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(128, 1)
     // ---------------- epilogue: 4 warps, one TMEM lane (= output row) per thread ----------------
     const bool ok = mbar_wait_idle(&done_bar, 0, g.err, 14);
     tc_fence_after();
+    const int nacc_used = min(g.nacc, nk);     // accumulators that received a K atom
     const long boff = (long)b1 * g.c_b1 + (long)b2 * g.c_b2;
     auto row_off = [&](int m) { return boff + (long)(m / g.rdiv) * g.c_mh + (long)(m % g.rdiv) * g.c_m; };
     auto col_off = [&](int n) { return (long)(n / g.cdiv) * g.c_nh + (long)(n % g.cdiv) * g.c_n; };
@@ -147,13 +152,22 @@ __global__ void __launch_bounds__(128, 1)
         int nq = n0 / g.cdiv, nr = n0 % g.cdiv;     // column split tracked incrementally
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
+            float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            for (int ac = 1; ac < nacc_used; ++ac) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ac * BN + c0), r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int n = n0 + c0 + j;
                 if (m < g.M && n < g.N)
-                    store_out(g, base + (long)nq * g.c_nh + (long)nr * g.c_n, g.alpha * __uint_as_float(r[j]));
+                    store_out(g, base + (long)nq * g.c_nh + (long)nr * g.c_n, g.alpha * v[j]);
                 if (++nr == g.cdiv) {
                     nr = 0;
                     ++nq;
@@ -179,6 +193,18 @@ __global__ void __launch_bounds__(128, 1)
                 if (c < nck)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) stg[lane * 65 + 16 * c + j] = __uint_as_float(r[c][j]);
+            for (int ac = 1; ac < nacc_used; ++ac) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c < nck)
+                        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ac * BN + cb + 16 * c), r[c]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c < nck)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) stg[lane * 65 + 16 * c + j] += __uint_as_float(r[c][j]);
+            }
             __syncwarp();
             // this lane's two columns: offsets computed once per chunk
             const int cc0 = lane, cc1 = 32 + lane;
@@ -292,8 +318,10 @@ int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf
         g.BN -= 16;
         stage = (size_t)(split ? 2 : 1) * (128 * 128 + (size_t)g.BN * 128);
     }
-    g.tmem_cols = tmem_cols_for(g.BN);
     const int nk_atoms = (g.K + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64);
+    // split precisions: up to 4 accumulators along K (TMEM permitting), summed in float32
+    g.nacc = split ? std::max(1, std::min({nk_atoms, 4, 512 / g.BN})) : 1;
+    g.tmem_cols = tmem_cols_for(g.nacc * g.BN);
     g.stages = (int)std::min<size_t>({(size_t)tcg::kMaxStages, (budget - 1024) / stage, (size_t)nk_atoms});
     // the epilogue stages 4 warps x 32 rows x 65 floats in the (then idle) pipeline buffers
     const size_t smem = std::max(stage * g.stages, (size_t)4 * 32 * 65 * 4) + 1024;

@@ -11,6 +11,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <string>
 
 #include "tx_tc_common.cuh"
@@ -34,6 +36,7 @@ struct ProjArgs {
     size_t s1_pair;          // elements per pair
     size_t s1_lo;            // element offset of the lo part
     uint32_t tmem_cols;
+    int nacc;                // accumulators along K (split precisions), summed in float32
     int* err;
 };
 
@@ -162,11 +165,13 @@ __global__ void __launch_bounds__(128, 1)
             const int nsteps = (min(a.n3 - kb * ZB, ZB) + kMmaK - 1) / kMmaK;
             // descriptors advance by adds (32 bytes per K step = 2 in the address / 16 field)
             uint64_t ad = sdesc_sw128(ra), bd = sdesc_sw128(ba), al = sdesc_sw128(rl), bdl = sdesc_sw128(bl);
+            // K chunk kb accumulates into accumulator kb % nacc (added in float32 by the epilogue)
+            const uint32_t dacc = tmem + (uint32_t)((kb % a.nacc) * a.N3p);
             for (int k = 0; k < nsteps; ++k) {
-                mma_ss<TF32>(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_ss<TF32>(dacc, ad, bd, idesc, (kb >= a.nacc || k > 0) ? 1u : 0u);
                 if constexpr (SPLIT) {
-                    mma_ss<TF32>(tmem, ad, bdl, idesc, 1u);
-                    mma_ss<TF32>(tmem, al, bd, idesc, 1u);
+                    mma_ss<TF32>(dacc, ad, bdl, idesc, 1u);
+                    mma_ss<TF32>(dacc, al, bd, idesc, 1u);
                 }
                 ad += 2;
                 bd += 2;
@@ -193,16 +198,26 @@ __global__ void __launch_bounds__(128, 1)
         const bool valid = x < a.n1;
         const size_t base = (size_t)pl * a.s1_pair + (size_t)x * a.ld_y + y;
         const size_t gstride = (size_t)a.n1 * a.ld_y;
+        const int nacc_used = min(a.nacc, nk);
         for (int c0 = 0; c0 < a.N3p; c0 += 16) {
             uint32_t r[16];
+            float acc[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = __uint_as_float(r[j]);
+            for (int ac = 1; ac < nacc_used; ++ac) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ac * a.N3p + c0), r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(r[j]);
+            }
             if (!valid) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int g = c0 + j;
                 if (g >= a.r3) break;
-                const float v = __uint_as_float(r[j]);
+                const float v = acc[j];
                 const size_t o = base + (size_t)g * gstride;
                 if constexpr (TF32) {
                     const float h = tf32_hi(v);
@@ -237,7 +252,12 @@ int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const
     a.S1 = S1;
     a.s1_pair = sc.s1;
     a.s1_lo = (size_t)np * sc.s1;          // lo part follows the batch's hi part
-    a.tmem_cols = a.N3p <= 32 ? 32 : (a.N3p <= 64 ? 64 : (a.N3p <= 128 ? 128 : 256));
+    {
+        const int nk = (n3 + (op->tf32 ? 32 : 64) - 1) / (op->tf32 ? 32 : 64);
+        a.nacc = op->split ? std::max(1, std::min({nk, 4, 512 / a.N3p})) : 1;
+        const int cols = a.nacc * a.N3p;
+        a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
+    }
     a.err = c->d_err;
     if (a.N3p > 256) return fail(TX_ERR_UNSUPPORTED_SHAPE, "tensor-core projection needs r3 <= 256");
     const int ZB = op->tf32 ? 32 : 64;

@@ -181,3 +181,25 @@ def test_tensor_core_precisions_reject_unaligned_rows(prec):
         P.Context.from_system(s, precision=prec)
     assert ei.value.status == -9
     P.Context.from_system(s, precision="fp32")          # the float32 path takes any shape
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_accumulation_chunk_bounds_the_accumulator_error(prec):
+    """Shorter accumulation chunks of the final contraction do not increase the error (the
+    tensor core's float32 accumulator is restarted and the chunks are added in float32), and
+    every chunk length gives the same result within the precision's tolerance."""
+    P = _P()
+    s = W.config_small()
+    S = O.Setup.from_system(s)
+    ref = O.exchange_apply(s.psi, S)
+    errs = {}
+    for ch in (0, 1000, 7, 1):
+        ctx = P.Context.from_system(s, precision=prec)
+        P.tx_set_accumulation_chunk(ctx, ch)
+        got = P.tx_exchange_apply(ctx, to_gpu(s.psi)).cpu().numpy()
+        ctx.check_device_error()
+        errs[ch] = rel(got, ref)
+        assert errs[ch] < W_TOL[prec], (ch, errs[ch])
+    assert errs[1] <= errs[1000] * 1.02
+    with pytest.raises(P.TuckerExchangeError):
+        P.tx_set_accumulation_chunk(P.Context.from_system(s, precision=prec), -1)
