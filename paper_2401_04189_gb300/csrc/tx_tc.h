@@ -34,6 +34,7 @@ struct TcGemmArgs {
     float alpha;
     uint32_t tmem_cols;
     int nacc;                // TMEM accumulators, one per K atom in turn (summed in float32)
+    int vec;                 // set by the launcher: rows are contiguous and 16-byte aligned
     int stages;
     int* err;
 };

@@ -27,6 +27,31 @@ using namespace tx::tc;
 constexpr int kMaxStages = 4;
 constexpr int kBM = 128;
 
+// 16-byte store of VE consecutive outputs (8 bf16 or 4 float), hi and, for split types, lo
+__device__ __forceinline__ void store_vec(const TcGemmArgs& g, long o, const float* v) {
+    if (g.c_type == TC_OUT_F32 || g.c_type == TC_OUT_F32_SPLIT) {
+        float h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) h[e] = g.c_type == TC_OUT_F32 ? v[e] : tf32_hi(v[e]);
+        *(float4*)((float*)g.C + o) = make_float4(h[0], h[1], h[2], h[3]);
+        if (g.c_type == TC_OUT_F32_SPLIT)
+            *(float4*)((float*)g.C + o + g.c_lo) = make_float4(tf32_hi(v[0] - h[0]), tf32_hi(v[1] - h[1]),
+                                                               tf32_hi(v[2] - h[2]), tf32_hi(v[3] - h[3]));
+    } else {
+        uint32_t w[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            w[e] = *(const uint32_t*)&hv;
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+            l[e] = *(const uint32_t*)&lv;
+        }
+        *(uint4*)((__nv_bfloat16*)g.C + o) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (g.c_type == TC_OUT_BF16_SPLIT) *(uint4*)((__nv_bfloat16*)g.C + o + g.c_lo) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 __device__ __forceinline__ void store_out(const TcGemmArgs& g, long o, float v) {
     if (g.c_type == TC_OUT_F32) {
         ((float*)g.C)[o] = v;
@@ -206,6 +231,25 @@ __global__ void __launch_bounds__(128, 1)
                         for (int j = 0; j < 16; ++j) stg[lane * 65 + 16 * c + j] += __uint_as_float(r[c][j]);
             }
             __syncwarp();
+            if (g.vec) {
+                // contiguous 16-byte aligned rows: each lane stores one vector of one row
+                const int VE = (g.c_type == TC_OUT_F32 || g.c_type == TC_OUT_F32_SPLIT) ? 4 : 8;
+                const int lpr = 64 / VE, rpp = 32 / lpr;            // lanes per row, rows per pass
+                const int sub = lane / lpr, cv = (lane % lpr) * VE;
+                for (int rr0 = 0; rr0 < 32; rr0 += rpp) {
+                    const int rr = rr0 + sub;
+                    const long base = __shfl_sync(0xffffffffu, my_row, rr);
+                    const int n = n0 + cb + cv;
+                    if (m0 + warp * 32 + rr < g.M && cb + cv < BN && n < g.N) {
+                        float v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] = e < VE ? g.alpha * stg[rr * 65 + cv + e] : 0.f;
+                        store_vec(g, base + n, v);
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
             // this lane's two columns: offsets computed once per chunk
             const int cc0 = lane, cc1 = 32 + lane;
             const int n_0 = n0 + cb + cc0, n_1 = n0 + cb + cc1;
@@ -322,6 +366,13 @@ int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf
     // split precisions: up to 4 accumulators along K (TMEM permitting), summed in float32
     g.nacc = split ? std::max(1, std::min({nk_atoms, 4, 512 / g.BN})) : 1;
     g.tmem_cols = tmem_cols_for(g.nacc * g.BN);
+    {
+        // vector stores: contiguous columns, no column split, every row start and the lo copy
+        // 16-byte aligned, whole vectors
+        const long ve = (g.c_type == TC_OUT_F32 || g.c_type == TC_OUT_F32_SPLIT) ? 4 : 8;
+        g.vec = g.c_n == 1 && g.cdiv >= g.N && g.c_m != 1 && ((uintptr_t)g.C % 16) == 0 && g.c_m % ve == 0 &&
+                g.c_mh % ve == 0 && g.c_b1 % ve == 0 && g.c_b2 % ve == 0 && g.c_lo % ve == 0 && g.N % ve == 0;
+    }
     g.stages = (int)std::min<size_t>({(size_t)tcg::kMaxStages, (budget - 1024) / stage, (size_t)nk_atoms});
     // the epilogue stages 4 warps x 32 rows x 65 floats in the (then idle) pipeline buffers
     const size_t smem = std::max(stage * g.stages, (size_t)4 * 32 * 65 * 4) + 1024;
