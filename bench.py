@@ -318,6 +318,13 @@ def dtype_name(prec):
     return {"fp32": "f32", "bf16": "bf16", "tf32": "tf32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}.get(prec, prec)
 
 
+# DRAM bytes (read + write) per distinct pair of the dominant kernel, from one ncu capture of
+# the current kernel on the same block with 8 orbitals (36 pairs in one launch), scaled by the
+# pairs a bench launch processes (traffic grows in proportion to pairs).  Source and command:
+# profiles/k_consume_ts_pt8_bf16.md.  None where no capture of the current kernel exists.
+DRAM_BYTES_PER_PAIR = {("tc_consume", "bf16"): (709.594112e6 + 83.000064e6) / 36}
+
+
 def roofline(dom, prof, n, r, T, N, steps, prec, peaks, ck):
     """Achieved algorithmic FLOP/s of the dominant kernel over its live launch time."""
     if dom is None:
@@ -345,8 +352,11 @@ def roofline(dom, prof, n, r, T, N, steps, prec, peaks, ck):
         bound = "tensor"
         src = ("measured sustained bf16" if peaks else "fallback bf16") + (
             " x 0.5 (nominal tf32/bf16 ratio)" if ratio != 1.0 else "")
+    bpp = DRAM_BYTES_PER_PAIR.get((dom, prec))
+    traffic = bpp * unique * steps / k if bpp else None     # bytes per launch
     return dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=None, launches=k, avg_launch_ms=kms / k, peak_source=src)
+                traffic=traffic, traffic_unit="bytes per launch (ncu dram read + write, scaled)" if traffic else None,
+                launches=k, avg_launch_ms=kms / k, peak_source=src)
 
 
 if __name__ == "__main__":

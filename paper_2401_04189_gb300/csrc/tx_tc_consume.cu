@@ -187,6 +187,10 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
         if (blk + 1 < nblk) cp_async_wait<1>(); else cp_async_wait<0>();
         __syncwarp();
         const float4* lb = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
+        // The energy terms of a block (at most 32 per thread) are summed in float32 and the block
+        // sum is added in float64: this GPU runs float64 arithmetic at a small fraction of the
+        // float32 rate, and a float64 multiply-add per grid point used to dominate this loop.
+        float eb = 0.f;
         // lanes 0-15 take row rr, lanes 16-31 row rr + 1; four consecutive z per lane
 #pragma unroll 2
         for (int it = 0; it < 8; ++it) {
@@ -206,10 +210,11 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
             if (en) {
                 const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
                 const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
-                e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
-                     (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
+                eb += wv.x * va.x * vb.x * phi.x + wv.y * va.y * vb.y * phi.y + wv.z * va.z * vb.z * phi.z +
+                      wv.w * va.w * vb.w * phi.w;
             }
         }
+        e += (double)eb;
         __syncwarp();
     }
     return e;
@@ -242,6 +247,7 @@ __device__ __forceinline__ double consume_fold_direct(const ConsumeArgs& a, cons
             tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + 16 * c), r);
             tmem_ld_wait();
             if (!in) continue;
+            float eb = 0.f;
 #pragma unroll
             for (int j = 0; j < 16; j += 4) {
                 const int z = 16 * c + j;
@@ -263,10 +269,11 @@ __device__ __forceinline__ double consume_fold_direct(const ConsumeArgs& a, cons
                 }
                 if (en) {
                     const float4 va = __ldg((const float4*)(sa + idx)), vb = __ldg((const float4*)(sb + idx));
-                    e += (double)wv.x * va.x * vb.x * phi.x + (double)wv.y * va.y * vb.y * phi.y +
-                         (double)wv.z * va.z * vb.z * phi.z + (double)wv.w * va.w * vb.w * phi.w;
+                    eb += wv.x * va.x * vb.x * phi.x + wv.y * va.y * vb.y * phi.y + wv.z * va.z * vb.z * phi.z +
+                          wv.w * va.w * vb.w * phi.w;
                 }
             }
+            e += (double)eb;     // float32 within a 16-column block, float64 across blocks
         }
     }
     return e;
