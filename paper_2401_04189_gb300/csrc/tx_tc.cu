@@ -79,6 +79,7 @@ bool tc_supported(const tx_ctx* c, std::string* why) {
 void tc_release(tx_ctx* c) {
     if (!c->tc) return;
     cudaFree(c->tc->buf);
+    if (c->tc->img) cudaFree(c->tc->img);
     delete c->tc;
     c->tc = nullptr;
 }
@@ -144,6 +145,7 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
                                                                     op->st.A3f, 0);
         TX_LAUNCHED();
     }
+    if (!op->split) TX_TRY(tc_build_operand_image(c, s));
     return TX_OK;
 }
 

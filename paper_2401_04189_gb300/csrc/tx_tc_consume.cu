@@ -6,8 +6,9 @@
 //     phi[(x,y)][z] += sum_g Y_t[(x,y)][g] (mu_t A_t3)[z][g]        stage 3 -> TMEM (all t)
 //   out0[o0] -= mul0[m0] * phi,  out1[o1] -= mul1[m1] * phi,  energy += ew * w * psi_a psi_b phi
 //
-// Z_t = G x1 A_t1 comes from the first-mode GEMM.  Stage 2 puts y on the TMEM lanes and g on
-// the columns, so each converter lane already holds one row (x, y) of the K-major stage-3
+// Z_t = G x1 A_t1 comes from the first-mode GEMM.  The split precisions run k_consume below
+// (the single-pass precisions run k_consume_ts, described at its definition).  Stage 2 puts y
+// on the TMEM lanes and g on the columns, so each converter lane already holds one row (x, y) of the K-major stage-3
 // operand: it rounds the row to the operand type and writes it with 16-byte stores.  Each x
 // plane has its own TMEM columns and its own full / free barriers, so the MMA of plane p for
 // the next term starts as soon as plane p has been converted.  phi stays in TMEM across every
@@ -61,6 +62,11 @@ struct ConsumeArgs {
     int emul;                  // 1: SA == MUL1 and SB == MUL0 at the same orbital indices (symmetric pairs)
     double* epart;
     int* err;
+    // single-pass kernel: per-term operator image, and the batch's Z for L2 prefetches
+    const uint8_t* img;
+    uint32_t img_stride;       // bytes per term of img: ya_bytes + b3_bytes
+    const uint8_t* zsrc;
+    uint32_t z_plane;          // bytes of one x plane of one term of Z
 };
 
 constexpr int kThreads = 320;
@@ -588,11 +594,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // issue stage 3, one x plane each, as soon as the term's stage 2 has finished.  A warp needs
 // more time to issue a tcgen05.mma than the tensor pipe needs to run one of these small
 // tiles, so the stage-3 streams are issued in parallel.  Operand tiles use the 128-byte
-// swizzle (one 128-byte row per TMA request).
+// swizzle.  Per term, a load stage receives the A_t2 and mu_t A_t3 tiles as two plain bulk
+// copies of their ready-made image (k_operand_image below) and each Z plane as one TMA box:
+// the copy engine walks tensor boxes one row at a time, and its per-row cost, not bandwidth,
+// bounded the loop when every operator tile was a box.
 template <bool S2TF32>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_consume_ts(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mA2,
-                 const __grid_constant__ CUtensorMap mA3f, const __grid_constant__ CUtensorMap mA3t, ConsumeArgs a) {
+    k_consume_ts(const __grid_constant__ CUtensorMap mZ, ConsumeArgs a) {
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
@@ -643,7 +651,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
     // mu_t A_t3: na3f full 128-byte atoms (32 K each), then kt single K steps of 32-byte rows
-    // (the K tail, so that no box row is mostly zero fill)
+    // (the K tail, so that no row is mostly zero fill)
     const int na3f = a.ks3 / 4, kt = a.ks3 % 4;
 
     // The producer and MMA roles run on whole warps with uniform control flow; one elected lane
@@ -651,6 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 8) {
         // ------------------------------ TMA producer ------------------------------
         const int na2 = (a.ks2 + 3) / 4;   // 128-byte atoms along K
+        const int nplanes = min(BX, a.n1 - x0);
         int issued = 0;
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
@@ -659,25 +668,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             issued = t + 1;
+            // the slab's planes of one term are contiguous in Z: one L2 prefetch per later term
             for (int ahead = (t == 0 ? 1 : NL + 1); ahead <= NL + 1; ++ahead)
                 if (t + ahead < a.nt)
-                    for (int p = 0; p < BX; ++p)
-                        for (int k = 0; k < na2; ++k)
-                            tma_prefetch_l2_3d_w(&mZ, k * AK2, (x0 + p) * a.r3, pl * a.nt + term_of(t + ahead));
+                    bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(t + ahead)) * a.n1 + x0) * a.z_plane,
+                                       (uint32_t)nplanes * a.z_plane);
             mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
             const int tt = term_of(t);
             const int zdep = pl * a.nt + tt;
-            for (int k = 0; k < na2; ++k) {
-                tma_load_3d_w(YAs(s) + k * ya_atom, &mA2, &full_bar[s], k * AK2, 0, tt);
+            // operator tiles: two plain copies of their ready-made image; Z planes: one box each
+            const uint8_t* im = a.img + (size_t)tt * a.img_stride;
+            bulk_load_w(YAs(s), im, a.ya_bytes, &full_bar[s]);
+            for (int k = 0; k < na2; ++k)
                 // plane p's rows start at row p * gs (a multiple of 8) of the Z tile
                 for (int p = 0; p < BX; ++p)
                     tma_load_3d_w(Zs(s) + k * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s], k * AK2,
                                   (x0 + p) * a.r3, zdep);
-            }
-            for (int k = 0; k < na3f; ++k) tma_load_3d_w(B3s(s) + k * b3_atom, &mA3f, &full_bar[s], k * 32, 0, tt);
-            for (int j = 0; j < kt; ++j)
-                tma_load_3d_w(B3s(s) + na3f * b3_atom + (uint32_t)j * a.n3p * 32u, &mA3t, &full_bar[s], na3f * 32 + 8 * j, 0,
-                              tt);
+            bulk_load_w(B3s(s), im + a.ya_bytes, a.b3_bytes, &full_bar[s]);
         }
         if (!ok)
             for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
@@ -773,6 +780,50 @@ __global__ void __launch_bounds__(kThreads, 1)
         a.epart[(long)pl * gridDim.x + slab] = s;
     }
     if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// Image of the per-term operator tiles of the single-pass kernel, built once per context:
+// [A_t2 tile][mu_t A_t3 tile] for every term t, byte for byte as the tensor-map loads of a load
+// stage lay them out (128-byte swizzle, the 32-byte-swizzled K tail of mu_t A_t3, zero fill).
+// The expansion kernel then brings each term's operators in with two plain bulk copies, which
+// the copy engine streams at its byte rate, instead of walking one box row at a time.
+struct ImageArgs {
+    int ks2, ks3, n3p;
+    uint32_t ya_rows, ya_bytes, b3_bytes;
+    uint8_t* img;
+    int* err;
+};
+
+template <bool S2TF32>
+__global__ void __launch_bounds__(32, 1)
+    k_operand_image(const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA3f,
+                    const __grid_constant__ CUtensorMap mA3t, ImageArgs g) {
+    constexpr int AK2 = S2TF32 ? 32 : 64;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int t = blockIdx.x;
+    const int na2 = (g.ks2 + 3) / 4, na3f = g.ks3 / 4, kt = g.ks3 % 4;
+    const uint32_t ya_atom = g.ya_rows * 128u, b3_atom = (uint32_t)g.n3p * 128u;
+    uint8_t* b3 = smem + g.ya_bytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+        mbar_arrive_expect_tx(&bar, g.ya_bytes + g.b3_bytes);
+        for (int k = 0; k < na2; ++k) tma_load_3d(smem + k * ya_atom, &mA2, &bar, k * AK2, 0, t);
+        for (int k = 0; k < na3f; ++k) tma_load_3d(b3 + k * b3_atom, &mA3f, &bar, k * 32, 0, t);
+        for (int j = 0; j < kt; ++j)
+            tma_load_3d(b3 + na3f * b3_atom + (uint32_t)j * g.n3p * 32u, &mA3t, &bar, na3f * 32 + 8 * j, 0, t);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&bar, 0, g.err, 47);
+    if (!__all_sync(0xffffffffu, ok)) {
+        mbar_drain(&bar, 0);
+        return;
+    }
+    const uint4* src = (const uint4*)smem;
+    uint4* dst = (uint4*)(g.img + (size_t)t * (g.ya_bytes + g.b3_bytes));
+    for (uint32_t i = threadIdx.x; i < (g.ya_bytes + g.b3_bytes) / 16; i += 32) dst[i] = src[i];
 }
 
 }  // namespace tcc
@@ -983,6 +1034,53 @@ long tc_consume_blocks(const tx_ctx* c) {
     return (c->n[0] + p.bx - 1) / p.bx;
 }
 
+int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
+    TcOperands* op = c->tc;
+    if (op->img) {
+        cudaFree(op->img);
+        op->img = nullptr;
+    }
+    ConsumePlan p;
+    if (op->split || !ts_possible(c, op->tf32)) return TX_OK;
+    for (int nl = 2; nl <= tcc::kMaxLoad; ++nl)
+        if (plan_ts(c, op->tf32, 1, nl, &p)) break;
+    // the tile shapes below depend on (n, r, precision) only, not on the slab or the stages
+    const int n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T, eb = op->esize;
+    op->img_stride = p.ya + p.b3;
+    if (cudaMalloc(&op->img, (size_t)T * op->img_stride) != cudaSuccess) {
+        cudaGetLastError();
+        op->img = nullptr;
+        return fail(TX_ERR_OOM, "expansion operator image");
+    }
+    CUtensorMap mA2, mA3f, mA3t;
+    const uint32_t AK2 = op->tf32 ? 32 : 64;   // elements per 128-byte box row
+    // K extents are the zero-padded row lengths (whole 32-byte sectors)
+    const int l2 = ldk(r2, eb);
+    TX_TRY(make_map(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, AK2, (uint32_t)p.n2p));
+    TX_TRY(make_map(&mA3f, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 32, (uint32_t)p.n3p));
+    TX_TRY(make_map_sw(&mA3t, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 8, (uint32_t)p.n3p,
+                       CU_TENSOR_MAP_SWIZZLE_32B));
+    tcc::ImageArgs g{};
+    g.ks2 = p.ks2;
+    g.ks3 = p.ks3;
+    g.n3p = p.n3p;
+    g.ya_rows = p.ya_rows;
+    g.ya_bytes = p.ya;
+    g.b3_bytes = p.b3;
+    g.img = (uint8_t*)op->img;
+    g.err = c->d_err;
+    const int smem = (int)op->img_stride + 1024;
+    if (op->tf32) {
+        cudaFuncSetAttribute(tcc::k_operand_image<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        tcc::k_operand_image<true><<<(unsigned)T, 32, smem, s>>>(mA2, mA3f, mA3t, g);
+    } else {
+        cudaFuncSetAttribute(tcc::k_operand_image<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        tcc::k_operand_image<false><<<(unsigned)T, 32, smem, s>>>(mA2, mA3f, mA3t, g);
+    }
+    TX_LAUNCHED();
+    return TX_OK;
+}
+
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
                const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
                cudaStream_t s, bool emul) {
@@ -1017,23 +1115,23 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         // bytes per stage (128-byte rows; zero-filled parts count): A_t2, Z planes, mu_t A_t3
         const int na2 = (p.ks2 + 3) / 4;
         a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3 + (p.ks3 / 4) * p.n3p) + 32 * (p.ks3 % 4) * p.n3p);
-        CUtensorMap mZ, mA2, mA3f, mA3t;
+        if (!op->img || op->img_stride != p.ya + p.b3)
+            return fail(TX_ERR_CUDA, "operator image missing or built for another tile shape");
+        a.img = (const uint8_t*)op->img;
+        a.img_stride = op->img_stride;
+        a.zsrc = (const uint8_t*)Z;
+        a.z_plane = (uint32_t)((size_t)r3 * sc.ld_b * eb);
+        CUtensorMap mZ;
         const uint32_t AK2 = op->tf32 ? 32 : 64;   // elements per 128-byte box row
-        // K extents are the zero-padded row lengths (whole 32-byte sectors)
-        const int l2 = ldk(r2, eb);
         TX_TRY(make_map(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b,
                         AK2, (uint32_t)r3));
-        TX_TRY(make_map(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, AK2, (uint32_t)p.n2p));
-        TX_TRY(make_map(&mA3f, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 32, (uint32_t)p.n3p));
-        TX_TRY(make_map_sw(&mA3t, op->st.A3f, 4, pad8(r3), n3, T, pad8(r3), (uint64_t)n3 * pad8(r3), 8, (uint32_t)p.n3p,
-                           CU_TENSOR_MAP_SWIZZLE_32B));
         const int ps = prof_begin("tc_consume", s);
         if (op->tf32) {
             cudaFuncSetAttribute(tcc::k_consume_ts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, mA3t, a);
+            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, a);
         } else {
             cudaFuncSetAttribute(tcc::k_consume_ts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, mA2, mA3f, mA3t, a);
+            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, a);
         }
         prof_end(ps, s);
         TX_LAUNCHED();

@@ -33,6 +33,10 @@ struct TcOperands {
     char* buf;            // one allocation for every static operand (hi, then lo)
     TcStatic st;
     int bx;               // x planes per expansion CTA
+    // single-pass expansion: per Gaussian term, the shared-memory image of its operator tiles
+    // ([A_t2 tile][mu_t A_t3 tile], swizzled and zero-filled as the tile loads lay them out)
+    void* img;
+    uint32_t img_stride;  // bytes per term
 };
 
 // per-pair scratch (elements of the operand type; doubled for split precisions)
@@ -44,6 +48,7 @@ TcScratch tc_scratch(const tx_ctx* c);
 
 int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
                      int nB, int flags, void* S1, cudaStream_t s);
+int tc_build_operand_image(tx_ctx* c, cudaStream_t s);
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
                const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
                cudaStream_t s, bool emul = false);
