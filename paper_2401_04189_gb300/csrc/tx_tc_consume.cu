@@ -46,6 +46,8 @@ struct ConsumeArgs {
     uint32_t ya_rows, z_rows;                          // rows of the stage-2 A tile (A_t2) and B tile (Z)
     uint32_t ya_bytes, z_bytes, b3_bytes, a3_bytes;    // one hi copy of each operand tile
     uint32_t load_bytes, stage_tx, a3_off;             // load stage stride, bytes per stage, A3 buffers
+    int nload3;                                        // single-pass kernel: stage-3 ring stages
+    uint32_t load3_bytes;                              // single-pass kernel: stage-3 ring stride
     uint32_t tmem_cols, y_cols;
     int p0;
     const PairRec* recs;
@@ -67,9 +69,11 @@ struct ConsumeArgs {
     uint32_t img_stride;       // bytes per term of img: ya_bytes + b3_bytes
     const uint8_t* zsrc;
     uint32_t z_plane;          // bytes of one x plane of one term of Z
+    int zone;                  // 1: the slab's Z planes load as one box (gs == r3, bx * r3 <= 256 rows)
 };
 
 constexpr int kThreads = 320;
+constexpr int kThreadsTs = 352;   // single-pass kernel: one more producer warp (10)
 // epilogue shared memory (reuses the pipeline buffers): phi staging, 8 warps x 32 rows x 68
 // floats, then per warp two blocks of orbital values, 8 row pairs x 2 multipliers x 32 lanes
 constexpr uint32_t kStgBytes = 8u * 32u * 68u * 4u;
@@ -585,6 +589,82 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// MMA issue sequences of the single-pass kernel.  Every descriptor of a sequence is a per-term
+// base plus an immediate and the K steps are unrolled at compile time: a runtime loop or a
+// dispatch around the instructions costs the issuing warp more per MMA than the tensor pipe
+// needs to run one of these tiles.  The kernel is instantiated for the common step counts
+// (KS > 0); other ranks take the dispatch below (KS == 0).
+//   stage 2: KS K steps of one 128 x N tile; A (A_t2) and B (Z) K-major, 128-byte swizzle,
+//            atoms of 4 K steps `a16` / `b16` descriptor units apart
+//   stage 3: KS = 4 * na + kt K steps; A = Y from TMEM (8 columns per step), B = mu_t A_t3:
+//            na full 128-byte-swizzled atoms `atom16` apart, then kt 32-byte-swizzled K steps
+//            `tail16` apart
+template <bool TF32, int KS>
+__device__ __forceinline__ void s2_mmas_k(uint32_t d, uint64_t ad, uint64_t bd, uint32_t a16, uint32_t b16, uint32_t id) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+        mma_ss_w<TF32>(d, ad + (uint32_t)(k >> 2) * a16 + (uint32_t)(k & 3) * 2u,
+                       bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : 0u);
+}
+template <bool TF32, int KS>
+__device__ __forceinline__ void s2_mmas(int ks, uint32_t d, uint64_t ad, uint64_t bd, uint32_t a16, uint32_t b16,
+                                        uint32_t id) {
+    if constexpr (KS > 0) {
+        s2_mmas_k<TF32, KS>(d, ad, bd, a16, b16, id);
+    } else {
+        switch (ks) {
+            case 1: s2_mmas_k<TF32, 1>(d, ad, bd, a16, b16, id); break;
+            case 2: s2_mmas_k<TF32, 2>(d, ad, bd, a16, b16, id); break;
+            case 3: s2_mmas_k<TF32, 3>(d, ad, bd, a16, b16, id); break;
+            case 4: s2_mmas_k<TF32, 4>(d, ad, bd, a16, b16, id); break;
+            case 5: s2_mmas_k<TF32, 5>(d, ad, bd, a16, b16, id); break;
+            case 6: s2_mmas_k<TF32, 6>(d, ad, bd, a16, b16, id); break;
+            case 8: s2_mmas_k<TF32, 8>(d, ad, bd, a16, b16, id); break;
+            default:
+                for (int k = 0; k < ks; ++k)
+                    mma_ss_w<TF32>(d, ad + (uint32_t)(k >> 2) * a16 + (uint32_t)(k & 3) * 2u,
+                                   bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : 0u);
+        }
+    }
+}
+template <int KS>
+__device__ __forceinline__ void s3_mmas_k(uint32_t d, uint32_t aT, uint64_t b3, uint64_t b3t, uint32_t atom16,
+                                          uint32_t tail16, uint32_t id, uint32_t acc0) {
+    constexpr int NF = (KS / 4) * 4;   // K steps in full 128-byte atoms; the rest is the 32-byte tail
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const uint64_t bd = k < NF ? b3 + (uint32_t)(k >> 2) * atom16 + (uint32_t)(k & 3) * 2u
+                                   : b3t + (uint32_t)(k - NF) * tail16;
+        mma_ts_tf32_w(d, aT + 8u * k, bd, id, k > 0 ? 1u : acc0);
+    }
+}
+template <int KS>
+__device__ __forceinline__ void s3_mmas(int ks, uint32_t d, uint32_t aT, uint64_t b3, uint64_t b3t, uint32_t atom16,
+                                        uint32_t tail16, uint32_t id, uint32_t acc0) {
+    if constexpr (KS > 0) {
+        s3_mmas_k<KS>(d, aT, b3, b3t, atom16, tail16, id, acc0);
+    } else {
+        switch (ks) {
+            case 1: s3_mmas_k<1>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 2: s3_mmas_k<2>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 3: s3_mmas_k<3>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 4: s3_mmas_k<4>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 5: s3_mmas_k<5>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 6: s3_mmas_k<6>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 7: s3_mmas_k<7>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            case 8: s3_mmas_k<8>(d, aT, b3, b3t, atom16, tail16, id, acc0); break;
+            default: {
+                const int nf = (ks / 4) * 4;
+                for (int k = 0; k < ks; ++k) {
+                    const uint64_t bd = k < nf ? b3 + (uint32_t)(k >> 2) * atom16 + (uint32_t)(k & 3) * 2u
+                                               : b3t + (uint32_t)(k - nf) * tail16;
+                    mma_ts_tf32_w(d, aT + 8u * k, bd, id, k > 0 ? 1u : acc0);
+                }
+            }
+        }
+    }
+}
+
 // Variant for the single-pass precisions: stage 3 runs as kind::tf32 with its A operand read
 // straight from TMEM.  Stage 2 leaves Y_t,x[y][g] in TMEM with y on the lanes and g on the
 // columns, which is exactly the K-major layout of an A operand whose rows are the y of one x
@@ -593,17 +673,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Schedule.  Warp 9 issues stage 2 of every term into nyb rotating Y buffers; warps 0..ns3-1
 // issue stage 3, one x plane each, as soon as the term's stage 2 has finished.  A warp needs
 // more time to issue a tcgen05.mma than the tensor pipe needs to run one of these small
-// tiles, so the stage-3 streams are issued in parallel.  Operand tiles use the 128-byte
-// swizzle.  Per term, a load stage receives the A_t2 and mu_t A_t3 tiles as two plain bulk
-// copies of their ready-made image (k_operand_image below) and each Z plane as one TMA box:
-// the copy engine walks tensor boxes one row at a time, and its per-row cost, not bandwidth,
-// bounded the loop when every operator tile was a box.
-template <bool S2TF32>
-__global__ void __launch_bounds__(kThreads, 1)
+// tiles, so the stage-3 streams are issued in parallel.
+//
+// Loads.  Operand tiles use the 128-byte swizzle.  The stage-2 operands (A_t2 tile and the
+// slab's Z planes) and the stage-3 operand (mu_t A_t3) travel in two separate rings of load
+// stages, each with its own producer warp (8 and 10): a stage-2 stage is free again as soon
+// as stage 2 of its term has run, so the Z reads from HBM start several terms ahead instead
+// of waiting for the slower stage-3 release.  A_t2 and mu_t A_t3 arrive as plain bulk copies
+// of a per-context image (k_operand_image below); each Z plane is one TMA box.
+template <bool S2TF32, int KS2, int KS3>
+__global__ void __launch_bounds__(kThreadsTs, 1)
     k_consume_ts(const __grid_constant__ CUtensorMap mZ, ConsumeArgs a) {
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
+    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
+    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
     __shared__ uint32_t tmem_base;
     __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -611,19 +695,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int slab = blockIdx.x, pl = blockIdx.y;
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
-    const int NL = a.nload, NYB = a.nyb, BX = a.bx;
+    const int NL = a.nload, NL3 = a.nload3, NYB = a.nyb, BX = a.bx;
     auto term_of = [&](int t) { return t; };     // theta ascending, as in the split-precision kernel
 
-    // load stage s: [A_t2 tile][Z tile][mu_t A_t3 tile (tf32)], each [atom][rows][128 bytes]
+    // stage-2 ring, stage s: [A_t2 tile][Z tile]; stage-3 ring, stage s: [mu_t A_t3 tile (tf32)];
+    // every tile [atom][rows][128 bytes] (the A_t3 K tail: [rows][32 bytes])
     auto YAs = [&](int s) { return smem + s * a.load_bytes; };
     auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
-    auto B3s = [&](int s) { return Zs(s) + a.z_bytes; };
+    auto B3s = [&](int s) { return smem + a.a3_off + s * a.load3_bytes; };
 
     if (threadIdx.x == 0) {
-        // stage-3 commits (empty, phidone) come from each of the ns3 plane warps
+        // stage-2 stages are released by the stage-2 warp, stage-3 stages, Y buffers and phi by
+        // each of the ns3 plane warps
         for (int s = 0; s < kMaxLoad; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], a.ns3);
+            mbar_init(&empty_bar[s], 1);
+            mbar_init(&full3[s], 1);
+            mbar_init(&empty3[s], a.ns3);
         }
         for (int b = 0; b < kMaxYBuf; ++b) {
             mbar_init(&s2bar[b], 1);
@@ -637,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // feed Y columns that stage 3 multiplies by zeros: they must hold finite values
     for (int s = 0; s < NL; ++s) {
         uint4* z = (uint4*)Zs(s);
-        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreadsTs) z[i] = make_uint4(0, 0, 0, 0);
     }
     fence_async_smem();
     if (warp == 8) {
@@ -650,73 +738,107 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = tmem_base;
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
-    // mu_t A_t3: na3f full 128-byte atoms (32 K each), then kt single K steps of 32-byte rows
-    // (the K tail, so that no row is mostly zero fill)
-    const int na3f = a.ks3 / 4, kt = a.ks3 % 4;
+    // mu_t A_t3: na3f full 128-byte atoms (32 K each), then the K tail in 32-byte rows (so that
+    // no row is mostly zero fill)
+    const int na3f = a.ks3 / 4;
 
     // The producer and MMA roles run on whole warps with uniform control flow; one elected lane
     // issues each TMA / tcgen05 instruction (see the _w helpers).
     if (warp == 8) {
-        // ------------------------------ TMA producer ------------------------------
+        // ------------------------- stage-2 producer: A_t2 and Z -------------------------
         const int na2 = (a.ks2 + 3) / 4;   // 128-byte atoms along K
         const int nplanes = min(BX, a.n1 - x0);
-        int issued = 0;
+        int issued = 0, s = 0;
+        uint32_t ph = 0;
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
-            const int s = t % NL;
-            ok = mbar_wait(&empty_bar[s], ((t / NL) & 1) ^ 1, a.err, 41);
+            ok = mbar_wait(&empty_bar[s], ph ^ 1, a.err, 41);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             issued = t + 1;
             // the slab's planes of one term are contiguous in Z: one L2 prefetch per later term
-            for (int ahead = (t == 0 ? 1 : NL + 1); ahead <= NL + 1; ++ahead)
-                if (t + ahead < a.nt)
-                    bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(t + ahead)) * a.n1 + x0) * a.z_plane,
+            // (nl + 1 terms ahead; the first iteration covers terms 1 .. nl + 1)
+            if (t == 0) {
+                for (int ahead = 1; ahead <= NL + 1 && ahead < a.nt; ++ahead)
+                    bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(ahead)) * a.n1 + x0) * a.z_plane,
                                        (uint32_t)nplanes * a.z_plane);
+            } else if (t + NL + 1 < a.nt) {
+                bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(t + NL + 1)) * a.n1 + x0) * a.z_plane,
+                                   (uint32_t)nplanes * a.z_plane);
+            }
             mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
             const int tt = term_of(t);
             const int zdep = pl * a.nt + tt;
-            // operator tiles: two plain copies of their ready-made image; Z planes: one box each
-            const uint8_t* im = a.img + (size_t)tt * a.img_stride;
-            bulk_load_w(YAs(s), im, a.ya_bytes, &full_bar[s]);
-            for (int k = 0; k < na2; ++k)
-                // plane p's rows start at row p * gs (a multiple of 8) of the Z tile
-                for (int p = 0; p < BX; ++p)
-                    tma_load_3d_w(Zs(s) + k * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s], k * AK2,
-                                  (x0 + p) * a.r3, zdep);
-            bulk_load_w(B3s(s), im + a.ya_bytes, a.b3_bytes, &full_bar[s]);
+            bulk_load_w(YAs(s), a.img + (size_t)tt * a.img_stride, a.ya_bytes, &full_bar[s]);
+            if (a.zone) {
+                // planes packed back to back (gs == r3): one box of bx * r3 rows per K atom
+                tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, x0 * a.r3, zdep);
+                for (int k = 1; k < na2; ++k)
+                    tma_load_3d_w(Zs(s) + k * z_atom, &mZ, &full_bar[s], k * AK2, x0 * a.r3, zdep);
+            } else {
+                for (int k = 0; k < na2; ++k)
+                    // plane p's rows start at row p * gs (a multiple of 8) of the Z tile
+                    for (int p = 0; p < BX; ++p)
+                        tma_load_3d_w(Zs(s) + k * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s], k * AK2,
+                                      (x0 + p) * a.r3, zdep);
+            }
+            if (++s == NL) { s = 0; ph ^= 1; }
         }
         if (!ok)
             for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
+    } else if (warp == 10) {
+        // --------------------------- stage-3 producer: mu_t A_t3 ---------------------------
+        int issued = 0, s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int t = 0; t < a.nt && ok; ++t) {
+            ok = mbar_wait(&empty3[s], ph ^ 1, a.err, 46);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            issued = t + 1;
+            mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
+            bulk_load_w(B3s(s), a.img + (size_t)term_of(t) * a.img_stride + a.ya_bytes, a.b3_bytes, &full3[s]);
+            if (++s == NL3) { s = 0; ph ^= 1; }
+        }
+        if (!ok)
+            for (int t = (issued > NL3 ? issued - NL3 : 0); t < issued; ++t) mbar_drain(&full3[t % NL3], (t / NL3) & 1);
     } else if (warp == 9) {
         // ------------------------------ stage-2 MMA issuer ------------------------------
         // descriptors are built once and advanced by adds: +32 bytes (2 units of the
         // address / 16 field) per K step inside a 128-byte atom, one atom stride every 4 steps
+        //
+        // Ring positions advance by counters, not t % n: a runtime division per barrier index
+        // sits on this warp's critical path every term.  The common tile (y tile 0, the first
+        // chunk of planes) is issued outside any runtime loop; other tiles follow in a loop.
         const uint64_t d0 = sdesc_sw128(0);
+        const int n0 = pad16c(min(a.npc, BX) * a.gs);
+        const uint32_t id0 = S2TF32 ? idesc_tf32(128, n0) : idesc_bf16(128, n0);
+        const bool more = a.nY > 1 || a.npc < BX;
+        int s = 0, yb = 0;
+        uint32_t ph = 0, yph = 0;
         bool ok = true;
         for (int t = 0; t < a.nt && ok; ++t) {
-            bool w = mbar_wait(&full_bar[t % NL], (t / NL) & 1, a.err, 42);
-            // Y buffer t % nyb was last read by stage 3 of term t - nyb.  With nyb == nload that
-            // is the stage-3 term whose completion freed this load stage, which the producer
-            // waited for before loading term t: the full barrier already covers it.
-            if (w && NYB != NL && t >= NYB) w = mbar_wait(&ybar[t % NYB], ((t - NYB) / NYB) & 1, a.err, 43);
+            bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
+            // Y buffer yb was last read by stage 3 of term t - nyb
+            if (w && t >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
             if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
             tc_fence_after();
-            const int s = t % NL;
             const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
-            const uint32_t tY = tmem + (uint32_t)(t % NYB) * a.y_cols;
-            for (int i = 0; i < a.nY; ++i)
-                for (int p0 = 0; p0 < BX; p0 += a.npc) {
-                    const int N = pad16c(min(a.npc, BX - p0) * a.gs);
-                    const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
-                    const uint32_t d = tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs);
-                    const uint64_t ad0 = ya + (uint32_t)i * 1024u, bd0 = zb + (uint32_t)(p0 * a.gs) * 8u;
-                    for (int k = 0; k < a.ks2; ++k)
-                        mma_ss_w<S2TF32>(d, ad0 + (uint32_t)(k >> 2) * (ya_atom >> 4) + (uint32_t)(k & 3) * 2u,
-                                         bd0 + (uint32_t)(k >> 2) * (z_atom >> 4) + (uint32_t)(k & 3) * 2u, id2,
-                                         k > 0 ? 1u : 0u);
-                }
-            mma_commit_w(&s2bar[t % NYB]);
+            const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
+            s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
+            if (more)
+                for (int i = 0; i < a.nY; ++i)
+                    for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
+                        const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                        const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                        const uint32_t d = tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs);
+                        s2_mmas<S2TF32, KS2>(a.ks2, d, ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u,
+                                          ya_atom >> 4, z_atom >> 4, id2);
+                    }
+            mma_commit_w(&s2bar[yb]);
+            mma_commit_w(&empty_bar[s]);
+            if (++s == NL) { s = 0; ph ^= 1; }
+            if (++yb == NYB) { yb = 0; yph ^= 1; }
         }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s2fin);
@@ -729,30 +851,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         double e = 0.0;
         bool ok = true;
         if (warp < a.ns3) {
+            // ring counters and a loop-free common case, as in the stage-2 issuer: this warp's
+            // first plane (warp < ns3 <= bx), y tile 0; further planes / y tiles in a loop
             const uint32_t id3 = idesc_tf32(128, a.n3p);
             const uint64_t d0 = sdesc_sw128(0);
+            const uint32_t dP = tPhi + (uint32_t)(warp * a.nY * a.n3p), aP = (uint32_t)(warp * a.gs);
+            const bool more = a.nY > 1 || BX > a.ns3;
+            int s = 0, yb = 0;
+            uint32_t ph = 0, yph = 0;
             for (int t = 0; t < a.nt && ok; ++t) {
-                const bool w = mbar_wait(&s2bar[t % NYB], (t / NYB) & 1, a.err, 44);
+                bool w = mbar_wait(&s2bar[yb], yph, a.err, 44);
+                if (w) w = mbar_wait(&full3[s], ph, a.err, 48);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc_fence_after();
-                const int s = t % NL;
                 const uint64_t b3 = d0 + (smem_u32(B3s(s)) >> 4);
                 const uint64_t b3t = sdesc_sw32(0) + (smem_u32(B3s(s) + na3f * b3_atom) >> 4);
-                const uint32_t tY = tmem + (uint32_t)(t % NYB) * a.y_cols;
+                const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
                 const uint32_t acc0 = t > 0 ? 1u : 0u;
-                for (int p = warp; p < BX; p += a.ns3)
-                    for (int i = 0; i < a.nY; ++i) {
-                        const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
-                        const uint32_t d = tPhi + (uint32_t)((p * a.nY + i) * a.n3p);
-                        for (int k = 0; k < 4 * na3f; ++k)
-                            mma_ts_tf32_w(d, aT + 8u * k, b3 + (uint32_t)(k >> 2) * (b3_atom >> 4) + (uint32_t)(k & 3) * 2u,
-                                          id3, k > 0 ? 1u : acc0);
-                        for (int j = 0; j < kt; ++j)
-                            mma_ts_tf32_w(d, aT + 8u * (4 * na3f + j), b3t + (uint32_t)j * (uint32_t)a.n3p * 2u, id3,
-                                          (na3f > 0 || j > 0) ? 1u : acc0);
-                    }
-                if (NYB != NL) mma_commit_w(&ybar[t % NYB]);
-                mma_commit_w(&empty_bar[s]);
+                s3_mmas<KS3>(a.ks3, dP, tY + aP, b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
+                if (more)
+                    for (int p = warp; p < BX; p += a.ns3)
+                        for (int i = (p == warp ? 1 : 0); i < a.nY; ++i) {
+                            const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
+                            const uint32_t d = tPhi + (uint32_t)((p * a.nY + i) * a.n3p);
+                            s3_mmas<KS3>(a.ks3, d, aT, b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
+                        }
+                mma_commit_w(&ybar[yb]);
+                mma_commit_w(&empty3[s]);
+                if (++s == NL3) { s = 0; ph ^= 1; }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
             mma_commit_w(&phidone);
         }
@@ -838,6 +965,8 @@ struct ConsumePlan {
     bool ts;                 // single-pass kernel (stage 3 from TMEM) instead of the converter kernel
     int bx, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, nload, na3, nyb, gs, ycol_tile;
     uint32_t ya_rows, z_rows, ya, zb, b3, a3, load, a3_off, tmem_cols, y_cols;
+    int nload3;              // single-pass: stages of the stage-3 (mu_t A_t3) ring
+    uint32_t load3;          // single-pass: stride of the stage-3 ring
     size_t smem;
 };
 
@@ -880,10 +1009,16 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->ya = (uint32_t)na2 * p->ya_rows * 128u;
     p->zb = (uint32_t)na2 * p->z_rows * 128u;
     p->b3 = (uint32_t)(p->ks3 / 4) * p->n3p * 128u + (uint32_t)(p->ks3 % 4) * p->n3p * 32u;
-    p->load = (p->ya + p->zb + p->b3 + 1023) & ~1023u;
+    // two rings: nload stages of [A_t2][Z] (stage 2), then up to four of [mu_t A_t3] (stage 3)
+    p->load = (p->ya + p->zb + 1023) & ~1023u;
+    p->load3 = (p->b3 + 1023) & ~1023u;
     p->nload = nload;
-    p->smem = std::max((size_t)p->load * nload + 16384, (size_t)tcc::kEpiBytes) + 1024;
-    return p->smem <= 226 * 1024;
+    p->a3_off = p->load * (uint32_t)nload;
+    for (p->nload3 = std::min(nload, 4); p->nload3 >= 2; --p->nload3) {
+        p->smem = std::max((size_t)p->a3_off + (size_t)p->load3 * p->nload3 + 16384, (size_t)tcc::kEpiBytes) + 1024;
+        if (p->smem <= 226 * 1024) return true;
+    }
+    return false;
 }
 
 // tensor-pipe cycles per plane and term of a single-pass plan (one MMA costs max(50, N / 2))
@@ -1112,9 +1247,10 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     dim3 grid((unsigned)((n1 + p.bx - 1) / p.bx), (unsigned)np);
     if (p.ts) {
         a.gs = p.gs; a.ycol_tile = p.ycol_tile; a.ns3 = std::min(p.bx, 8);
-        // bytes per stage (128-byte rows; zero-filled parts count): A_t2, Z planes, mu_t A_t3
+        a.nload3 = p.nload3; a.load3_bytes = p.load3;
+        // bytes per stage-2 stage (128-byte rows; zero-filled parts count): A_t2, Z planes
         const int na2 = (p.ks2 + 3) / 4;
-        a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3 + (p.ks3 / 4) * p.n3p) + 32 * (p.ks3 % 4) * p.n3p);
+        a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3));
         if (!op->img || op->img_stride != p.ya + p.b3)
             return fail(TX_ERR_CUDA, "operator image missing or built for another tile shape");
         a.img = (const uint8_t*)op->img;
@@ -1123,16 +1259,21 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         a.z_plane = (uint32_t)((size_t)r3 * sc.ld_b * eb);
         CUtensorMap mZ;
         const uint32_t AK2 = op->tf32 ? 32 : 64;   // elements per 128-byte box row
+        a.zone = (p.gs == r3 && p.bx * r3 <= 256) ? 1 : 0;
         TX_TRY(make_map(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b,
-                        AK2, (uint32_t)r3));
+                        AK2, (uint32_t)(a.zone ? p.bx * r3 : r3)));
+        // instantiations with compile-time K step counts for ranks 32, 40, 48 and 64; any other
+        // rank runs the dispatching form (see s2_mmas / s3_mmas)
+        using Kern = void (*)(const CUtensorMap, tcc::ConsumeArgs);
+        Kern kern = op->tf32 ? (Kern)tcc::k_consume_ts<true, 0, 0> : (Kern)tcc::k_consume_ts<false, 0, 0>;
+#define TX_TS_CASE(TF, K2, K3) \
+    if (op->tf32 == TF && p.ks2 == K2 && p.ks3 == K3) kern = tcc::k_consume_ts<TF, K2, K3>;
+        TX_TS_CASE(false, 2, 4) TX_TS_CASE(false, 3, 5) TX_TS_CASE(false, 3, 6) TX_TS_CASE(false, 4, 8)
+        TX_TS_CASE(true, 4, 4) TX_TS_CASE(true, 5, 5) TX_TS_CASE(true, 6, 6) TX_TS_CASE(true, 8, 8)
+#undef TX_TS_CASE
         const int ps = prof_begin("tc_consume", s);
-        if (op->tf32) {
-            cudaFuncSetAttribute(tcc::k_consume_ts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<true><<<grid, tcc::kThreads, p.smem, s>>>(mZ, a);
-        } else {
-            cudaFuncSetAttribute(tcc::k_consume_ts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-            tcc::k_consume_ts<false><<<grid, tcc::kThreads, p.smem, s>>>(mZ, a);
-        }
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        kern<<<grid, tcc::kThreadsTs, p.smem, s>>>(mZ, a);
         prof_end(ps, s);
         TX_LAUNCHED();
         return TX_OK;
