@@ -747,7 +747,6 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
     if (warp == 8) {
         // ------------------------- stage-2 producer: A_t2 and Z -------------------------
         const int na2 = (a.ks2 + 3) / 4;   // 128-byte atoms along K
-        const int nplanes = min(BX, a.n1 - x0);
         int issued = 0, s = 0;
         uint32_t ph = 0;
         bool ok = true;
@@ -756,16 +755,6 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             issued = t + 1;
-            // the slab's planes of one term are contiguous in Z: one L2 prefetch per later term
-            // (nl + 1 terms ahead; the first iteration covers terms 1 .. nl + 1)
-            if (t == 0) {
-                for (int ahead = 1; ahead <= NL + 1 && ahead < a.nt; ++ahead)
-                    bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(ahead)) * a.n1 + x0) * a.z_plane,
-                                       (uint32_t)nplanes * a.z_plane);
-            } else if (t + NL + 1 < a.nt) {
-                bulk_prefetch_l2_w(a.zsrc + ((size_t)(pl * a.nt + term_of(t + NL + 1)) * a.n1 + x0) * a.z_plane,
-                                   (uint32_t)nplanes * a.z_plane);
-            }
             mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
             const int tt = term_of(t);
             const int zdep = pl * a.nt + tt;
@@ -787,10 +776,18 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         if (!ok)
             for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
     } else if (warp == 10) {
-        // --------------------------- stage-3 producer: mu_t A_t3 ---------------------------
+        // ------------------- stage-3 producer: mu_t A_t3, and the Z prefetches -------------------
+        // The slab's planes of one term are contiguous in Z: one L2 prefetch per term, issued
+        // here (this warp runs a few terms behind stage 2, so nl + 2 terms ahead of its own
+        // position is ahead of the stage-2 loads) to keep the stage-2 producer's issue short.
+        const int nplanes = min(BX, a.n1 - x0);
+        const uint32_t zbytes = (uint32_t)nplanes * a.z_plane;
+        const uint8_t* zslab = a.zsrc + ((size_t)pl * a.nt * a.n1 + x0) * a.z_plane;
+        const size_t zterm = (size_t)a.n1 * a.z_plane;
         int issued = 0, s = 0;
         uint32_t ph = 0;
         bool ok = true;
+        for (int t = 1; t <= NL + 2 && t < a.nt; ++t) bulk_prefetch_l2_w(zslab + (size_t)term_of(t) * zterm, zbytes);
         for (int t = 0; t < a.nt && ok; ++t) {
             ok = mbar_wait(&empty3[s], ph ^ 1, a.err, 46);
             ok = __all_sync(0xffffffffu, ok);
@@ -798,6 +795,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
             issued = t + 1;
             mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
             bulk_load_w(B3s(s), a.img + (size_t)term_of(t) * a.img_stride + a.ya_bytes, a.b3_bytes, &full3[s]);
+            if (t > 0 && t + NL + 2 < a.nt) bulk_prefetch_l2_w(zslab + (size_t)term_of(t + NL + 2) * zterm, zbytes);
             if (++s == NL3) { s = 0; ph ^= 1; }
         }
         if (!ok)
