@@ -218,7 +218,7 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
         g.b_z1 = 1;
         g.C = Z; g.c_m = (long)r3 * sc.ld_b; g.c_n = 1; g.c_b1 = (long)sc.z;
         g.c_lo = (long)np * sc.z; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
-        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
+        TX_TRY(tc_rows_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
     }
     // 5. modes 2 and 3 for every term, phi accumulated in TMEM, Hadamard / energy epilogue
     int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;

@@ -51,5 +51,10 @@ int make_map_f32_plain(CUtensorMap* m, const void* base, uint64_t k_extent, uint
                        uint32_t box_k, uint32_t box_rows);
 int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf32, bool split, const char* prof,
                    cudaStream_t s);
+// The same product by the row-streaming kernel where it applies (single-pass precision, K of
+// at most two 128-byte atoms, contiguous 16-byte aligned output rows, N >= 128); otherwise
+// tc_gemm_launch.
+int tc_rows_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf32, bool split, const char* prof,
+                   cudaStream_t s);
 
 }  // namespace tx

@@ -408,6 +408,234 @@ int tc_gemm_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf
     return TX_OK;
 }
 
+// ======================================================================================
+// Row-streaming form for GEMMs with a short K (at most two 128-byte atoms), many row tiles and
+// contiguous output rows: one CTA per (column tile, batch, row-tile stride) keeps its B tile in
+// shared memory and walks its row tiles with two A stages, two TMEM accumulators and TMA
+// stores of the output, so that the loads, the MMAs and the output of consecutive row tiles
+// overlap and the output leaves as whole 128-byte lines.  Used for the expansion's first mode
+// (T * n1 rows against one pair's core), a store stream of T n r^2 operand values per pair.
+// ======================================================================================
+namespace tcg {
+
+constexpr int kRowsThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t kStgBuf = 32 * 128;   // one staged 32-row x 128-byte output box
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"((uint64_t)m),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <bool TF32>
+__global__ void __launch_bounds__(kRowsThreads, 1)
+    k_tc_rows(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+              const __grid_constant__ CUtensorMap mC, TcGemmArgs g) {
+    constexpr int kAtomK = TF32 ? 32 : 64;      // elements per 128-byte row
+    constexpr int kMmaK = TF32 ? 8 : 16;        // K per instruction (32 bytes)
+    constexpr int CE = TF32 ? 32 : 64;          // output elements per 128-byte staged row
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bbar, afull[2], aempty[2], accfull[2], accfree[2];
+    __shared__ uint32_t tmem_base;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int BN = g.BN;
+    const int nk = (g.K + kAtomK - 1) / kAtomK;
+    const uint32_t a_atom = kBM * 128, b_atom = (uint32_t)BN * 128;
+    uint8_t* sB = smem;                                                  // [nk][BN][128 B]
+    uint8_t* sA = smem + ((nk * b_atom + 1023) & ~1023u);                 // [2][nk][128][128 B]
+    uint8_t* sC = sA + 2 * nk * a_atom;                                   // [4 warps][2][32][128 B]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, b1 = blockIdx.y;
+    const int mtiles = (g.M + kBM - 1) / kBM;
+    const int ntile = blockIdx.z < mtiles ? (mtiles - 1 - (int)blockIdx.z) / (int)gridDim.z + 1 : 0;
+    auto m0_of = [&](int j) { return ((int)blockIdx.z + j * (int)gridDim.z) * kBM; };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bbar, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&afull[i], 1);
+            mbar_init(&aempty[i], 1);
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accfree[i], 4);
+        }
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_base, g.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: B once, then A per row tile ----------------
+        const int brow = n0 + b1 * g.b_row1, bz = b1 * g.b_z1;
+        const int arow = b1 * g.a_row1, az = b1 * g.a_z1;
+        mbar_arrive_expect_tx_w(&bbar, (uint32_t)nk * b_atom);
+        for (int kb = 0; kb < nk; ++kb) tma_load_3d_w(sB + kb * b_atom, &mB, &bbar, kb * kAtomK, brow, bz);
+        int s = 0, issued = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int j = 0; j < ntile; ++j) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&aempty[s], ph ^ 1, g.err, 15));
+            if (!ok) break;
+            issued = j + 1;
+            mbar_arrive_expect_tx_w(&afull[s], (uint32_t)nk * a_atom);
+            for (int kb = 0; kb < nk; ++kb)
+                tma_load_3d_w(sA + (s * nk + kb) * a_atom, &mA, &afull[s], kb * kAtomK, arow + m0_of(j), az);
+            if (++s == 2) { s = 0; ph ^= 1; }
+        }
+        // do not leave the kernel with copies in flight
+        mbar_drain(&bbar, 0);
+        if (!ok)
+            for (int j = (issued > 2 ? issued - 2 : 0); j < issued; ++j) mbar_drain(&afull[j & 1], (j >> 1) & 1);
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = TF32 ? idesc_tf32(kBM, BN) : idesc_bf16(kBM, BN);
+        bool ok = __all_sync(0xffffffffu, mbar_wait(&bbar, 0, g.err, 16));
+        const uint64_t bd0 = sdesc_sw128(smem_u32(sB));
+        int s = 0;
+        uint32_t ph = 0;
+        for (int j = 0; j < ntile && ok; ++j) {
+            bool w = mbar_wait(&afull[s], ph, g.err, 17);
+            // accumulator s was last read by the epilogue for row tile j - 2
+            if (w && j >= 2) w = mbar_wait(&accfree[s], ph ^ 1, g.err, 18);
+            if (!__all_sync(0xffffffffu, w)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(s * BN);
+            const uint64_t ad0 = sdesc_sw128(smem_u32(sA + s * nk * a_atom));
+            for (int kb = 0; kb < nk; ++kb) {
+                const int steps = (min(g.K - kb * kAtomK, kAtomK) + kMmaK - 1) / kMmaK;
+                const uint64_t ad = ad0 + (uint64_t)(kb * (a_atom >> 4)), bd = bd0 + (uint64_t)(kb * (b_atom >> 4));
+                for (int k = 0; k < steps; ++k)
+                    mma_ss_w<TF32>(d, ad + 2u * k, bd + 2u * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit_w(&aempty[s]);
+            mma_commit_w(&accfull[s]);
+            if (++s == 2) { s = 0; ph ^= 1; }
+        }
+    } else {
+        // ---------------- epilogue: warps 2-5, TMEM lane quadrant = warp % 4 ----------------
+        // Each warp stages its 32 rows x 128 bytes per chunk in the 128-byte swizzle (16-byte
+        // piece q of row r at ((q ^ (r & 7)) * 16), conflict-free) and lane 0 stores the box
+        // with TMA; two staging buffers alternate, the older store must have read its buffer.
+        const int q4 = warp & 3;
+        uint8_t* stg = sC + (warp - 2) * 2 * kStgBuf;
+        int s = 0, buf = 0;
+        uint32_t ph = 0;
+        for (int j = 0; j < ntile; ++j) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&accfull[s], ph, g.err, 19))) break;
+            tc_fence_after();
+            const int mrow = m0_of(j) + q4 * 32;
+            for (int c0 = 0; c0 < BN; c0 += CE) {
+                if (lane == 0) bulk_wait_read1();
+                __syncwarp();
+                uint8_t* sb = stg + buf * kStgBuf + lane * 128;
+#pragma unroll
+                for (int u = 0; u < CE / 16; ++u) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(s * BN + c0 + 16 * u), r);
+                    tmem_ld_wait();
+                    if constexpr (TF32) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int pc = 4 * u + h;
+                            *(uint4*)(sb + ((pc ^ (lane & 7)) << 4)) =
+                                make_uint4(__float_as_uint(g.alpha * __uint_as_float(r[4 * h])),
+                                           __float_as_uint(g.alpha * __uint_as_float(r[4 * h + 1])),
+                                           __float_as_uint(g.alpha * __uint_as_float(r[4 * h + 2])),
+                                           __float_as_uint(g.alpha * __uint_as_float(r[4 * h + 3])));
+                        }
+                    } else {
+                        uint32_t w[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const __nv_bfloat162 hv = __floats2bfloat162_rn(g.alpha * __uint_as_float(r[2 * e]),
+                                                                            g.alpha * __uint_as_float(r[2 * e + 1]));
+                            w[e] = *(const uint32_t*)&hv;
+                        }
+                        *(uint4*)(sb + (((2 * u) ^ (lane & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *(uint4*)(sb + (((2 * u + 1) ^ (lane & 7)) << 4)) = make_uint4(w[4], w[5], w[6], w[7]);
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_3d(&mC, stg + buf * kStgBuf, n0 + c0, mrow, b1);
+                    bulk_commit();
+                }
+                buf ^= 1;
+            }
+            // this warp's TMEM reads of accumulator s are complete: release it to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accfree[s]);
+            if (++s == 2) { s = 0; ph ^= 1; }
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, g.tmem_cols);
+}
+
+}  // namespace tcg
+
+// Whether tc_rows_launch can run this product (else tc_gemm_launch)
+static bool rows_form_fits(const TcGemmArgs& g, bool tf32, bool split) {
+    const int eb = tf32 ? 4 : 2;
+    const int atom = tf32 ? 32 : 64;
+    return !split && (g.c_type == (tf32 ? TC_OUT_F32 : TC_OUT_BF16)) && g.K <= 2 * atom && g.nb2 == 1 && g.c_n == 1 &&
+           g.rdiv <= 0 && g.cdiv <= 0 && g.N >= 128 && g.c_m >= g.N && ((uintptr_t)g.C % 16) == 0 &&
+           (g.c_m * eb) % 16 == 0 && (g.c_b1 * eb) % 16 == 0 && g.nb1 <= 65535;
+}
+
+int tc_rows_launch(const TcOperand& A, const TcOperand& B, TcGemmArgs g, bool tf32, bool split, const char* prof,
+                   cudaStream_t s) {
+    if (!rows_form_fits(g, tf32, split)) return tc_gemm_launch(A, B, g, tf32, split, prof, s);
+    if (g.M <= 0) return TX_OK;
+    const int eb = tf32 ? 4 : 2;
+    const uint32_t atom_k = 128 / eb;
+    const int nk = (g.K + (int)atom_k - 1) / (int)atom_k;
+    g.BN = 128;
+    g.nacc = 1;
+    g.tmem_cols = tmem_cols_for(2 * g.BN);
+    const size_t smem = (((size_t)nk * g.BN * 128 + 1023) & ~(size_t)1023) + 2 * (size_t)nk * 128 * 128 +
+                        4 * 2 * tcg::kStgBuf + 1024;
+    CUtensorMap mA, mB, mC;
+    TX_TRY(make_map(&mA, A.hi, eb, A.k_extent, A.rows, A.depth, A.row_stride, A.depth_stride, atom_k, 128));
+    TX_TRY(make_map(&mB, B.hi, eb, B.k_extent, B.rows, B.depth, B.row_stride, B.depth_stride, atom_k, g.BN));
+    // output [nb1][M][N] with row stride c_m and batch stride c_b1; 32-row x 128-byte boxes
+    TX_TRY(make_map(&mC, g.C, eb, (uint64_t)g.N, (uint64_t)g.M, (uint64_t)g.nb1, (uint64_t)g.c_m, (uint64_t)g.c_b1,
+                    atom_k, 32));
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int mtiles = (g.M + 127) / 128;
+    const long base = (long)((g.N + g.BN - 1) / g.BN) * g.nb1;
+    // enough CTAs for about three per SM; each walks mtiles / gz row tiles
+    const int gz = (int)std::max<long>(1, std::min<long>(mtiles, (3L * nsm + base - 1) / base));
+    dim3 grid((unsigned)((g.N + g.BN - 1) / g.BN), (unsigned)g.nb1, (unsigned)gz);
+    const int ps = prof_begin(prof ? prof : "tc_gemm", s);
+    if (tf32) {
+        cudaFuncSetAttribute(tcg::k_tc_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tcg::k_tc_rows<true><<<grid, tcg::kRowsThreads, smem, s>>>(mA, mB, mC, g);
+    } else {
+        cudaFuncSetAttribute(tcg::k_tc_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tcg::k_tc_rows<false><<<grid, tcg::kRowsThreads, smem, s>>>(mA, mB, mC, g);
+    }
+    prof_end(ps, s);
+    TX_LAUNCHED();
+    return TX_OK;
+}
+
 // ---- self-test of the building block ---------------------------------------------------
 namespace {
 __global__ void k_split_f32(const float* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, long n) {
