@@ -230,6 +230,107 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
     return e;
 }
 
+// Epilogue of the single-pass kernel: tile jt of phi holds plane x0 + jt / nY, y rows
+// (jt % nY) * 128 + lane.  The same data flow as consume_epilogue (phi staged per warp in shared
+// memory, orbital values prefetched with cp.async, 16-byte reductions into W), with every
+// per-row and per-block quantity hoisted out of the inner loop: the quadrature weights come
+// from registers (w2 of the warp's 32 rows by shuffle, w3 per block), so the loop issues no
+// global load other than the prefetch, whose latency the double buffer hides.
+__device__ __forceinline__ double consume_epilogue_ts(const ConsumeArgs& a, const PairRec& rec, uint8_t* smem,
+                                                      uint32_t tPhi, int x0, int warp, int lane) {
+    const int q = warp & 3, h = warp >> 2;
+    double e = 0.0;
+    const long N3 = (long)a.n1 * a.n2 * a.n3;
+    const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
+    const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
+    float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
+    float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
+    const float* sa = a.SA + (long)rec.ia * N3;
+    const float* sb = a.SB + (long)rec.ib * N3;
+    const bool en = (a.flags & EPI_ENERGY) != 0;
+    const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
+    const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
+    float* stg = (float*)smem + warp * (32 * 68);
+    float4* lbuf = (float4*)(smem + kStgBytes) + warp * (2 * 8 * 2 * 32);   // [buf][it][m][lane]
+    const int sub = lane >> 4, zl = 4 * (lane & 15);
+    const int ncb = (a.n3p + 63) / 64, nblk = a.nT3 * ncb;
+    // block blk: tile jt = blk / ncb (plane x0 + jt / nY, y tile jt % nY), z columns cb..cb+63;
+    // iteration it covers row 2h + 4it + sub of the warp's quadrant, z = cb + zl .. + 3
+    auto prefetch = [&](int blk) {
+        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
+        const int p = jt / a.nY, x = x0 + p, ybase = (jt - p * a.nY) * 128 + q * 32;
+        const int z = cb + zl;
+        float4* d = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
+        if (x < a.n1 && z < a.n3) {
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int y = ybase + 2 * h + 4 * it + sub;
+                if (y >= a.n2) continue;
+                const int idx = (x * a.n2 + y) * a.n3 + z;
+                if (need0) cp_async16(d + (2 * it) * 32, mul0 + idx);
+                if (need1) cp_async16(d + (2 * it + 1) * 32, mul1 + idx);
+            }
+        }
+        cp_async_commit();
+    };
+    prefetch(0);
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
+        const int p = jt / a.nY, x = x0 + p, ybase = (jt - p * a.nY) * 128 + q * 32;
+        if (blk + 1 < nblk) prefetch(blk + 1);
+        const int nck = min(64, a.n3p - cb) / 16;
+        uint32_t r[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < nck) tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + jt * a.n3p + cb + 16 * c, r[c]);
+        // per-block weights (registers): w1(x) w2(y) for the warp's rows by shuffle, w3 per lane
+        const bool xin = x < a.n1;
+        const int z = cb + zl;
+        const bool zin = z < a.n3;
+        const float w2l = (xin && ybase + lane < a.n2) ? a.w2[ybase + lane] * a.w1[x] : 0.f;
+        const float4 w3 = zin ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < nck)
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *(float4*)(stg + lane * 68 + 16 * c + j) =
+                        make_float4(__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
+                                    __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3]));
+        if (blk + 1 < nblk) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncwarp();
+        const float4* lb = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
+        // energy terms of a block are summed in float32, the block sums in float64
+        float eb = 0.f;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int rr = 2 * h + 4 * it + sub;
+            const float wxy = __shfl_sync(0xffffffffu, w2l, rr);
+            const int y = ybase + rr;
+            if (!xin || !zin || y >= a.n2) continue;
+            const int idx = (x * a.n2 + y) * a.n3 + z;
+            const float4 phi = *(const float4*)(stg + rr * 68 + zl);
+            const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+            float4 f = phi;
+            if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+            const float4 m0 = need0 ? lb[(2 * it) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 m1 = need1 ? lb[(2 * it + 1) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o0) atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+            if (o1) atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+            if (en) {
+                const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
+                const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
+                eb += wv.x * va.x * vb.x * phi.x + wv.y * va.y * vb.y * phi.y + wv.z * va.z * vb.z * phi.z +
+                      wv.w * va.w * vb.w * phi.w;
+            }
+        }
+        e += (double)eb;
+        __syncwarp();
+    }
+    return e;
+}
+
 // Fold of phi into the outputs and the energy sum without shared memory (the pipeline
 // buffers are still in use): each thread takes its TMEM lane, i.e. one grid row (x, y), and
 // 16 z columns per load; the two warps of a lane quadrant take alternate column blocks.
@@ -883,12 +984,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         }
         if (ok && mbar_wait_idle(&phidone, 0, a.err, 45) && *(volatile int*)a.err == 0) {
             tc_fence_after();
-            e = consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, [&](int jt, int r, int& x, int& y) {
-                const int p = jt / a.nY, i = jt - p * a.nY;
-                y = i * 128 + r;
-                x = x0 + p;
-                return y < a.n2 && x < a.n1;
-            });
+            e = consume_epilogue_ts(a, rec, smem, tPhi, x0, warp, lane);
         } else if (warp < a.ns3) {
             mbar_drain(&phidone, 0);
         }
