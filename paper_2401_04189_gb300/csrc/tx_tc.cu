@@ -224,7 +224,11 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
     int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
     if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
     // symmetric pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers
-    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, flags, b.epart, s, subset));
+    // OUT rows: the call's targets (apply only; the energy call writes no W)
+    const int nout = cs.out0 ? cs.n_tgt : 0;
+    const OrbCounts cnt{nA, cs.n_occ, cs.n_occ, cs.n_occ, nout, nout};
+    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, b.epart, s,
+                      subset));
     (void)r1;
     return TX_OK;
 }

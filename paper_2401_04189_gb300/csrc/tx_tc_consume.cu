@@ -230,104 +230,134 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
     return e;
 }
 
-// Epilogue of the single-pass kernel: tile jt of phi holds plane x0 + jt / nY, y rows
-// (jt % nY) * 128 + lane.  The same data flow as consume_epilogue (phi staged per warp in shared
-// memory, orbital values prefetched with cp.async, 16-byte reductions into W), with every
-// per-row and per-block quantity hoisted out of the inner loop: the quadrature weights come
-// from registers (w2 of the warp's 32 rows by shuffle, w3 per block), so the loop issues no
-// global load other than the prefetch, whose latency the double buffer hides.
-__device__ __forceinline__ double consume_epilogue_ts(const ConsumeArgs& a, const PairRec& rec, uint8_t* smem,
-                                                      uint32_t tPhi, int x0, int warp, int lane) {
+// Orbital and output arrays of the single-pass epilogue as TMA tensors: [orbital * n1 + x][y][z]
+// float32, boxes of 32 z x 32 y, 128-byte swizzle.  Maps of absent arrays are never used.
+struct EpiMaps {
+    CUtensorMap m0, m1, sa, sb, o0, o1;
+};
+constexpr uint32_t kEpiBox = 32 * 32 * 4;   // one 32 x 32 float32 box
+constexpr uint32_t kEpiWarpBytes = 4 * kEpiBox;
+
+// Epilogue of the single-pass kernel, on the copy engine.  Work units are (tile jt, 32-column
+// z chunk): tile jt holds plane x0 + jt / nY, y rows (jt % nY) * 128 + lane.  The two warps of a
+// TMEM lane quadrant take alternate units.  Per unit a warp loads the orbital boxes its outputs
+// and energy need (TMA, 128-byte swizzle), each lane combines its own row of phi (tcgen05.ld)
+// with them, writes -psi * phi in place, and lane 0 adds the boxes into W with TMA reductions:
+// no per-element atomics.  With two boxes per unit the loads of the next unit overlap this one.
+__device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, const EpiMaps& em, const PairRec& rec,
+                                                       uint8_t* smem, uint64_t* ebar, uint32_t tPhi, int x0, int warp,
+                                                       int lane) {
     const int q = warp & 3, h = warp >> 2;
-    double e = 0.0;
-    const long N3 = (long)a.n1 * a.n2 * a.n3;
-    const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
-    const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
-    float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
-    float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
-    const float* sa = a.SA + (long)rec.ia * N3;
-    const float* sb = a.SB + (long)rec.ib * N3;
     const bool en = (a.flags & EPI_ENERGY) != 0;
-    const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
-    const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
-    float* stg = (float*)smem + warp * (32 * 68);
-    float4* lbuf = (float4*)(smem + kStgBytes) + warp * (2 * 8 * 2 * 32);   // [buf][it][m][lane]
-    const int sub = lane >> 4, zl = 4 * (lane & 15);
-    const int ncb = (a.n3p + 63) / 64, nblk = a.nT3 * ncb;
-    // block blk: tile jt = blk / ncb (plane x0 + jt / nY, y tile jt % nY), z columns cb..cb+63;
-    // iteration it covers row 2h + 4it + sub of the warp's quadrant, z = cb + zl .. + 3
-    auto prefetch = [&](int blk) {
-        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
-        const int p = jt / a.nY, x = x0 + p, ybase = (jt - p * a.nY) * 128 + q * 32;
-        const int z = cb + zl;
-        float4* d = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
-        if (x < a.n1 && z < a.n3) {
-#pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const int y = ybase + 2 * h + 4 * it + sub;
-                if (y >= a.n2) continue;
-                const int idx = (x * a.n2 + y) * a.n3 + z;
-                if (need0) cp_async16(d + (2 * it) * 32, mul0 + idx);
-                if (need1) cp_async16(d + (2 * it + 1) * 32, mul1 + idx);
-            }
-        }
-        cp_async_commit();
+    const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0, o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
+    const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul), needab = en && !a.emul;
+    // box slots of a unit: m0, m1, then sa, sb (only those needed)
+    const int k0 = 0, k1 = need0 ? 1 : 0, ka = k1 + (need1 ? 1 : 0), kb = ka + 1;
+    const int nbox = ka + (needab ? 2 : 0);
+    const int nsets = nbox <= 2 ? 2 : 1;
+    uint8_t* wbuf = smem + warp * kEpiWarpBytes;
+    auto slot = [&](int set, int k) { return wbuf + (set * 2 + k) * kEpiBox; };
+    const int nch = (a.n3 + 31) / 32, nunits = a.nT3 * nch;
+    double e = 0.0;
+    if (nbox == 0) return e;
+    // this warp's units: h, h + 2, ...
+    const int nmine = nunits > h ? (nunits - 1 - h) / 2 + 1 : 0;
+    auto unit = [&](int i, int& x, int& y0, int& zc, int& jt) {
+        const int u = h + 2 * i;
+        jt = u / nch;
+        zc = (u - jt * nch) * 32;
+        const int p = jt / a.nY;
+        x = x0 + p;
+        y0 = (jt - p * a.nY) * 128 + q * 32;
+        return x < a.n1 && y0 < a.n2;
     };
-    prefetch(0);
-    for (int blk = 0; blk < nblk; ++blk) {
-        const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
-        const int p = jt / a.nY, x = x0 + p, ybase = (jt - p * a.nY) * 128 + q * 32;
-        if (blk + 1 < nblk) prefetch(blk + 1);
-        const int nck = min(64, a.n3p - cb) / 16;
-        uint32_t r[4][16];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (c < nck) tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + jt * a.n3p + cb + 16 * c, r[c]);
-        // per-block weights (registers): w1(x) w2(y) for the warp's rows by shuffle, w3 per lane
-        const bool xin = x < a.n1;
-        const int z = cb + zl;
-        const bool zin = z < a.n3;
-        const float w2l = (xin && ybase + lane < a.n2) ? a.w2[ybase + lane] * a.w1[x] : 0.f;
-        const float4 w3 = zin ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
+    bool pending[2] = {false, false};      // a set's loads issued and not yet waited for
+    auto issue = [&](int i) {
+        int x, y0, zc, jt;
+        if (!unit(i, x, y0, zc, jt)) return;
+        const int set = i % nsets;
+        pending[set] = true;
+        if (lane != 0) return;
+        mbar_arrive_expect_tx(&ebar[set], (uint32_t)nbox * kEpiBox);
+        if (need0) tma_load_3d(slot(set, k0), &em.m0, &ebar[set], zc, y0, rec.m0 * a.n1 + x);
+        if (need1) tma_load_3d(slot(set, k1), &em.m1, &ebar[set], zc, y0, rec.m1 * a.n1 + x);
+        if (needab) {
+            tma_load_3d(slot(set, ka), &em.sa, &ebar[set], zc, y0, rec.ia * a.n1 + x);
+            tma_load_3d(slot(set, kb), &em.sb, &ebar[set], zc, y0, rec.ib * a.n1 + x);
+        }
+    };
+    uint32_t use[2] = {0u, 0u};
+    issue(0);
+    for (int i = 0; i < nmine; ++i) {
+        const int set = i % nsets;
+        int x, y0, zc, jt;
+        const bool valid = unit(i, x, y0, zc, jt);
+        if (nsets == 1 && i > 0) {
+            // single buffer set: the previous unit's reductions must have read it
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+            issue(i);
+        }
+        if (nsets == 2 && i + 1 < nmine) {
+            // the other set was last read by the reductions of unit i - 1
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+            issue(i + 1);
+        }
+        if (!valid) continue;
+        // phi of this lane's row, 32 z (only the columns of this tile)
+        uint32_t r[32];
+        const uint32_t ta = tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + zc);
+        tmem_ld16(ta, *(uint32_t(*)[16])&r[0]);
+        if (zc + 16 < a.n3p) tmem_ld16(ta + 16, *(uint32_t(*)[16])&r[16]);
+        const int y = y0 + lane;
+        const bool rowin = y < a.n2;
+        const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
         tmem_ld_wait();
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (c < nck)
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *(float4*)(stg + lane * 68 + 16 * c + j) =
-                        make_float4(__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
-                                    __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3]));
-        if (blk + 1 < nblk) cp_async_wait<1>(); else cp_async_wait<0>();
-        __syncwarp();
-        const float4* lb = lbuf + (blk & 1) * (8 * 2 * 32) + lane;
-        // energy terms of a block are summed in float32, the block sums in float64
+        if (!mbar_wait(&ebar[set], use[set] & 1, a.err, 49)) break;
+        pending[set] = false;
+        ++use[set];
         float eb = 0.f;
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int rr = 2 * h + 4 * it + sub;
-            const float wxy = __shfl_sync(0xffffffffu, w2l, rr);
-            const int y = ybase + rr;
-            if (!xin || !zin || y >= a.n2) continue;
-            const int idx = (x * a.n2 + y) * a.n3 + z;
-            const float4 phi = *(const float4*)(stg + rr * 68 + zl);
+        for (int c = 0; c < 8; ++c) {
+            const int z = zc + 4 * c;
+            const uint32_t off = (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4);
+            float4 phi = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                     __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+            if (zc + 16 >= a.n3p && c >= 4) phi = make_float4(0.f, 0.f, 0.f, 0.f);   // columns past the tile
+            const float4 w3 = (rowin && z < a.n3) ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
             float4 f = phi;
             if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
-            const float4 m0 = need0 ? lb[(2 * it) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 m1 = need1 ? lb[(2 * it + 1) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (o0) atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
-            if (o1) atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
-            if (en) {
-                const float4 va = a.emul ? m1 : *(const float4*)(sa + idx);
-                const float4 vb = a.emul ? m0 : *(const float4*)(sb + idx);
+            const float4 m0 = need0 ? *(const float4*)(slot(set, k0) + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 m1 = need1 ? *(const float4*)(slot(set, k1) + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o0) *(float4*)(slot(set, k0) + off) = make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w);
+            if (o1) *(float4*)(slot(set, k1) + off) = make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w);
+            if (en && rowin && z < a.n3) {
+                const float4 va = a.emul ? m1 : *(const float4*)(slot(set, ka) + off);
+                const float4 vb = a.emul ? m0 : *(const float4*)(slot(set, kb) + off);
                 eb += wv.x * va.x * vb.x * phi.x + wv.y * va.y * vb.y * phi.y + wv.z * va.z * vb.z * phi.z +
                       wv.w * va.w * vb.w * phi.w;
             }
         }
         e += (double)eb;
+        if (o0 || o1) {
+            // rows past n2 and columns past n3 lie outside the tensors: the reductions skip them
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (o0) tma_reduce_add_3d(&em.o0, slot(set, k0), zc, y0, rec.o0 * a.n1 + x);
+                if (o1) tma_reduce_add_3d(&em.o1, slot(set, k1), zc, y0, rec.o1 * a.n1 + x);
+                bulk_commit();
+            }
+        }
         __syncwarp();
     }
+    // never leave with a load in flight (error path)
+    for (int set = 0; set < 2; ++set)
+        if (pending[set]) mbar_drain(&ebar[set], use[set] & 1);
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
     return e;
 }
 
@@ -784,11 +814,11 @@ __device__ __forceinline__ void s3_mmas(int ks, uint32_t d, uint32_t aT, uint64_
 // of a per-context image (k_operand_image below); each Z plane is one TMA box.
 template <bool S2TF32, int KS2, int KS3>
 __global__ void __launch_bounds__(kThreadsTs, 1)
-    k_consume_ts(const __grid_constant__ CUtensorMap mZ, ConsumeArgs a) {
+    k_consume_ts(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ EpiMaps em, ConsumeArgs a) {
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
-    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin;
+    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin, ebar[8][2];
     __shared__ uint32_t tmem_base;
     __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -820,6 +850,10 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         }
         mbar_init(&phidone, a.ns3);
         mbar_init(&s2fin, 1);
+        for (int w = 0; w < 8; ++w) {
+            mbar_init(&ebar[w][0], 1);
+            mbar_init(&ebar[w][1], 1);
+        }
         fence_barrier_init();
     }
     // Z tile rows that no copy writes (rows r3..gs-1 of each plane, the tail up to the MMA's N)
@@ -984,7 +1018,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         }
         if (ok && mbar_wait_idle(&phidone, 0, a.err, 45) && *(volatile int*)a.err == 0) {
             tc_fence_after();
-            e = consume_epilogue_ts(a, rec, smem, tPhi, x0, warp, lane);
+            e = consume_epilogue_tma(a, em, rec, smem, ebar[warp], tPhi, x0, warp, lane);
         } else if (warp < a.ns3) {
             mbar_drain(&phidone, 0);
         }
@@ -1311,8 +1345,8 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
 }
 
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
-               const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
-               cudaStream_t s, bool emul) {
+               const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, const OrbCounts& cnt, int flags,
+               double* epart, cudaStream_t s, bool emul) {
     const TcOperands* op = c->tc;
     ConsumePlan p;
     if (!choose_plan(c, op->tf32, op->split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
@@ -1358,7 +1392,24 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
                         AK2, (uint32_t)(a.zone ? p.bx * r3 : r3)));
         // instantiations with compile-time K step counts for ranks 32, 40, 48 and 64; any other
         // rank runs the dispatching form (see s2_mmas / s3_mmas)
-        using Kern = void (*)(const CUtensorMap, tcc::ConsumeArgs);
+        // epilogue tensors [orbital * n1 + x][y][z]: absent arrays take a valid stand-in map
+        tcc::EpiMaps em;
+        auto orb_map = [&](CUtensorMap* m, const float* base, int norb) -> int {
+            if (!base || norb < 1) {
+                *m = mZ;
+                return TX_OK;
+            }
+            return make_map(m, base, 4, (uint64_t)n3, (uint64_t)n2, (uint64_t)norb * n1, (uint64_t)n3, (uint64_t)n2 * n3,
+                            32, 32);
+        };
+        TX_TRY(orb_map(&em.m0, MUL0, cnt.mul0));
+        TX_TRY(orb_map(&em.m1, MUL1, cnt.mul1));
+        TX_TRY(orb_map(&em.sa, SA, cnt.sa));
+        TX_TRY(orb_map(&em.sb, SB, cnt.sb));
+        TX_TRY(orb_map(&em.o0, OUT0, cnt.out0));
+        TX_TRY(orb_map(&em.o1, OUT1, cnt.out1));
+        if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
+        using Kern = void (*)(const CUtensorMap, const tcc::EpiMaps, tcc::ConsumeArgs);
         Kern kern = op->tf32 ? (Kern)tcc::k_consume_ts<true, 0, 0> : (Kern)tcc::k_consume_ts<false, 0, 0>;
 #define TX_TS_CASE(TF, K2, K3) \
     if (op->tf32 == TF && p.ks2 == K2 && p.ks3 == K3) kern = tcc::k_consume_ts<TF, K2, K3>;
@@ -1367,7 +1418,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
 #undef TX_TS_CASE
         const int ps = prof_begin("tc_consume", s);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-        kern<<<grid, tcc::kThreadsTs, p.smem, s>>>(mZ, a);
+        kern<<<grid, tcc::kThreadsTs, p.smem, s>>>(mZ, em, a);
         prof_end(ps, s);
         TX_LAUNCHED();
         return TX_OK;

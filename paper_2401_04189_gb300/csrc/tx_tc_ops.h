@@ -49,8 +49,12 @@ TcScratch tc_scratch(const tx_ctx* c);
 int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
                      int nB, int flags, void* S1, cudaStream_t s);
 int tc_build_operand_image(tx_ctx* c, cudaStream_t s);
+// orbital counts of the arrays the expansion epilogue reads and writes (bounds of its tensors)
+struct OrbCounts {
+    int sa, sb, mul0, mul1, out0, out1;
+};
 int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void* Z, const float* SA, const float* SB,
-               const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, int flags, double* epart,
+               const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, const OrbCounts& cnt, int flags, double* epart,
                cudaStream_t s, bool emul = false);
 long tc_consume_blocks(const tx_ctx* c);
 
