@@ -236,14 +236,16 @@ struct EpiMaps {
     CUtensorMap m0, m1, sa, sb, o0, o1;
 };
 constexpr uint32_t kEpiBox = 32 * 32 * 4;   // one 32 x 32 float32 box
-constexpr uint32_t kEpiWarpBytes = 4 * kEpiBox;
+constexpr uint32_t kEpiWarpBytes = 6 * kEpiBox;   // six box slots per epilogue warp
+constexpr int kEpiSets = 3;
 
 // Epilogue of the single-pass kernel, on the copy engine.  Work units are (tile jt, 32-column
 // z chunk): tile jt holds plane x0 + jt / nY, y rows (jt % nY) * 128 + lane.  The two warps of a
 // TMEM lane quadrant take alternate units.  Per unit a warp loads the orbital boxes its outputs
 // and energy need (TMA, 128-byte swizzle), each lane combines its own row of phi (tcgen05.ld)
 // with them, writes -psi * phi in place, and lane 0 adds the boxes into W with TMA reductions:
-// no per-element atomics.  With two boxes per unit the loads of the next unit overlap this one.
+// no per-element atomics.  The slots form a ring of up to three units, so the loads of the
+// next units are in flight while one is combined.
 __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, const EpiMaps& em, const PairRec& rec,
                                                        uint8_t* smem, uint64_t* ebar, uint32_t tPhi, int x0, int warp,
                                                        int lane) {
@@ -254,9 +256,9 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
     // box slots of a unit: m0, m1, then sa, sb (only those needed)
     const int k0 = 0, k1 = need0 ? 1 : 0, ka = k1 + (need1 ? 1 : 0), kb = ka + 1;
     const int nbox = ka + (needab ? 2 : 0);
-    const int nsets = nbox <= 2 ? 2 : 1;
+    const int nsets = nbox == 0 ? 1 : min(kEpiSets, 6 / nbox);
     uint8_t* wbuf = smem + warp * kEpiWarpBytes;
-    auto slot = [&](int set, int k) { return wbuf + (set * 2 + k) * kEpiBox; };
+    auto slot = [&](int set, int k) { return wbuf + (set * nbox + k) * kEpiBox; };
     const int nch = (a.n3 + 31) / 32, nunits = a.nT3 * nch;
     double e = 0.0;
     if (nbox == 0) return e;
@@ -271,7 +273,7 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
         y0 = (jt - p * a.nY) * 128 + q * 32;
         return x < a.n1 && y0 < a.n2;
     };
-    bool pending[2] = {false, false};      // a set's loads issued and not yet waited for
+    bool pending[kEpiSets] = {false, false, false};   // a set's loads issued and not yet waited for
     auto issue = [&](int i) {
         int x, y0, zc, jt;
         if (!unit(i, x, y0, zc, jt)) return;
@@ -286,23 +288,19 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
             tma_load_3d(slot(set, kb), &em.sb, &ebar[set], zc, y0, rec.ib * a.n1 + x);
         }
     };
-    uint32_t use[2] = {0u, 0u};
-    issue(0);
+    uint32_t use[kEpiSets] = {0u, 0u, 0u};
+    for (int i = 0; i < nsets - 1 && i < nmine; ++i) issue(i);
     for (int i = 0; i < nmine; ++i) {
         const int set = i % nsets;
         int x, y0, zc, jt;
         const bool valid = unit(i, x, y0, zc, jt);
-        if (nsets == 1 && i > 0) {
-            // single buffer set: the previous unit's reductions must have read it
-            if (lane == 0) bulk_wait_read0();
-            __syncwarp();
-            issue(i);
-        }
-        if (nsets == 2 && i + 1 < nmine) {
-            // the other set was last read by the reductions of unit i - 1
-            if (lane == 0) bulk_wait_read0();
-            __syncwarp();
-            issue(i + 1);
+        if (i + nsets - 1 < nmine) {
+            // set (i - 1) % nsets was last read by the reductions of unit i - 1
+            if (i > 0) {
+                if (lane == 0) bulk_wait_read0();
+                __syncwarp();
+            }
+            issue(i + nsets - 1);
         }
         if (!valid) continue;
         // phi of this lane's row, 32 z (only the columns of this tile)
@@ -354,7 +352,7 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
         __syncwarp();
     }
     // never leave with a load in flight (error path)
-    for (int set = 0; set < 2; ++set)
+    for (int set = 0; set < kEpiSets; ++set)
         if (pending[set]) mbar_drain(&ebar[set], use[set] & 1);
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -818,7 +816,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
-    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin, ebar[8][2];
+    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, s2fin, ebar[8][kEpiSets];
     __shared__ uint32_t tmem_base;
     __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -850,10 +848,8 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         }
         mbar_init(&phidone, a.ns3);
         mbar_init(&s2fin, 1);
-        for (int w = 0; w < 8; ++w) {
-            mbar_init(&ebar[w][0], 1);
-            mbar_init(&ebar[w][1], 1);
-        }
+        for (int w = 0; w < 8; ++w)
+            for (int k = 0; k < kEpiSets; ++k) mbar_init(&ebar[w][k], 1);
         fence_barrier_init();
     }
     // Z tile rows that no copy writes (rows r3..gs-1 of each plane, the tail up to the MMA's N)
