@@ -1133,12 +1133,14 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->ya = (uint32_t)na2 * p->ya_rows * 128u;
     p->zb = (uint32_t)na2 * p->z_rows * 128u;
     p->b3 = (uint32_t)(p->ks3 / 4) * p->n3p * 128u + (uint32_t)(p->ks3 % 4) * p->n3p * 32u;
-    // two rings: nload stages of [A_t2][Z] (stage 2), then up to four of [mu_t A_t3] (stage 3)
+    // two rings: nload stages of [A_t2][Z] (stage 2), then as many stages of [mu_t A_t3]
+    // (stage 3, up to kMaxLoad) as shared memory holds: its loads start only when stage 3 of
+    // an earlier term has finished, so this ring needs the deeper lead
     p->load = (p->ya + p->zb + 1023) & ~1023u;
     p->load3 = (p->b3 + 1023) & ~1023u;
     p->nload = nload;
     p->a3_off = p->load * (uint32_t)nload;
-    for (p->nload3 = std::min(nload, 4); p->nload3 >= 2; --p->nload3) {
+    for (p->nload3 = tcc::kMaxLoad; p->nload3 >= 2; --p->nload3) {
         p->smem = std::max((size_t)p->a3_off + (size_t)p->load3 * p->nload3 + 16384, (size_t)tcc::kEpiBytes) + 1024;
         if (p->smem <= 226 * 1024) return true;
     }
