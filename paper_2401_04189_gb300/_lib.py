@@ -25,7 +25,7 @@ EXPORTED = [
     "tx_check_device_error", "tx_status_string", "tx_last_error_message", "tx_launch_count",
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
-    "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk",
+    "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
     "tx_exchange_apply_static",
 ]
 
@@ -101,6 +101,8 @@ def lib():
     L.tx_set_tile_plan.restype = _I
     L.tx_set_accumulation_chunk.argtypes = [_P, _I]
     L.tx_set_accumulation_chunk.restype = _I
+    L.tx_set_expansion_form.argtypes = [_P, _I]
+    L.tx_set_expansion_form.restype = _I
     L.tx_selftest_gemm.argtypes = [_I, _I, _I, _I, _I, _P, _P, _P, _P]
     L.tx_selftest_gemm.restype = _I
     L.tx_exchange_energy.argtypes = [_P, _P, _I, _P, _P]
@@ -385,6 +387,11 @@ def tx_set_tile_plan(ctx, bx, nstage):
 def tx_set_accumulation_chunk(ctx, terms):
     """Split precisions: Gaussian terms per tensor-core accumulation chunk of phi (0 = default)."""
     _check(lib().tx_set_accumulation_chunk(ctx.handle, int(terms)), "tx_set_accumulation_chunk")
+
+
+def tx_set_expansion_form(ctx, form):
+    """Single-pass precisions: 0 = one CTA per (pair, slab) item (default), 1 = persistent expansion kernel."""
+    _check(lib().tx_set_expansion_form(ctx.handle, int(form)), "tx_set_expansion_form")
 
 
 def tx_launch_count() -> int:

@@ -107,6 +107,13 @@ extern "C" int tx_set_accumulation_chunk(tx_ctx* c, int terms) {
     return TX_OK;
 }
 
+extern "C" int tx_set_expansion_form(tx_ctx* c, int form) {
+    if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
+    if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (one CTA per item) or 1 (persistent)");
+    c->consume_form = form;
+    return TX_OK;
+}
+
 extern "C" int tx_set_tile_plan(tx_ctx* c, int bx, int nstage) {
     if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
     if (bx == 0 && nstage == 0) {

@@ -70,10 +70,14 @@ struct ConsumeArgs {
     const uint8_t* zsrc;
     uint32_t z_plane;          // bytes of one x plane of one term of Z
     int zone;                  // 1: the slab's Z planes load as one box (gs == r3, bx * r3 <= 256 rows)
+    // persistent single-pass kernel: work items (pair, slab), slabs per pair, epilogue region
+    int nitems, nslab;
+    uint32_t epi_off;
 };
 
 constexpr int kThreads = 320;
 constexpr int kThreadsTs = 352;   // single-pass kernel: one more producer warp (10)
+constexpr int kThreadsTp = 384;   // persistent single-pass kernel: a second MMA-issuing warp (11)
 // epilogue shared memory (reuses the pipeline buffers): phi staging, 8 warps x 32 rows x 68
 // floats, then per warp two blocks of orbital values, 8 row pairs x 2 multipliers x 32 lanes
 constexpr uint32_t kStgBytes = 8u * 32u * 68u * 4u;
@@ -1033,6 +1037,328 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
     if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
 }
 
+// Persistent form of the single-pass kernel.  One CTA per SM walks the work items (pair, slab)
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the two load rings and the MMAs run across item
+// boundaries without a break, and the epilogue of item k overlaps the main loop of item k + 1:
+// as soon as the last stage-3 MMA of item k has run, the epilogue warps copy phi from TMEM into
+// registers (each lane one row of one tile, at most 96 columns) and release the accumulator,
+// then combine it with the orbital boxes and reduce into W through the copy engine while the
+// next item accumulates.  Warp roles: 0-7 epilogue, 8 stage-2 producer, 9 stage-2 MMAs and
+// stage 3 of plane 0, 10 stage-3 producer, 11 stage 3 of plane 1 (one warp cannot issue both
+// stages of both planes as fast as the tensor pipe runs them).  Used when every epilogue warp
+// holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
+constexpr int kTpMaxZ = 96;                           // phi registers per epilogue lane
+constexpr uint32_t kTpEpiBytes = 8 * 2 * kEpiBox;     // two 32 x 32 boxes per epilogue warp
+
+template <bool S2TF32, int KS2, int KS3>
+__global__ void __launch_bounds__(kThreadsTp, 1)
+    k_consume_tp(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ EpiMaps em, ConsumeArgs a) {
+    constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
+    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, phifree, s3fin[2], ebar[8];
+    __shared__ uint32_t tmem_base;
+    __shared__ double red[2][8];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NL = a.nload, NL3 = a.nload3, NYB = a.nyb, BX = a.bx, NT = a.nt;
+    const int nmine = (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto item_of = [&](int k, int& pl, int& slab) {
+        const int it = (int)blockIdx.x + k * (int)gridDim.x;
+        pl = it / a.nslab;
+        slab = it - pl * a.nslab;
+    };
+    auto YAs = [&](int s) { return smem + s * a.load_bytes; };
+    auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
+    auto B3s = [&](int s) { return smem + a.a3_off + s * a.load3_bytes; };
+
+    if (threadIdx.x == 0) {
+        // stage-3 commits (empty3, ybar, phidone) come from each of the ns3 plane warps
+        for (int s = 0; s < kMaxLoad; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+            mbar_init(&full3[s], 1);
+            mbar_init(&empty3[s], a.ns3);
+        }
+        for (int b = 0; b < kMaxYBuf; ++b) {
+            mbar_init(&s2bar[b], 1);
+            mbar_init(&ybar[b], a.ns3);
+        }
+        mbar_init(&phidone, a.ns3);
+        mbar_init(&phifree, 8);
+        mbar_init(&s3fin[0], 1);
+        mbar_init(&s3fin[1], 1);
+        for (int w = 0; w < 8; ++w) mbar_init(&ebar[w], 1);
+        fence_barrier_init();
+    }
+    // Z tile rows that no copy writes feed Y columns that stage 3 multiplies by zeros
+    for (int s = 0; s < NL; ++s) {
+        uint4* z = (uint4*)Zs(s);
+        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreadsTp) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    fence_async_smem();
+    if (warp == 8) {
+        tmem_alloc(&tmem_base, a.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
+    const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
+    const int na3f = a.ks3 / 4;
+    const int na2 = (a.ks2 + 3) / 4;
+
+    if (warp == 8) {
+        // ------------------------- stage-2 producer: A_t2 and Z -------------------------
+        int issued = 0, s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k) {
+            int pl, slab;
+            item_of(k, pl, slab);
+            const int x0 = slab * BX;
+            for (int t = 0; t < NT; ++t) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[s], ph ^ 1, a.err, 41));
+                if (!ok) break;
+                ++issued;
+                mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
+                const int zdep = pl * NT + t;
+                bulk_load_w(YAs(s), a.img + (size_t)t * a.img_stride, a.ya_bytes, &full_bar[s]);
+                if (a.zone) {
+                    tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, x0 * a.r3, zdep);
+                    for (int kk = 1; kk < na2; ++kk)
+                        tma_load_3d_w(Zs(s) + kk * z_atom, &mZ, &full_bar[s], kk * AK2, x0 * a.r3, zdep);
+                } else {
+                    for (int kk = 0; kk < na2; ++kk)
+                        for (int p = 0; p < BX; ++p)
+                            tma_load_3d_w(Zs(s) + kk * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s],
+                                          kk * AK2, (x0 + p) * a.r3, zdep);
+                }
+                if (++s == NL) { s = 0; ph ^= 1; }
+            }
+        }
+        if (!ok)
+            for (int g = (issued > NL ? issued - NL : 0); g < issued; ++g) mbar_drain(&full_bar[g % NL], (g / NL) & 1);
+    } else if (warp == 10) {
+        // ---------------- stage-3 producer: mu_t A_t3, and the Z L2 prefetches ----------------
+        const size_t zterm = (size_t)a.n1 * a.z_plane;
+        // global term g = k * nt + t; the prefetch runs nl + 2 terms ahead, across items
+        auto prefetch = [&](int g) {
+            const int k = g / NT, t = g - k * NT;
+            if (k >= nmine) return;
+            int pl, slab;
+            item_of(k, pl, slab);
+            const int x0 = slab * BX;
+            const int np_ = min(BX, a.n1 - x0);
+            bulk_prefetch_l2_w(a.zsrc + ((size_t)pl * NT * a.n1 + x0) * a.z_plane + (size_t)t * zterm,
+                               (uint32_t)np_ * a.z_plane);
+        };
+        for (int g = 1; g <= NL + 2; ++g) prefetch(g);
+        int issued = 0, s = 0, g = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t, ++g) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&empty3[s], ph ^ 1, a.err, 46));
+                if (!ok) break;
+                ++issued;
+                mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
+                bulk_load_w(B3s(s), a.img + (size_t)t * a.img_stride + a.ya_bytes, a.b3_bytes, &full3[s]);
+                if (g > 0) prefetch(g + NL + 2);
+                if (++s == NL3) { s = 0; ph ^= 1; }
+            }
+        if (!ok)
+            for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q) mbar_drain(&full3[q % NL3], (q / NL3) & 1);
+    } else if (warp == 9 || warp == 11) {
+        // ---------------- MMA issuers: warp 9 stage 2 and stage 3 of plane 0, warp 11 stage 3 of
+        // plane 1 (ns3 = 2).  Warp 9 issues stage 3 one term behind its stage 2, so its wait on
+        // the stage-2 commit of that term finds it complete.
+        const int w3 = warp == 9 ? 0 : 1;
+        const uint64_t d0 = sdesc_sw128(0);
+        const int n0 = pad16c(min(a.npc, BX) * a.gs);
+        const uint32_t id0 = S2TF32 ? idesc_tf32(128, n0) : idesc_bf16(128, n0);
+        const uint32_t id3 = idesc_tf32(128, a.n3p);
+        const bool more2 = a.nY > 1 || a.npc < BX;
+        const bool more3 = a.nY > 1 || BX > a.ns3;
+        int s = 0, yb = 0, g = 0, s3 = 0, y3 = 0;
+        uint32_t ph = 0, yph = 0, ph3 = 0, y3ph = 0;
+        bool ok = true;
+        // stage 3 of this warp's planes for the term in Y buffer y3 (term t of local item k)
+        auto stage3 = [&](int t, int k) -> bool {
+            bool w = mbar_wait(&s2bar[y3], y3ph, a.err, 44);
+            if (w) w = mbar_wait(&full3[s3], ph3, a.err, 48);
+            // the accumulator is free once the epilogue of the previous item holds phi
+            if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
+            if (!__all_sync(0xffffffffu, w)) return false;
+            tc_fence_after();
+            const uint64_t b3 = d0 + (smem_u32(B3s(s3)) >> 4);
+            const uint64_t b3t = sdesc_sw32(0) + (smem_u32(B3s(s3) + na3f * b3_atom) >> 4);
+            const uint32_t tY = tmem + (uint32_t)y3 * a.y_cols;
+            const uint32_t acc0 = t > 0 ? 1u : 0u;
+            s3_mmas<KS3>(a.ks3, tPhi + (uint32_t)(w3 * a.nY * a.n3p), tY + (uint32_t)(w3 * a.gs), b3, b3t, b3_atom >> 4,
+                         (uint32_t)a.n3p * 2u, id3, acc0);
+            if (more3)
+                for (int p = w3; p < BX; p += a.ns3)
+                    for (int i = (p == w3 ? 1 : 0); i < a.nY; ++i)
+                        s3_mmas<KS3>(a.ks3, tPhi + (uint32_t)((p * a.nY + i) * a.n3p), tY + (uint32_t)(i * a.ycol_tile + p * a.gs),
+                                     b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
+            mma_commit_w(&ybar[y3]);
+            mma_commit_w(&empty3[s3]);
+            if (t == NT - 1) mma_commit_w(&phidone);
+            if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
+            if (++y3 == NYB) { y3 = 0; y3ph ^= 1; }
+            return true;
+        };
+        if (warp == 11) {
+            if (w3 < a.ns3)
+                for (int k = 0; k < nmine && ok; ++k)
+                    for (int t = 0; t < NT && ok; ++t) ok = stage3(t, k);
+        } else {
+            int pt = -1, pk = 0;     // the term whose stage 3 is pending
+            for (int k = 0; k < nmine && ok; ++k)
+                for (int t = 0; t < NT; ++t, ++g) {
+                    bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
+                    // Y buffer yb was last read by stage 3 of term g - nyb
+                    if (w && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
+                    ok = __all_sync(0xffffffffu, w);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
+                    const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
+                    s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
+                    if (more2)
+                        for (int i = 0; i < a.nY; ++i)
+                            for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
+                                const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                                const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                                s2_mmas<S2TF32, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs),
+                                                     ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u,
+                                                     ya_atom >> 4, z_atom >> 4, id2);
+                            }
+                    mma_commit_w(&s2bar[yb]);
+                    mma_commit_w(&empty_bar[s]);
+                    if (++s == NL) { s = 0; ph ^= 1; }
+                    if (++yb == NYB) { yb = 0; yph ^= 1; }
+                    if (pt >= 0 && !(ok = stage3(pt, pk))) break;
+                    pt = t;
+                    pk = k;
+                }
+            if (ok && pt >= 0) stage3(pt, pk);
+        }
+        // the CTA must not release TMEM while these MMAs run
+        mma_commit_w(&s3fin[w3]);
+        mbar_drain(&s3fin[w3], 0);
+    } else {
+        // ---------------- epilogue warps 0-7: one tile (plane / y tile) per warp ----------------
+        const int q = warp & 3, jt = warp >> 2;
+        uint8_t* b0 = smem + a.epi_off + warp * 2 * kEpiBox;
+        uint8_t* b1 = b0 + kEpiBox;
+        uint32_t eph = 0;
+        for (int k = 0; k < nmine; ++k) {
+            // on an error every later wait returns at once; the warps still meet at the named
+            // barrier below once per item, so none of them is left waiting there
+            const bool live = mbar_wait_idle(&phidone, (uint32_t)(k & 1), a.err, 45);
+            tc_fence_after();
+            int pl, slab;
+            item_of(k, pl, slab);
+            const int x0 = slab * BX;
+            const PairRec rec = a.recs[a.p0 + pl];
+            // phi of this lane's row of tile jt, into registers; then release the accumulator
+            uint32_t phr[kTpMaxZ];
+            const bool has = live && jt < a.nT3;
+            if (has) {
+#pragma unroll
+                for (int c = 0; c < kTpMaxZ / 16; ++c)
+                    if (16 * c < a.n3p)
+                        tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + 16 * c),
+                                  *(uint32_t(*)[16]) & phr[16 * c]);
+                tmem_ld_wait();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&phifree);
+            double e = 0.0;
+            const int p = jt / a.nY, x = x0 + p, y0 = (jt - p * a.nY) * 128 + q * 32;
+            const bool en = (a.flags & EPI_ENERGY) != 0;
+            const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0;
+            const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
+            const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
+            if (has && x < a.n1 && y0 < a.n2 && (need0 || need1)) {
+                const int y = y0 + lane;
+                const bool rowin = y < a.n2;
+                const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
+                const int nbx = (need0 ? 1 : 0) + (need1 ? 1 : 0);
+                uint8_t* s0 = b0;
+                uint8_t* s1 = need0 ? b1 : b0;
+#pragma unroll
+                for (int ch = 0; ch < kTpMaxZ / 32; ++ch) {
+                    const int zc = 32 * ch;
+                    if (zc >= a.n3) break;
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&ebar[warp], (uint32_t)nbx * kEpiBox);
+                        if (need0) tma_load_3d(s0, &em.m0, &ebar[warp], zc, y0, rec.m0 * a.n1 + x);
+                        if (need1) tma_load_3d(s1, &em.m1, &ebar[warp], zc, y0, rec.m1 * a.n1 + x);
+                    }
+                    const bool w = mbar_wait(&ebar[warp], eph, a.err, 49);
+                    eph ^= 1;
+                    if (!__all_sync(0xffffffffu, w)) break;
+                    float eb = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int z = zc + 4 * c;
+                        const uint32_t off = (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4);
+                        float4 phi = make_float4(__uint_as_float(phr[zc + 4 * c]), __uint_as_float(phr[zc + 4 * c + 1]),
+                                                 __uint_as_float(phr[zc + 4 * c + 2]), __uint_as_float(phr[zc + 4 * c + 3]));
+                        if (z >= a.n3p) phi = make_float4(0.f, 0.f, 0.f, 0.f);     // registers past the tile
+                        const float4 w3 = (rowin && z < a.n3) ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+                        float4 f = phi;
+                        if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+                        const float4 m0 = need0 ? *(const float4*)(s0 + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 m1 = need1 ? *(const float4*)(s1 + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (o0) *(float4*)(s0 + off) = make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w);
+                        if (o1) *(float4*)(s1 + off) = make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w);
+                        if (en && a.emul && rowin && z < a.n3)
+                            eb += wv.x * m1.x * m0.x * phi.x + wv.y * m1.y * m0.y * phi.y + wv.z * m1.z * m0.z * phi.z +
+                                  wv.w * m1.w * m0.w * phi.w;
+                    }
+                    e += (double)eb;
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (o0 || o1) {
+                            if (o0) tma_reduce_add_3d(&em.o0, s0, zc, y0, rec.o0 * a.n1 + x);
+                            if (o1) tma_reduce_add_3d(&em.o1, s1, zc, y0, rec.o1 * a.n1 + x);
+                            bulk_commit();
+                        }
+                        // the next chunk reloads these buffers
+                        bulk_wait_read0();
+                    }
+                    __syncwarp();
+                }
+            }
+            if (a.flags & EPI_ENERGY) {
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+                if (lane == 0) red[k & 1][warp] = e * rec.ew;
+            }
+            // the eight epilogue warps meet once per item (named barrier 1): energy partial
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if ((a.flags & EPI_ENERGY) && warp == 0 && lane == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < 8; ++w) sum += red[k & 1][w];
+                a.epart[(long)pl * a.nslab + slab] = sum;
+            }
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
+}
+
 // Image of the per-term operator tiles of the single-pass kernel, built once per context:
 // [A_t2 tile][mu_t A_t3 tile] for every term t, byte for byte as the tensor-map loads of a load
 // stage lay them out (128-byte swizzle, the 32-byte-swizzled K tail of mu_t A_t3, zero fill).
@@ -1388,8 +1714,6 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         a.zone = (p.gs == r3 && p.bx * r3 <= 256) ? 1 : 0;
         TX_TRY(make_map(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b,
                         AK2, (uint32_t)(a.zone ? p.bx * r3 : r3)));
-        // instantiations with compile-time K step counts for ranks 32, 40, 48 and 64; any other
-        // rank runs the dispatching form (see s2_mmas / s3_mmas)
         // epilogue tensors [orbital * n1 + x][y][z]: absent arrays take a valid stand-in map
         tcc::EpiMaps em;
         auto orb_map = [&](CUtensorMap* m, const float* base, int norb) -> int {
@@ -1407,16 +1731,57 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         TX_TRY(orb_map(&em.o0, OUT0, cnt.out0));
         TX_TRY(orb_map(&em.o1, OUT1, cnt.out1));
         if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
+        // Persistent form on request (the epilogue of one item overlaps the main loop of the
+        // next), where each epilogue warp holds one tile of phi in registers and the energy
+        // factors are the multipliers; it needs its own shared-memory split (rings + epilogue)
+        bool tp = c->consume_form == 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
+                  (!(flags & EPI_ENERGY) || a.emul);
+        size_t smem = p.smem;
+        if (tp) {
+            const int nl1 = std::min(p.nload, 4);
+            const uint32_t a3_off = p.load * (uint32_t)nl1;
+            int nl3 = tcc::kMaxLoad;
+            while (nl3 >= 2 && (size_t)a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 > 226 * 1024) --nl3;
+            if (nl3 >= 2) {
+                a.nload = nl1;
+                a.a3_off = a3_off;
+                a.nload3 = nl3;
+                a.epi_off = a3_off + (uint32_t)nl3 * p.load3;
+                smem = (size_t)a.epi_off + tcc::kTpEpiBytes + 1024;
+            } else {
+                tp = false;
+            }
+        }
+        // instantiations with compile-time K step counts for ranks 32, 40, 48 and 64; any other
+        // rank runs the dispatching form (see s2_mmas / s3_mmas)
         using Kern = void (*)(const CUtensorMap, const tcc::EpiMaps, tcc::ConsumeArgs);
-        Kern kern = op->tf32 ? (Kern)tcc::k_consume_ts<true, 0, 0> : (Kern)tcc::k_consume_ts<false, 0, 0>;
+        Kern kern;
+        if (tp) {
+            kern = op->tf32 ? (Kern)tcc::k_consume_tp<true, 0, 0> : (Kern)tcc::k_consume_tp<false, 0, 0>;
+#define TX_TP_CASE(TF, K2, K3) \
+    if (op->tf32 == TF && p.ks2 == K2 && p.ks3 == K3) kern = tcc::k_consume_tp<TF, K2, K3>;
+            TX_TP_CASE(false, 2, 4) TX_TP_CASE(false, 3, 5) TX_TP_CASE(false, 3, 6) TX_TP_CASE(false, 4, 8)
+            TX_TP_CASE(true, 4, 4) TX_TP_CASE(true, 5, 5) TX_TP_CASE(true, 6, 6) TX_TP_CASE(true, 8, 8)
+#undef TX_TP_CASE
+        } else {
+            kern = op->tf32 ? (Kern)tcc::k_consume_ts<true, 0, 0> : (Kern)tcc::k_consume_ts<false, 0, 0>;
 #define TX_TS_CASE(TF, K2, K3) \
     if (op->tf32 == TF && p.ks2 == K2 && p.ks3 == K3) kern = tcc::k_consume_ts<TF, K2, K3>;
-        TX_TS_CASE(false, 2, 4) TX_TS_CASE(false, 3, 5) TX_TS_CASE(false, 3, 6) TX_TS_CASE(false, 4, 8)
-        TX_TS_CASE(true, 4, 4) TX_TS_CASE(true, 5, 5) TX_TS_CASE(true, 6, 6) TX_TS_CASE(true, 8, 8)
+            TX_TS_CASE(false, 2, 4) TX_TS_CASE(false, 3, 5) TX_TS_CASE(false, 3, 6) TX_TS_CASE(false, 4, 8)
+            TX_TS_CASE(true, 4, 4) TX_TS_CASE(true, 5, 5) TX_TS_CASE(true, 6, 6) TX_TS_CASE(true, 8, 8)
 #undef TX_TS_CASE
+        }
+        a.nslab = (int)grid.x;
+        a.nitems = (int)grid.x * np;
+        if (tp) {
+            int dev = 0, nsm = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            grid = dim3((unsigned)std::min(a.nitems, nsm));
+        }
         const int ps = prof_begin("tc_consume", s);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-        kern<<<grid, tcc::kThreadsTs, p.smem, s>>>(mZ, em, a);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, tp ? tcc::kThreadsTp : tcc::kThreadsTs, smem, s>>>(mZ, em, a);
         prof_end(ps, s);
         TX_LAUNCHED();
         return TX_OK;

@@ -203,3 +203,38 @@ def test_accumulation_chunk_bounds_the_accumulator_error(prec):
     assert errs[1] <= errs[1000] * 1.02
     with pytest.raises(P.TuckerExchangeError):
         P.tx_set_accumulation_chunk(P.Context.from_system(s, precision=prec), -1)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("system", ["small", "ragged", "pt8"])
+def test_expansion_forms_agree(prec, system):
+    """The one-CTA-per-item expansion kernel (default) and the persistent kernel give the same
+    apply and energy, and both match the oracle."""
+    P = _P()
+    if system == "small":
+        s = W.config_small()
+    elif system == "ragged":
+        s = ragged_system()
+    else:
+        s = W.config_pt(n_orb=8)
+    S = O.Setup.from_system(s)
+    outs, energies = [], []
+    for form in (0, 1):
+        ctx = P.Context.from_system(s, precision=prec)
+        P.tx_set_expansion_form(ctx, form)
+        occ = to_gpu(s.psi)
+        outs.append(P.tx_exchange_apply(ctx, occ).cpu().numpy())
+        energies.append(float(P.tx_exchange_energy(ctx, occ).item()))
+        ctx.check_device_error()
+    assert rel(outs[0], outs[1]) < 1e-5
+    assert abs(energies[0] - energies[1]) <= 1e-5 * abs(energies[1])
+    if system != "pt8":
+        ref = O.exchange_apply(s.psi, S)
+        assert rel(outs[0], ref) < W_TOL[prec]
+        e_ref = O.exchange_energy(s.psi, S)
+        assert abs(energies[0] - e_ref) / abs(e_ref) < E_TOL[prec]
+    else:
+        ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
+        assert rel(outs[0][3:4], ref) < W_TOL[prec]
+    with pytest.raises(P.TuckerExchangeError):
+        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
