@@ -210,13 +210,12 @@ int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
 int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
 
 /* Single-pass precisions (BF16, TF32): form of the expansion kernel (the final contraction of
- * Eq. final, fused with the Hadamard product and the sum over j).  0 (default): one CTA per
- * (pair, x slab) work item.  1: persistent -- one CTA per SM walks the work items and the
- * epilogue of one item overlaps the MMAs of the next; it applies where every epilogue warp holds
- * one phi tile (at most two x planes per CTA, n3 <= 96 after padding to 16) and the energy
- * factors equal the multipliers, and falls back to form 0 elsewhere.  Form 1 is slower than
- * form 0 on the Pt-shaped block at present (its main loop issues from fewer warps).  Both give
- * the same result up to float32 summation order.  TX_ERR_INVALID_ARG outside 0..1. */
+ * Eq. final, fused with the Hadamard product and the sum over j).  0 (default): automatic --
+ * the persistent form, in which one CTA per SM walks the (pair, x slab) work items and the
+ * epilogue of one item overlaps the MMAs of the next, wherever its limits hold (at most two x
+ * planes per CTA, n3 <= 96 after padding to 16, energy factors equal to the multipliers); one
+ * CTA per work item elsewhere.  1: always one CTA per work item.  Both give the same result
+ * up to float32 summation order.  TX_ERR_INVALID_ARG outside 0..1. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
 /*

@@ -390,7 +390,7 @@ def tx_set_accumulation_chunk(ctx, terms):
 
 
 def tx_set_expansion_form(ctx, form):
-    """Single-pass precisions: 0 = one CTA per (pair, slab) item (default), 1 = persistent expansion kernel."""
+    """Single-pass precisions: 0 = automatic (persistent expansion kernel where it applies, default), 1 = one CTA per item."""
     _check(lib().tx_set_expansion_form(ctx.handle, int(form)), "tx_set_expansion_form")
 
 

@@ -109,7 +109,7 @@ extern "C" int tx_set_accumulation_chunk(tx_ctx* c, int terms) {
 
 extern "C" int tx_set_expansion_form(tx_ctx* c, int form) {
     if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
-    if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (one CTA per item) or 1 (persistent)");
+    if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic) or 1 (one CTA per item)");
     c->consume_form = form;
     return TX_OK;
 }

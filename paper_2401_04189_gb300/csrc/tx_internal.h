@@ -108,7 +108,7 @@ struct tx_ctx {
     cudaStream_t last_stream;
     int tile_bx, tile_nstage;   // forced expansion tile plan (0 = built-in choice)
     int acc_chunk;              // split precisions: Gaussian terms per phi accumulation chunk (0 = default)
-    int consume_form;           // single-pass expansion: 0 = one CTA per work item, 1 = persistent
+    int consume_form;           // single-pass expansion: 0 = automatic (persistent where it applies), 1 = one CTA per item
 };
 
 namespace tx {

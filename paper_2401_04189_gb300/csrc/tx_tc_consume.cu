@@ -77,7 +77,7 @@ struct ConsumeArgs {
 
 constexpr int kThreads = 320;
 constexpr int kThreadsTs = 352;   // single-pass kernel: one more producer warp (10)
-constexpr int kThreadsTp = 384;   // persistent single-pass kernel: a second MMA-issuing warp (11)
+constexpr int kThreadsTp = 384;   // persistent single-pass kernel: a separate stage-3 warp (11)
 // epilogue shared memory (reuses the pipeline buffers): phi staging, 8 warps x 32 rows x 68
 // floats, then per warp two blocks of orbital values, 8 row pairs x 2 multipliers x 32 lanes
 constexpr uint32_t kStgBytes = 8u * 32u * 68u * 4u;
@@ -1043,10 +1043,9 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
 // as soon as the last stage-3 MMA of item k has run, the epilogue warps copy phi from TMEM into
 // registers (each lane one row of one tile, at most 96 columns) and release the accumulator,
 // then combine it with the orbital boxes and reduce into W through the copy engine while the
-// next item accumulates.  Warp roles: 0-7 epilogue, 8 stage-2 producer, 9 stage-2 MMAs and
-// stage 3 of plane 0, 10 stage-3 producer, 11 stage 3 of plane 1 (one warp cannot issue both
-// stages of both planes as fast as the tensor pipe runs them).  Used when every epilogue warp
-// holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
+// next item accumulates.  Warp roles: 0-7 epilogue, 8 stage-2 producer, 9 stage-2 MMAs, 10
+// stage-3 producer and Z prefetches, 11 stage-3 MMAs of every plane.  Used when every epilogue
+// warp holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
 constexpr int kTpMaxZ = 96;                           // phi registers per epilogue lane
 constexpr uint32_t kTpEpiBytes = 8 * 2 * kEpiBox;     // two 32 x 32 boxes per epilogue warp
 
@@ -1073,18 +1072,17 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     auto B3s = [&](int s) { return smem + a.a3_off + s * a.load3_bytes; };
 
     if (threadIdx.x == 0) {
-        // stage-3 commits (empty3, ybar, phidone) come from each of the ns3 plane warps
         for (int s = 0; s < kMaxLoad; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
             mbar_init(&full3[s], 1);
-            mbar_init(&empty3[s], a.ns3);
+            mbar_init(&empty3[s], 1);
         }
         for (int b = 0; b < kMaxYBuf; ++b) {
             mbar_init(&s2bar[b], 1);
-            mbar_init(&ybar[b], a.ns3);
+            mbar_init(&ybar[b], 1);
         }
-        mbar_init(&phidone, a.ns3);
+        mbar_init(&phidone, 1);
         mbar_init(&phifree, 8);
         mbar_init(&s3fin[0], 1);
         mbar_init(&s3fin[1], 1);
@@ -1171,85 +1169,76 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             }
         if (!ok)
             for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q) mbar_drain(&full3[q % NL3], (q / NL3) & 1);
-    } else if (warp == 9 || warp == 11) {
-        // ---------------- MMA issuers: warp 9 stage 2 and stage 3 of plane 0, warp 11 stage 3 of
-        // plane 1 (ns3 = 2).  Warp 9 issues stage 3 one term behind its stage 2, so its wait on
-        // the stage-2 commit of that term finds it complete.
-        const int w3 = warp == 9 ? 0 : 1;
+    } else if (warp == 9) {
+        // ------------------------------ stage-2 MMA issuer ------------------------------
         const uint64_t d0 = sdesc_sw128(0);
         const int n0 = pad16c(min(a.npc, BX) * a.gs);
         const uint32_t id0 = S2TF32 ? idesc_tf32(128, n0) : idesc_bf16(128, n0);
-        const uint32_t id3 = idesc_tf32(128, a.n3p);
         const bool more2 = a.nY > 1 || a.npc < BX;
-        const bool more3 = a.nY > 1 || BX > a.ns3;
-        int s = 0, yb = 0, g = 0, s3 = 0, y3 = 0;
-        uint32_t ph = 0, yph = 0, ph3 = 0, y3ph = 0;
+        int s = 0, yb = 0, g = 0;
+        uint32_t ph = 0, yph = 0;
         bool ok = true;
-        // stage 3 of this warp's planes for the term in Y buffer y3 (term t of local item k)
-        auto stage3 = [&](int t, int k) -> bool {
-            bool w = mbar_wait(&s2bar[y3], y3ph, a.err, 44);
-            if (w) w = mbar_wait(&full3[s3], ph3, a.err, 48);
-            // the accumulator is free once the epilogue of the previous item holds phi
-            if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
-            if (!__all_sync(0xffffffffu, w)) return false;
-            tc_fence_after();
-            const uint64_t b3 = d0 + (smem_u32(B3s(s3)) >> 4);
-            const uint64_t b3t = sdesc_sw32(0) + (smem_u32(B3s(s3) + na3f * b3_atom) >> 4);
-            const uint32_t tY = tmem + (uint32_t)y3 * a.y_cols;
-            const uint32_t acc0 = t > 0 ? 1u : 0u;
-            s3_mmas<KS3>(a.ks3, tPhi + (uint32_t)(w3 * a.nY * a.n3p), tY + (uint32_t)(w3 * a.gs), b3, b3t, b3_atom >> 4,
-                         (uint32_t)a.n3p * 2u, id3, acc0);
-            if (more3)
-                for (int p = w3; p < BX; p += a.ns3)
-                    for (int i = (p == w3 ? 1 : 0); i < a.nY; ++i)
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t, ++g) {
+                bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
+                // Y buffer yb was last read by stage 3 of term g - nyb
+                if (w && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
+                ok = __all_sync(0xffffffffu, w);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
+                const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
+                s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
+                if (more2)
+                    for (int i = 0; i < a.nY; ++i)
+                        for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
+                            const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                            const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                            s2_mmas<S2TF32, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs),
+                                                 ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u, ya_atom >> 4,
+                                                 z_atom >> 4, id2);
+                        }
+                mma_commit_w(&s2bar[yb]);
+                mma_commit_w(&empty_bar[s]);
+                if (++s == NL) { s = 0; ph ^= 1; }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
+            }
+        // the CTA must not release TMEM while these MMAs run
+        mma_commit_w(&s3fin[0]);
+        mbar_drain(&s3fin[0], 0);
+    } else if (warp == 11) {
+        // ---------------- stage-3 MMA issuer: every plane and y tile ----------------
+        const uint64_t d0 = sdesc_sw128(0);
+        const uint32_t id3 = idesc_tf32(128, a.n3p);
+        int s3 = 0, yb = 0;
+        uint32_t ph3 = 0, yph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t) {
+                bool w = mbar_wait(&s2bar[yb], yph, a.err, 44);
+                if (w) w = mbar_wait(&full3[s3], ph3, a.err, 48);
+                // the accumulator is free once the epilogue of the previous item holds phi
+                if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
+                ok = __all_sync(0xffffffffu, w);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t b3 = d0 + (smem_u32(B3s(s3)) >> 4);
+                const uint64_t b3t = sdesc_sw32(0) + (smem_u32(B3s(s3) + na3f * b3_atom) >> 4);
+                const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
+                const uint32_t acc0 = t > 0 ? 1u : 0u;
+                for (int p = 0; p < BX; ++p)
+                    for (int i = 0; i < a.nY; ++i)
                         s3_mmas<KS3>(a.ks3, tPhi + (uint32_t)((p * a.nY + i) * a.n3p), tY + (uint32_t)(i * a.ycol_tile + p * a.gs),
                                      b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
-            mma_commit_w(&ybar[y3]);
-            mma_commit_w(&empty3[s3]);
-            if (t == NT - 1) mma_commit_w(&phidone);
-            if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
-            if (++y3 == NYB) { y3 = 0; y3ph ^= 1; }
-            return true;
-        };
-        if (warp == 11) {
-            if (w3 < a.ns3)
-                for (int k = 0; k < nmine && ok; ++k)
-                    for (int t = 0; t < NT && ok; ++t) ok = stage3(t, k);
-        } else {
-            int pt = -1, pk = 0;     // the term whose stage 3 is pending
-            for (int k = 0; k < nmine && ok; ++k)
-                for (int t = 0; t < NT; ++t, ++g) {
-                    bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
-                    // Y buffer yb was last read by stage 3 of term g - nyb
-                    if (w && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
-                    ok = __all_sync(0xffffffffu, w);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
-                    const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
-                    s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
-                    if (more2)
-                        for (int i = 0; i < a.nY; ++i)
-                            for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
-                                const int N = pad16c(min(a.npc, BX - p0) * a.gs);
-                                const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
-                                s2_mmas<S2TF32, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs),
-                                                     ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u,
-                                                     ya_atom >> 4, z_atom >> 4, id2);
-                            }
-                    mma_commit_w(&s2bar[yb]);
-                    mma_commit_w(&empty_bar[s]);
-                    if (++s == NL) { s = 0; ph ^= 1; }
-                    if (++yb == NYB) { yb = 0; yph ^= 1; }
-                    if (pt >= 0 && !(ok = stage3(pt, pk))) break;
-                    pt = t;
-                    pk = k;
-                }
-            if (ok && pt >= 0) stage3(pt, pk);
-        }
+                mma_commit_w(&ybar[yb]);
+                mma_commit_w(&empty3[s3]);
+                if (t == NT - 1) mma_commit_w(&phidone);
+                if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
+            }
         // the CTA must not release TMEM while these MMAs run
-        mma_commit_w(&s3fin[w3]);
-        mbar_drain(&s3fin[w3], 0);
+        mma_commit_w(&s3fin[1]);
+        mbar_drain(&s3fin[1], 0);
     } else {
         // ---------------- epilogue warps 0-7: one tile (plane / y tile) per warp ----------------
         const int q = warp & 3, jt = warp >> 2;
@@ -1731,10 +1720,10 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         TX_TRY(orb_map(&em.o0, OUT0, cnt.out0));
         TX_TRY(orb_map(&em.o1, OUT1, cnt.out1));
         if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
-        // Persistent form on request (the epilogue of one item overlaps the main loop of the
-        // next), where each epilogue warp holds one tile of phi in registers and the energy
-        // factors are the multipliers; it needs its own shared-memory split (rings + epilogue)
-        bool tp = c->consume_form == 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
+        // Persistent form (the epilogue of one item overlaps the main loop of the next) where
+        // each epilogue warp holds one tile of phi in registers and the energy factors are the
+        // multipliers; it needs its own shared-memory split (rings + epilogue boxes)
+        bool tp = c->consume_form != 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
                   (!(flags & EPI_ENERGY) || a.emul);
         size_t smem = p.smem;
         if (tp) {

@@ -208,8 +208,8 @@ def test_accumulation_chunk_bounds_the_accumulator_error(prec):
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 @pytest.mark.parametrize("system", ["small", "ragged", "pt8"])
 def test_expansion_forms_agree(prec, system):
-    """The one-CTA-per-item expansion kernel (default) and the persistent kernel give the same
-    apply and energy, and both match the oracle."""
+    """The persistent expansion kernel (default where it applies) and the one-CTA-per-item
+    kernel give the same apply and energy, and both match the oracle."""
     P = _P()
     if system == "small":
         s = W.config_small()
