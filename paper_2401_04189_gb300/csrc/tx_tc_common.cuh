@@ -65,48 +65,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     }
 }
 
-// Non-blocking probe of a phase (mbarrier.test_wait never suspends the thread).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for a phase that is expected within microseconds, by spinning on test_wait: a thread
-// suspended in try_wait can take a long time to resume after the phase completes, which
-// costs the latency-critical hand-offs between the MMA issuing warps.
-__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity, int* err, int site) {
-    if (mbar_test_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    while (true) {
-#pragma unroll 1
-        for (int i = 0; i < 64; ++i)
-            if (mbar_test_wait(bar, parity)) return true;
-        if (*(volatile int*)err != 0) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) {
-            if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
-            return false;
-        }
-    }
-}
-
-// Wait by a whole warp that issues on the phase: lane 0 spins on test_wait (32 lanes probing
-// one mbarrier serialize in the shared-memory pipe; a lane suspended in try_wait resumes
-// late), the result is broadcast and __syncwarp orders the other lanes after the phase.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int* err, int site) {
-    bool ok = true;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait_spin(bar, parity, err, site);
-    ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-    __syncwarp();
-    return ok;
-}
-
 // For long waits by warps that have nothing else to do (an epilogue waiting for the whole
 // main loop): each probe suspends the thread for up to `hint_ns` unless the phase completes
 // first, so idle warps do not keep the shared-memory pipe busy with polls.
@@ -229,15 +187,6 @@ __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t adesc, uint64_t
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
     }
 }
-// tcgen05.mma kind::tf32 with A read from TMEM: row m of A is TMEM lane m, K element k is the
-// 32-bit column k (the operand is the float32 value; the tensor core uses its TF32 bits)
-__device__ __forceinline__ void mma_ts_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc));
-}
 // ---------------------------------------------------------------------------------------
 // Warp-uniform forms: the whole warp executes the call with identical operands and one
 // elected lane issues the instruction.  Operands that all lanes compute alike can live in
@@ -258,6 +207,8 @@ __device__ __forceinline__ void mma_ss_w(uint32_t d_tmem, uint64_t adesc, uint64
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
     }
 }
+// tcgen05.mma kind::tf32 with A read from TMEM: row m of A is TMEM lane m, K element k is the
+// 32-bit column k (the operand is the float32 value; the tensor core uses its TF32 bits)
 __device__ __forceinline__ void mma_ts_tf32_w(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
                                               uint32_t acc) {
     asm volatile(
@@ -277,13 +228,6 @@ __device__ __forceinline__ void tma_load_3d_w(void* dst, const CUtensorMap* m, u
         "@e cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n\t}\n" ::"r"(
             smem_u32(dst)),
         "l"((uint64_t)m), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_l2_3d_w(const CUtensorMap* m, int c0, int c1, int c2) {
-    asm volatile(
-        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
-        "@e cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];\n\t}\n" ::"l"((uint64_t)m), "r"(c0), "r"(c1),
-        "r"(c2)
         : "memory");
 }
 // Plain (untiled) bulk copy of `bytes` contiguous global bytes into shared memory, completing
