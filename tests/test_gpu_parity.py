@@ -238,3 +238,21 @@ def test_expansion_forms_agree(prec, system):
         assert rel(outs[0][3:4], ref) < W_TOL[prec]
     with pytest.raises(P.TuckerExchangeError):
         P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_large_grid_two_y_tiles(prec):
+    """n = 160 (two 128-row y tiles per plane, n3 past the persistent kernel's 96 columns) at
+    rank 64 (the K-step counts of the TiO2-shaped workload): apply and energy against the oracle."""
+    P = _P()
+    s = W.config_small(n=160, n_orb=2, rank=64, T=6, L=16.0)
+    S = O.Setup.from_system(s)
+    ref = O.exchange_apply(s.psi, S)
+    ctx = P.Context.from_system(s, precision=prec)
+    occ = to_gpu(s.psi)
+    got = P.tx_exchange_apply(ctx, occ).cpu().numpy()
+    e = float(P.tx_exchange_energy(ctx, occ).item())
+    ctx.check_device_error()
+    assert rel(got, ref) < W_TOL[prec]
+    e_ref = O.exchange_energy(s.psi, S)
+    assert abs(e - e_ref) / abs(e_ref) < E_TOL[prec]
