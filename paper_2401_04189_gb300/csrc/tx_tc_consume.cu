@@ -6,18 +6,19 @@
 //     phi[(x,y)][z] += sum_g Y_t[(x,y)][g] (mu_t A_t3)[z][g]        stage 3 -> TMEM (all t)
 //   out0[o0] -= mul0[m0] * phi,  out1[o1] -= mul1[m1] * phi,  energy += ew * w * psi_a psi_b phi
 //
-// Z_t = G x1 A_t1 comes from the first-mode GEMM.  The split precisions run k_consume below
-// (the single-pass precisions run k_consume_ts, described at its definition).  Stage 2 puts y
-// on the TMEM lanes and g on the columns, so each converter lane already holds one row (x, y) of the K-major stage-3
-// operand: it rounds the row to the operand type and writes it with 16-byte stores.  Each x
-// plane has its own TMEM columns and its own full / free barriers, so the MMA of plane p for
-// the next term starts as soon as plane p has been converted.  phi stays in TMEM across every
-// term and is read once by the epilogue.
-//
-// Operand tiles use the 32-byte swizzle: one sub-tile of `rows x 32 bytes` per MMA K-step, so K
-// is padded only to the K-step (48 for r = 40 in bf16, none for TF32), and the load stages are
-// small enough for three of them to be in flight.  Warp roles: 0-7 converters + epilogue,
-// 8 TMA producer + TMEM owner, 9 MMA issuer.
+// Z_t = G x1 A_t1 comes from the first-mode GEMM.  Three kernels:
+//  - k_consume (the split precisions, below): stage 2 puts y on the TMEM lanes and g on the
+//    columns, so each converter lane already holds one row (x, y) of the K-major stage-3
+//    operand: it splits the row into hi and lo and writes them with 16-byte stores.  Each x
+//    plane has its own TMEM columns and its own full / free barriers, so the MMA of plane p for
+//    the next term starts as soon as plane p has been converted.  Operand tiles use the 32-byte
+//    swizzle: one sub-tile of `rows x 32 bytes` per MMA K-step, so K is padded only to the
+//    K-step.  Warp roles: 0-7 converters + epilogue, 8 TMA producer + TMEM owner, 9 MMA issuer.
+//  - k_consume_ts (single-pass precisions): stage 3 reads Y straight from TMEM; one CTA per
+//    (pair, slab) work item (described at its definition).
+//  - k_consume_tp: the same loop, persistent over the work items, with the epilogue of one item
+//    overlapping the main loop of the next (described at its definition).
+// phi stays in TMEM across the terms it accumulates and is read once by the epilogue.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -804,9 +805,9 @@ __device__ __forceinline__ void s3_mmas(int ks, uint32_t d, uint32_t aT, uint64_
 // plane; so stage 3 is one 128-row MMA tile per plane, and no warp touches Y.
 //
 // Schedule.  Warp 9 issues stage 2 of every term into nyb rotating Y buffers; warps 0..ns3-1
-// issue stage 3, one x plane each, as soon as the term's stage 2 has finished.  A warp needs
-// more time to issue a tcgen05.mma than the tensor pipe needs to run one of these small
-// tiles, so the stage-3 streams are issued in parallel.
+// issue stage 3, one x plane each, as soon as the term's stage 2 has finished, and then run
+// the epilogue with warps 1..7.  A warp needs more time to issue a tcgen05.mma than the tensor
+// pipe needs to run one of these small tiles, so the stage-3 streams are issued in parallel.
 //
 // Loads.  Operand tiles use the 128-byte swizzle.  The stage-2 operands (A_t2 tile and the
 // slab's Z planes) and the stage-3 operand (mu_t A_t3) travel in two separate rings of load
