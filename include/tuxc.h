@@ -23,7 +23,8 @@
  *
  * Conventions for every entry point
  *  - Orbital blocks are float32, C-contiguous [count][n1][n2][n3] (z fastest), in device
- *    memory of the current CUDA device, 16-byte aligned.  Outputs must not alias inputs.
+ *    memory of the current CUDA device, 16-byte aligned.  Outputs must not overlap inputs
+ *    (an overlap is rejected with TX_ERR_INVALID_ARG).
  *  - Every call is asynchronous on the caller's stream; nothing is synchronised.  Scalars
  *    (energies) are written to caller-owned device memory.
  *  - Every call returns a status: TX_OK (0) or a negative TX_ERR_* code.  Arguments are

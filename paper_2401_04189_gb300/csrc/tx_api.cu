@@ -345,6 +345,16 @@ static int check_block(const float* p, int count, const char* what) {
     return TX_OK;
 }
 
+// an output block must share no memory with an input block (orbital blocks of n3 = N3 floats)
+static int check_no_alias(const tx_ctx* c, const float* out, int n_out, const float* in, int n_in, const char* what) {
+    if (!out || !in || n_out <= 0 || n_in <= 0) return TX_OK;
+    const uintptr_t N3b = (uintptr_t)c->n[0] * c->n[1] * c->n[2] * sizeof(float);
+    const uintptr_t o0 = (uintptr_t)out, o1 = o0 + N3b * (uintptr_t)n_out;
+    const uintptr_t i0 = (uintptr_t)in, i1 = i0 + N3b * (uintptr_t)n_in;
+    if (o0 < i1 && i0 < o1) return fail(TX_ERR_INVALID_ARG, std::string(what) + ": an output overlaps an input");
+    return TX_OK;
+}
+
 // decides how the targets relate to the occupied block
 static void classify_targets(const tx_ctx* c, const float* occ, int n_occ, const float* tgt, int n_tgt, int* mode,
                              int* k0) {
@@ -375,6 +385,8 @@ extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, con
     TX_TRY(check_block(out, n_tgt, "out"));
     if (!out && n_tgt > 0) return fail(TX_ERR_INVALID_ARG, "out is NULL");
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
+    TX_TRY(check_no_alias(c, out, n_tgt, psi_occ, n_occ, "out / psi_occ"));
+    TX_TRY(check_no_alias(c, out, n_tgt, psi_tgt, n_tgt, "out / psi_tgt"));
     cudaStream_t s = (cudaStream_t)stream;
     c->last_stream = s;
     if (n_tgt == 0) return TX_OK;
@@ -400,6 +412,7 @@ extern "C" int tx_exchange_apply_energy(tx_ctx* c, const float* psi_occ, int n_o
     TX_TRY(check_block(out, n_occ, "out"));
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
     if (!out || !e_dev) return fail(TX_ERR_INVALID_ARG, "out and e_dev must not be NULL");
+    TX_TRY(check_no_alias(c, out, n_occ, psi_occ, n_occ, "out / psi_occ"));
     cudaStream_t s = (cudaStream_t)stream;
     c->last_stream = s;
     CallSpec cs;
@@ -439,6 +452,7 @@ extern "C" int tx_exchange_energy_grad(tx_ctx* c, const float* psi_occ, int n_oc
     TX_TRY(check_block(grad, n_occ, "grad"));
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
     if (!grad) return fail(TX_ERR_INVALID_ARG, "grad is NULL");
+    TX_TRY(check_no_alias(c, grad, n_occ, psi_occ, n_occ, "grad / psi_occ"));
     cudaStream_t s = (cudaStream_t)stream;
     c->last_stream = s;
     CallSpec cs;
@@ -464,6 +478,13 @@ extern "C" int tx_exchange_apply_vjp(tx_ctx* c, const float* psi_occ, int n_occ,
     TX_TRY(check_block(grad_tgt, grad_tgt ? n_tgt : 0, "grad_tgt"));
     if (n_occ < 1 || n_tgt < 1) return fail(TX_ERR_INVALID_ARG, "n_occ and n_tgt must be >= 1");
     if (!grad_out) return fail(TX_ERR_INVALID_ARG, "grad_out is NULL");
+    const float* ins[3] = {psi_occ, psi_tgt, grad_out};
+    const int n_ins[3] = {n_occ, n_tgt, n_tgt};
+    for (int k = 0; k < 3; ++k) {
+        TX_TRY(check_no_alias(c, grad_occ, n_occ, ins[k], n_ins[k], "grad_occ"));
+        TX_TRY(check_no_alias(c, grad_tgt, n_tgt, ins[k], n_ins[k], "grad_tgt"));
+    }
+    TX_TRY(check_no_alias(c, grad_occ, n_occ, grad_tgt, n_tgt, "grad_occ / grad_tgt"));
     cudaStream_t s = (cudaStream_t)stream;
     c->last_stream = s;
     CallSpec cs;

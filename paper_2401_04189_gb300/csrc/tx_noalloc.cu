@@ -81,6 +81,11 @@ extern "C" int tx_exchange_apply_static(tx_ctx* c, const float* psi_occ, int n_o
     if (!psi_occ || !out || n_occ < 1) return fail(TX_ERR_INVALID_ARG, "psi_occ / out NULL or n_occ < 1");
     if (((uintptr_t)psi_occ | (uintptr_t)out) & 15u) return fail(TX_ERR_ALIGNMENT, "arrays must be 16-byte aligned");
     if (c->n[2] > 256) return fail(TX_ERR_UNSUPPORTED_SHAPE, "float32 kernels need n3 <= 256");
+    {
+        const uintptr_t bytes = (uintptr_t)n_occ * c->n[0] * c->n[1] * c->n[2] * sizeof(float);
+        const uintptr_t a = (uintptr_t)psi_occ, b = (uintptr_t)out;
+        if (a < b + bytes && b < a + bytes) return fail(TX_ERR_INVALID_ARG, "out overlaps psi_occ");
+    }
     int cur = -1;
     TX_TRY_CUDA(cudaGetDevice(&cur));
     if (cur != c->device) TX_TRY_CUDA(cudaSetDevice(c->device));

@@ -173,6 +173,32 @@ def test_invalid_alignment_and_null_are_rejected():
     assert st == -1
 
 
+def test_outputs_overlapping_inputs_are_rejected():
+    """An output block that shares memory with an input block is refused before any launch
+    (TX_ERR_INVALID_ARG); an output right after the inputs is accepted and correct."""
+    P = _P()
+    import torch
+    s = W.config_small(n=12, n_orb=2, rank=4, T=2, L=4.0)
+    ctx = P.Context.from_system(s, precision="fp32")
+    L = P.lib()
+    buf = torch.zeros((3,) + tuple(s.psi.shape[1:]), dtype=torch.float32, device="cuda")
+    buf[:2] = to_gpu(s.psi)
+    e = torch.zeros((), dtype=torch.float64, device="cuda")
+    occ, second, third = buf.data_ptr(), buf[1].data_ptr(), buf[2].data_ptr()
+    assert L.tx_exchange_apply(ctx.handle, occ, 2, None, 0, occ, None) == -1
+    assert L.tx_exchange_apply(ctx.handle, occ, 2, None, 0, second, None) == -1
+    assert L.tx_exchange_apply(ctx.handle, occ, 1, third, 1, third, None) == -1      # out on the target
+    assert L.tx_exchange_apply_energy(ctx.handle, occ, 2, second, e.data_ptr(), None) == -1
+    assert L.tx_exchange_energy_grad(ctx.handle, occ, 2, second, e.data_ptr(), None) == -1
+    assert L.tx_exchange_apply_vjp(ctx.handle, occ, 2, occ, 1, third, second, None, None) == -1
+    assert L.tx_exchange_apply_static(ctx.handle, occ, 2, second, None) == -1
+    assert L.tx_exchange_apply(ctx.handle, occ, 2, occ, 1, third, None) == 0         # adjacent: fine
+    ctx.check_device_error()
+    S = O.Setup.from_system(s)
+    ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[0:1])
+    assert rel(buf[2:3].cpu().numpy(), ref) < W_TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32x3"])
 def test_tensor_core_precisions_reject_unaligned_rows(prec):
     P = _P()
