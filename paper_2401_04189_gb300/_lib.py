@@ -234,6 +234,8 @@ def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None
     if out is None:
         out = torch.empty((n_tgt, *ctx.n), dtype=torch.float32, device=psi_occ.device)
     ctx._block(out, "out")
+    if n_tgt == 0:
+        return out          # no targets (an empty tensor has a NULL pointer, which the C call reads as "occupied")
     st = lib().tx_exchange_apply(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(psi_tgt),
                                  0 if psi_tgt is None else n_tgt, _ptr(out), _stream(stream))
     _check(st, "tx_exchange_apply")

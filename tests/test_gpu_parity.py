@@ -199,6 +199,17 @@ def test_outputs_overlapping_inputs_are_rejected():
     assert rel(buf[2:3].cpu().numpy(), ref) < W_TOL["fp32"]
 
 
+def test_empty_target_block_gives_empty_result():
+    P = _P()
+    import torch
+    s = W.config_small(n=12, n_orb=2, rank=4, T=2, L=4.0)
+    ctx = P.Context.from_system(s, precision="fp32")
+    occ = to_gpu(s.psi)
+    for tgt in (occ[:0], torch.empty((0, 12, 12, 12), dtype=torch.float32, device="cuda")):
+        assert tuple(P.tx_exchange_apply(ctx, occ, tgt).shape) == (0, 12, 12, 12)
+    ctx.check_device_error()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "tf32x3"])
 def test_tensor_core_precisions_reject_unaligned_rows(prec):
     P = _P()
