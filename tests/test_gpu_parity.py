@@ -313,3 +313,33 @@ def test_sharded_apply_matches_oracle(prec):
             assert Wl.shape[0] == b - a
             if b > a:
                 assert rel(Wl.cpu().numpy(), ref[a:b]) < W_TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def diff_case():
+    """The differentiation workload's grid, rank and terms (64^3 on [-10, 10]^3, rank 32, 35
+    terms) with 8 of its 32 orbitals, so that the oracle's E_x and full gradient take seconds."""
+    s = W.config_diff(n_orb=8)
+    S = O.Setup.from_system(s)
+    E_ref, g_ref = O.exchange_energy_grad(s.psi, S)
+    return s, E_ref, g_ref
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_energy_gradient_differentiation_workload(prec, diff_case):
+    """E_x and dE_x/dpsi against the oracle, directly and through the autograd wrapper."""
+    P = _P()
+    s, E_ref, g_ref = diff_case
+    ctx = P.Context.from_system(s, precision=prec)
+    psi = to_gpu(s.psi)
+    e, g = P.tx_exchange_energy_grad(ctx, psi)
+    ctx.check_device_error()
+    assert abs(float(e.item()) - E_ref) / abs(E_ref) < E_TOL[prec]
+    g = g.cpu().numpy()
+    assert rel(g, g_ref) < 5 * W_TOL[prec]
+    x = psi.clone().requires_grad_(True)
+    E = P.exchange_energy(ctx, x)
+    E.backward()
+    ctx.check_device_error()
+    assert abs(float(E.detach().item()) - E_ref) / abs(E_ref) < E_TOL[prec]
+    assert rel(x.grad.cpu().numpy(), g) < 1e-5
