@@ -219,6 +219,24 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
  * up to float32 summation order.  TX_ERR_INVALID_ARG outside 0..1. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
+/* Host-only description of the expansion kernel (the final contraction of Eq. final with the
+ * Hadamard product and the sum over j, the dominant kernel) that tx_exchange_apply and
+ * tx_exchange_apply_energy launch for a context of this shape, precision and expansion form
+ * (0 or 1, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
+ * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 12)
+ * values to out:
+ *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
+ *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items)
+ *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
+ *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
+ *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
+ *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs)
+ * For the float32 precision every value is 0.  Returns TX_OK; TX_ERR_INVALID_ARG for NULL
+ * arrays, nout < 1, T < 1 or a form outside 0..1; TX_ERR_SHAPE for sizes outside
+ * 2 <= n_d <= 4096, 1 <= r_d <= n_d; TX_ERR_UNSUPPORTED_PRECISION; TX_ERR_UNSUPPORTED_SHAPE
+ * where tx_set_precision would refuse the shape. */
+int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out, int nout);
+
 /*
  * tx_exchange_apply_static -- out = K psi_occ (targets = the occupied block), like
  * tx_exchange_apply with psi_tgt NULL, for callers that cannot let a library allocate device

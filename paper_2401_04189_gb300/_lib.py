@@ -26,7 +26,7 @@ EXPORTED = [
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
     "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
-    "tx_exchange_apply_static",
+    "tx_exchange_apply_static", "tx_describe_expansion_plan",
 ]
 
 
@@ -101,6 +101,8 @@ def lib():
     L.tx_set_tile_plan.restype = _I
     L.tx_set_accumulation_chunk.argtypes = [_P, _I]
     L.tx_set_accumulation_chunk.restype = _I
+    L.tx_describe_expansion_plan.argtypes = [ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _I, _I, ctypes.POINTER(_I), _I]
+    L.tx_describe_expansion_plan.restype = _I
     L.tx_set_expansion_form.argtypes = [_P, _I]
     L.tx_set_expansion_form.restype = _I
     L.tx_selftest_gemm.argtypes = [_I, _I, _I, _I, _I, _P, _P, _P, _P]
@@ -394,6 +396,23 @@ def tx_set_accumulation_chunk(ctx, terms):
 def tx_set_expansion_form(ctx, form):
     """Single-pass precisions: 0 = automatic (persistent expansion kernel where it applies, default), 1 = one CTA per item."""
     _check(lib().tx_set_expansion_form(ctx.handle, int(form)), "tx_set_expansion_form")
+
+
+PLAN_FIELDS = ("kernel", "planes", "stages2", "stages3", "ybuffers", "tmem_cols", "smem_bytes", "threads",
+               "ksteps2", "ksteps3", "n3p", "items_per_pair")
+PLAN_KERNELS = {0: "float32", 1: "converter", 2: "per_item", 3: "persistent"}
+
+
+def tx_describe_expansion_plan(n, r, T, precision, form=0):
+    """The expansion kernel and tile plan a context of this shape would launch (host only, no
+    device needed): a dict over PLAN_FIELDS, with "kernel" named as in PLAN_KERNELS."""
+    out = (_I * len(PLAN_FIELDS))()
+    st = lib().tx_describe_expansion_plan((_I * 3)(*[int(v) for v in n]), (_I * 3)(*[int(v) for v in r]), int(T),
+                                          int(Precision.parse(precision)), int(form), out, len(PLAN_FIELDS))
+    _check(st, "tx_describe_expansion_plan")
+    d = dict(zip(PLAN_FIELDS, (int(v) for v in out)))
+    d["kernel"] = PLAN_KERNELS[d["kernel"]]
+    return d
 
 
 def tx_launch_count() -> int:

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <fstream>
 #include <map>
 #include <sstream>
@@ -18,6 +19,7 @@ namespace tx {
 int tc_feasible_plans(const tx_ctx* c, int* bx, int* ns, int cap);
 bool tc_current_plan(const tx_ctx* c, int* bx, int* ns);
 bool tc_plan_fits(const tx_ctx* c, int bx, int ns);
+int tc_describe_plan(const tx_ctx* c, int* out, int nout);
 }  // namespace tx
 
 using namespace tx;
@@ -112,6 +114,37 @@ extern "C" int tx_set_expansion_form(tx_ctx* c, int form) {
     if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic) or 1 (one CTA per item)");
     c->consume_form = form;
     return TX_OK;
+}
+
+extern "C" int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out,
+                                          int nout) {
+    if (!n || !r || !out || nout < 1) return fail(TX_ERR_INVALID_ARG, "n, r and out must not be NULL; nout >= 1");
+    if (T < 1) return fail(TX_ERR_INVALID_ARG, "T must be >= 1");
+    if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic) or 1 (one CTA per item)");
+    if (precision < TX_PREC_FP32 || precision > TX_PREC_BF16X3)
+        return fail(TX_ERR_UNSUPPORTED_PRECISION, "unknown precision");
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 2 || n[d] > 4096) return fail(TX_ERR_SHAPE, "grid sizes must be in [2, 4096]");
+        if (r[d] < 1 || r[d] > n[d]) return fail(TX_ERR_SHAPE, "ranks must satisfy 1 <= r_d <= n_d");
+    }
+    for (int i = 0; i < nout; ++i) out[i] = 0;
+    if (precision == TX_PREC_FP32) {
+        if (n[2] > 256) return fail(TX_ERR_UNSUPPORTED_SHAPE, "float32 path supports n3 <= 256");
+        return TX_OK;
+    }
+    // a host-side stand-in with the fields the planner reads (no device state)
+    tx_ctx c;
+    std::memset(&c, 0, sizeof(c));
+    for (int d = 0; d < 3; ++d) {
+        c.n[d] = n[d];
+        c.r[d] = r[d];
+    }
+    c.T = T;
+    c.prec = precision;
+    c.consume_form = form;
+    std::string why;
+    if (!tc_supported(&c, &why)) return fail(TX_ERR_UNSUPPORTED_SHAPE, why);
+    return tc_describe_plan(&c, out, nout);
 }
 
 extern "C" int tx_set_tile_plan(tx_ctx* c, int bx, int nstage) {

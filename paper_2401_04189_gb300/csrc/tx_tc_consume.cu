@@ -1611,6 +1611,59 @@ long tc_consume_blocks(const tx_ctx* c) {
     return (c->n[0] + p.bx - 1) / p.bx;
 }
 
+// Persistent form of the single-pass kernel (the epilogue of one item overlaps the main loop of
+// the next): it applies where each epilogue warp holds one tile of phi in registers and the
+// energy factors are the multipliers, and it splits shared memory its own way (a stage-2 ring
+// of at most four stages, a stage-3 ring as deep as fits, the epilogue boxes).
+struct TpSplit {
+    bool on;
+    int nl1, nl3;
+    uint32_t a3_off, epi_off;
+    size_t smem;
+};
+
+static TpSplit tp_split(const tx_ctx* c, const ConsumePlan& p, bool energy, bool emul) {
+    TpSplit t{};
+    t.on = p.ts && c->consume_form != 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
+           (!energy || emul);
+    if (!t.on) return t;
+    t.nl1 = std::min(p.nload, 4);
+    t.a3_off = p.load * (uint32_t)t.nl1;
+    int nl3 = tcc::kMaxLoad;
+    while (nl3 >= 2 && (size_t)t.a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 > 226 * 1024) --nl3;
+    if (nl3 < 2) {
+        t.on = false;
+        return t;
+    }
+    t.nl3 = nl3;
+    t.epi_off = t.a3_off + (uint32_t)nl3 * p.load3;
+    t.smem = (size_t)t.epi_off + tcc::kTpEpiBytes + 1024;
+    return t;
+}
+
+// host-only description of the expansion plan (see tx_describe_expansion_plan)
+int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
+    const bool tf32 = c->prec == TX_PREC_TF32 || c->prec == TX_PREC_TF32X3;
+    const bool split = c->prec == TX_PREC_TF32X3 || c->prec == TX_PREC_BF16X3;
+    ConsumePlan p;
+    if (!choose_plan(c, tf32, split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
+    const TpSplit t = p.ts ? tp_split(c, p, false, false) : TpSplit{};
+    const int v[12] = {t.on ? 3 : (p.ts ? 2 : 1),
+                       p.bx,
+                       t.on ? t.nl1 : p.nload,
+                       p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
+                       p.ts ? p.nyb : 0,
+                       (int)p.tmem_cols,
+                       (int)(t.on ? t.smem : p.smem),
+                       t.on ? tcc::kThreadsTp : (p.ts ? tcc::kThreadsTs : tcc::kThreads),
+                       p.ks2,
+                       p.ks3,
+                       p.n3p,
+                       (c->n[0] + p.bx - 1) / p.bx};
+    for (int i = 0; i < nout && i < 12; ++i) out[i] = v[i];
+    return TX_OK;
+}
+
 int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
     TcOperands* op = c->tc;
     if (op->img) {
@@ -1721,26 +1774,15 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         TX_TRY(orb_map(&em.o0, OUT0, cnt.out0));
         TX_TRY(orb_map(&em.o1, OUT1, cnt.out1));
         if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
-        // Persistent form (the epilogue of one item overlaps the main loop of the next) where
-        // each epilogue warp holds one tile of phi in registers and the energy factors are the
-        // multipliers; it needs its own shared-memory split (rings + epilogue boxes)
-        bool tp = c->consume_form != 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
-                  (!(flags & EPI_ENERGY) || a.emul);
+        const TpSplit tps = tp_split(c, p, (flags & EPI_ENERGY) != 0, a.emul != 0);
+        const bool tp = tps.on;
         size_t smem = p.smem;
         if (tp) {
-            const int nl1 = std::min(p.nload, 4);
-            const uint32_t a3_off = p.load * (uint32_t)nl1;
-            int nl3 = tcc::kMaxLoad;
-            while (nl3 >= 2 && (size_t)a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 > 226 * 1024) --nl3;
-            if (nl3 >= 2) {
-                a.nload = nl1;
-                a.a3_off = a3_off;
-                a.nload3 = nl3;
-                a.epi_off = a3_off + (uint32_t)nl3 * p.load3;
-                smem = (size_t)a.epi_off + tcc::kTpEpiBytes + 1024;
-            } else {
-                tp = false;
-            }
+            a.nload = tps.nl1;
+            a.a3_off = tps.a3_off;
+            a.nload3 = tps.nl3;
+            a.epi_off = tps.epi_off;
+            smem = tps.smem;
         }
         // instantiations with compile-time K step counts for ranks 32, 40, 48 and 64; any other
         // rank runs the dispatching form (see s2_mmas / s3_mmas)

@@ -277,12 +277,16 @@ def test_expansion_forms_agree(prec, system):
         P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
 
 
+@pytest.mark.parametrize("rank,kernel", [(64, "converter"), (48, "per_item")])
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
-def test_large_grid_two_y_tiles(prec):
-    """n = 160 (two 128-row y tiles per plane, n3 past the persistent kernel's 96 columns) at
-    rank 64 (the K-step counts of the TiO2-shaped workload): apply and energy against the oracle."""
+def test_large_grid_two_y_tiles(prec, rank, kernel):
+    """n = 160: two 128-row y tiles per plane and n3 past the persistent kernel's 96 columns.
+    At rank 64 (the TiO2-shaped workload) two stage-2 output buffers (2 x 128 TMEM columns) and
+    phi (2 x 160) exceed TMEM's 512 columns, so the converter kernel runs; at rank 48 the
+    one-CTA-per-item kernel with stage 3 read from TMEM.  Apply and energy against the oracle."""
     P = _P()
-    s = W.config_small(n=160, n_orb=2, rank=64, T=6, L=16.0)
+    assert P.tx_describe_expansion_plan((160, 160, 160), (rank,) * 3, 6, prec)["kernel"] == kernel
+    s = W.config_small(n=160, n_orb=2, rank=rank, T=6, L=16.0)
     S = O.Setup.from_system(s)
     ref = O.exchange_apply(s.psi, S)
     ctx = P.Context.from_system(s, precision=prec)

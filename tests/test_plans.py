@@ -1,0 +1,99 @@
+"""Host logic of the expansion planner, without a GPU (tx_describe_expansion_plan): the plan of
+the Pt-shaped bench workload against the launch record of its ncu profile, and the limits every
+plan must respect (shared memory per CTA, TMEM columns, the persistent kernel's conditions) over
+a sweep of shapes and precisions."""
+import itertools
+
+import pytest
+
+import paper_2401_04189_gb300 as P
+
+MAX_DYN_SMEM = 227 * 1024          # opt-in dynamic shared memory per CTA (sm_100 family)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2401_04189_gb300 import build
+    build.build()
+
+
+def pad16(v):
+    return (v + 15) // 16 * 16
+
+
+def test_pt_shaped_bf16_plan_matches_the_profiled_launch():
+    """96^3, rank 40, 40 terms, bf16: the persistent kernel with 384 threads and 213 KiB of
+    dynamic shared memory, as ncu recorded for the bench kernel (152 CTAs x 384 threads,
+    213 KiB); 2 planes per item, so 48 items per pair (1,728 items for 36 pairs)."""
+    d = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16")
+    assert d["kernel"] == "persistent"
+    assert (d["threads"], d["smem_bytes"]) == (384, 213 * 1024)
+    assert (d["planes"], d["items_per_pair"]) == (2, 48)
+    assert (d["ybuffers"], d["tmem_cols"]) == (4, 512)       # 4 x 80 Y columns + 2 x 96 phi columns
+    assert (d["ksteps2"], d["ksteps3"]) == (3, 5)            # bf16 K = 16 per step (40 -> 48); tf32 K = 8
+    one = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16", form=1)
+    assert one["kernel"] == "per_item" and one["threads"] == 352
+
+
+def test_split_precisions_use_the_converter_kernel():
+    for prec in ("tf32x3", "bf16x3"):
+        assert P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, prec)["kernel"] == "converter"
+    assert P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "fp32")["kernel"] == "float32"
+
+
+SIZES = [(16, 16, 16), (20, 27, 36), (32, 32, 32), (48, 64, 80), (64, 64, 64), (96, 96, 96), (112, 112, 112),
+         (128, 128, 128), (160, 160, 160), (200, 200, 200), (256, 256, 256)]
+RANKS = [1, 5, 16, 32, 40, 48, 64]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "tf32x3", "bf16x3"])
+def test_every_plan_respects_the_hardware_limits(prec):
+    tf32 = prec.startswith("tf32")
+    split = prec.endswith("x3")
+    mk = 8 if tf32 else 16
+    planned = 0
+    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1)):
+        rr = tuple(min(r, v) for v in n)
+        try:
+            d = P.tx_describe_expansion_plan(n, rr, T, prec, form)
+        except P.TuckerExchangeError as e:
+            assert e.status == -9, (n, rr, T, form, str(e))     # unsupported shape, never another error
+            continue
+        planned += 1
+        key = (n, rr, T, form, d)
+        assert 0 < d["smem_bytes"] <= MAX_DYN_SMEM, key
+        assert d["tmem_cols"] in (32, 64, 128, 256, 512), key
+        assert d["planes"] >= 1 and d["items_per_pair"] == -(-n[0] // d["planes"]), key
+        assert d["n3p"] == pad16(n[2]), key
+        assert d["ksteps2"] == -(-rr[1] // mk), key
+        assert d["stages2"] >= 1, key
+        if split:
+            assert d["kernel"] == "converter", key
+            assert d["ksteps3"] == -(-rr[2] // mk), key
+            continue
+        if d["kernel"] == "converter":          # single-pass shapes no TMEM plan holds
+            continue
+        assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
+        assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
+        if d["kernel"] == "persistent":
+            assert form == 0 and d["threads"] == 384, key
+            assert d["planes"] <= 2 and d["n3p"] <= 96 and d["stages2"] <= 4, key
+            assert d["planes"] * -(-n[1] // 128) <= 2, key       # one phi tile per epilogue warp
+        else:
+            assert d["kernel"] == "per_item" and d["threads"] == 352, key
+    assert planned > 50
+
+
+def test_shapes_the_tensor_cores_cannot_take_are_refused():
+    with pytest.raises(P.TuckerExchangeError) as ei:
+        P.tx_describe_expansion_plan((12, 13, 15), (3, 4, 5), 3, "bf16")     # 15 floats: rows not 16-byte
+    assert ei.value.status == -9
+    P.tx_describe_expansion_plan((12, 13, 15), (3, 4, 5), 3, "fp32")
+    with pytest.raises(P.TuckerExchangeError) as ei:
+        P.tx_describe_expansion_plan((12, 13, 300), (3, 4, 5), 3, "fp32")    # float32 kernels: n3 <= 256
+    assert ei.value.status == -9
+    for bad, status in [(((1, 8, 8), (1, 1, 1), 3, "bf16", 0), -2), (((8, 8, 8), (9, 1, 1), 3, "bf16", 0), -2),
+                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 2), -1)]:
+        with pytest.raises(P.TuckerExchangeError) as ei:
+            P.tx_describe_expansion_plan(*bad)
+        assert ei.value.status == status, bad
