@@ -131,6 +131,28 @@ def test_full_rank_potential_equals_direct_sum(seed):
     assert _rel(phi, ref) < 1e-12
 
 
+def test_truncated_rank_potential_on_the_span_equals_direct_sum():
+    """At truncated rank the operator is L = sum_t mu_t (x)_d C_td U_d U_d^T: a density whose
+    mode factors lie in span(U_d) passes the projection unchanged, so its potential is the
+    brute-force sum; a density orthogonal to the span in one mode has none.  Catches a wrong
+    composition A_td = C_td U_d (transposed or swapped factors) that full rank (U = I) hides."""
+    rng = np.random.default_rng(11)
+    n, r = (7, 8, 9), (3, 4, 5)
+    S = _random_setup(rng, n, r, 3)
+    rho = np.zeros(n)
+    for _ in range(2):
+        f = [S.U[d] @ rng.standard_normal(r[d]) for d in range(3)]
+        rho += np.einsum("a,b,c->abc", *f)
+    ref = O.direct_gaussian_kernel_potential(rho, S.x, S.w, S.theta, S.mu)
+    assert _rel(O.apply_L(rho, S), ref) < 1e-12
+    # the mode-2 factor orthogonal to span(U_2): nothing survives the projection
+    g = rng.standard_normal(n[1])
+    g -= S.U[1] @ (S.U[1].T @ g)
+    perp = np.einsum("a,b,c->abc", S.U[0][:, 0], g, S.U[2][:, 1])
+    full = O.direct_gaussian_kernel_potential(perp, S.x, S.w, S.theta, S.mu)
+    assert np.linalg.norm(O.apply_L(perp, S)) < 1e-12 * np.linalg.norm(full)
+
+
 def test_direct_sum_reference_is_sensitive_to_transposed_weights():
     # the brute-force reference must tell C = K D apart from C = D K on a non-uniform grid
     rng = np.random.default_rng(3)
