@@ -346,11 +346,12 @@ def roofline(dom, prof, n, r, T, N, steps, prec, peaks, ck):
         peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12
         bound, src = "alu", "152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz (derived)"
     else:
-        bf16 = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+        measured = (peaks or {}).get("bf16_tflops_sustained")
+        bf16 = measured if measured else 1700.0
         ratio = {"bf16": 1.0, "bf16x3": 1.0, "tf32": 0.5, "tf32x3": 0.5}.get(prec, 1.0)
         peak = bf16 * ratio
         bound = "tensor"
-        src = ("measured sustained bf16" if peaks else "fallback bf16") + (
+        src = ("measured sustained bf16" if measured else "fallback bf16") + (
             " x 0.5 (nominal tf32/bf16 ratio)" if ratio != 1.0 else "")
     bpp = DRAM_BYTES_PER_PAIR.get((dom, prec))
     traffic = bpp * unique * steps / k if bpp else None     # bytes per launch

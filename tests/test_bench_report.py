@@ -39,6 +39,7 @@ def test_roofline_peaks_per_precision():
     peaks = {"bf16_tflops_sustained": 1700.0}
     assert bench.roofline(*args, "tf32", peaks, None)["peak"] == pytest.approx(850.0)
     assert bench.roofline(*args, "bf16", None, None)["peak_source"].startswith("fallback")
+    assert bench.roofline(*args, "bf16", {"hbm_gbs": 6800.0}, None)["peak_source"].startswith("fallback")
     f = bench.roofline(*args, "fp32", peaks, None)
     assert f["bound"] == "alu"
     assert f["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)   # FP32 FMA rate of 152 SMs
