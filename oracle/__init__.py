@@ -39,7 +39,7 @@ import numpy as np
 __all__ = [
     "Setup", "conv_matrix", "mode_product", "project", "expand", "expand_transpose",
     "apply_L", "apply_LT", "pair_potential", "exchange_apply", "exchange_energy",
-    "exchange_energy_grad", "exchange_apply_vjp",
+    "exchange_energy_grad", "exchange_apply_vjp", "ace_projectors", "ace_apply",
     "direct_gaussian_kernel_potential", "direct_coulomb_potential",
     "gaussian_charge_potential", "gaussian_kernel_charge_potential",
 ]
@@ -182,6 +182,34 @@ def exchange_apply_vjp(psi_occ, psi_tgt, grad_out, S: Setup):
             g_tgt[k] -= occ[j] * zeta
             g_occ[j] -= Wb[k] * pair_potential(tgt[k], occ[j], S) + tgt[k] * zeta
     return g_occ, g_tgt
+
+
+# ----------------------------------------------------------------------------------
+# adaptively compressed exchange (section "ACE implementation": Eqs. eta, ace1)
+# ----------------------------------------------------------------------------------
+def ace_projectors(psi_occ, S: Setup, W=None):
+    """(xi, M) of the ACE operator V_ACE(r, r') = - sum_k xi_k(r) xi_k(r'):
+    W_i = K psi_i (Eq. ace1), M_ij = <psi_i, W_j>_w (the integral by the grid's quadrature),
+    M = - L L^T (Cholesky), xi_k = sum_i W_i (L^-1)_ki (Eq. eta).  The paper is silent on the
+    asymmetry of M that a truncated Tucker rank leaves; M is symmetrised, (M + M^T) / 2, before
+    the factorisation."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    if W is None:
+        W = exchange_apply(occ, S)
+    N = occ.shape[0]
+    M = np.array([[np.sum(S.w3 * occ[i] * W[j]) for j in range(N)] for i in range(N)])
+    Ms = 0.5 * (M + M.T)
+    L = np.linalg.cholesky(-Ms)
+    Linv = np.linalg.inv(L)
+    xi = np.tensordot(Linv, W, axes=(1, 0))          # xi[k] = sum_i Linv[k, i] W[i]
+    return xi, M
+
+
+def ace_apply(xi, psi, S: Setup):
+    """V_ACE psi_a = - sum_k xi_k <xi_k, psi_a>_w for every orbital psi_a of the block."""
+    psi = np.asarray(psi, dtype=np.float64)
+    C = np.array([[np.sum(S.w3 * xi[k] * psi[a]) for a in range(psi.shape[0])] for k in range(xi.shape[0])])
+    return -np.tensordot(C, xi, axes=(0, 0))          # [a] = - sum_k C[k, a] xi[k]
 
 
 # ----------------------------------------------------------------------------------

@@ -73,6 +73,21 @@ MUTATIONS = [
     ("L^T does not map the core back with U_d",
      "    for d in range(3):\n        H = mode_product(H, S.U[d], d)\n    return H",
      "    return H"),
+    ("ACE projectors with L instead of L^-1",
+     "    xi = np.tensordot(Linv, W, axes=(1, 0))          # xi[k] = sum_i Linv[k, i] W[i]",
+     "    xi = np.tensordot(L, W, axes=(1, 0))          # xi[k] = sum_i Linv[k, i] W[i]"),
+    ("ACE projectors with L^-T instead of L^-1",
+     "    xi = np.tensordot(Linv, W, axes=(1, 0))          # xi[k] = sum_i Linv[k, i] W[i]",
+     "    xi = np.tensordot(Linv.T, W, axes=(1, 0))          # xi[k] = sum_i Linv[k, i] W[i]"),
+    ("ACE operator with the wrong sign",
+     "    return -np.tensordot(C, xi, axes=(0, 0))          # [a] = - sum_k C[k, a] xi[k]",
+     "    return np.tensordot(C, xi, axes=(0, 0))          # [a] = - sum_k C[k, a] xi[k]"),
+    ("ACE overlap M without quadrature weights",
+     "    M = np.array([[np.sum(S.w3 * occ[i] * W[j]) for j in range(N)] for i in range(N)])",
+     "    M = np.array([[np.sum(occ[i] * W[j]) for j in range(N)] for i in range(N)])"),
+    ("ACE without symmetrising M",
+     "    Ms = 0.5 * (M + M.T)",
+     "    Ms = M"),
     ("quadrature weight of mode 2 on mode 3",
      "        self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]",
      "        self.w3 = self.w[0][:, None, None] * self.w[2][None, None, :] * self.w[2][None, None, :]"),

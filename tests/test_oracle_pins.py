@@ -329,3 +329,64 @@ def test_apply_linear_in_target_quadratic_in_occupied():
     W1 = O.exchange_apply(occ, S, psi_tgt=occ[:1])
     assert _rel(O.exchange_apply(occ, S, psi_tgt=2 * occ[:1]), 2 * W1) < 1e-14
     assert _rel(O.exchange_apply(3 * occ, S, psi_tgt=occ[:1]), 9 * W1) < 1e-14
+
+
+# ---------------------------------------------------------------------------------
+# Adaptively compressed exchange (section "ACE implementation"): exact on the occupied space
+# ---------------------------------------------------------------------------------
+def _w_inner(S, a, b):
+    return float(np.sum(S.w3 * a * b))
+
+
+def test_ace_reproduces_the_exchange_operator_on_the_occupied_orbitals():
+    """At full rank M is symmetric negative definite and V_ACE psi_j = K psi_j = W_j for every
+    occupied j (the defining property of ACE), so its exchange energy is E_x."""
+    s = W.config_small(n=12, n_orb=3, rank=12, T=4, L=4.0, full_rank=True)
+    S = O.Setup.from_system(s)
+    Wx = O.exchange_apply(s.psi, S)
+    xi, M = O.ace_projectors(s.psi, S, W=Wx)
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(M).max()
+    assert np.all(np.linalg.eigvalsh(0.5 * (M + M.T)) < 0)
+    V = O.ace_apply(xi, s.psi, S)
+    assert _rel(V, Wx) < 1e-12
+    e_ace = 0.5 * sum(_w_inner(S, s.psi[i], V[i]) for i in range(len(s.psi)))
+    e = O.exchange_energy(s.psi, S, W=Wx)
+    assert abs(e_ace - e) < 1e-12 * abs(e)
+
+
+def test_ace_operator_is_symmetric_negative_semidefinite_of_rank_n():
+    """V_ACE = - sum_k xi_k xi_k^T (with the quadrature weights) at any rank: symmetric, NSD, and
+    zero on fields w-orthogonal to every W_j."""
+    s = W.config_small(n=10, n_orb=3, rank=6, T=4, L=5.0)
+    S = O.Setup.from_system(s)
+    Wx = O.exchange_apply(s.psi, S)
+    xi, _ = O.ace_projectors(s.psi, S, W=Wx)
+    rng = np.random.default_rng(17)
+    f, g = rng.standard_normal((2,) + s.psi.shape[1:])
+    Vf, Vg = O.ace_apply(xi, np.stack([f, g]), S)
+    assert abs(_w_inner(S, f, Vg) - _w_inner(S, g, Vf)) < 1e-13 * abs(_w_inner(S, f, Vf))
+    assert _w_inner(S, f, Vf) < 0 and _w_inner(S, g, Vg) < 0
+    # remove from h its w-projection onto span(W): V_ACE h must vanish
+    h = rng.standard_normal(s.psi.shape[1:])
+    G = np.array([[_w_inner(S, a, b) for b in Wx] for a in Wx])
+    c = np.linalg.solve(G, np.array([_w_inner(S, a, h) for a in Wx]))
+    h = h - np.tensordot(c, Wx, axes=(0, 0))
+    assert np.linalg.norm(O.ace_apply(xi, h[None], S)) < 1e-12 * np.linalg.norm(Vf)
+
+
+def test_ace_at_truncated_rank_is_exact_up_to_the_asymmetry_of_M():
+    """At truncated rank M = <psi_i, W_j> is slightly asymmetric (one-sided projection) and the
+    symmetrised factorisation reproduces W_j up to an error of the size of that asymmetry."""
+    s = W.config_small(n=12, n_orb=3, rank=7, T=5, L=4.0)
+    S = O.Setup.from_system(s)
+    Wx = O.exchange_apply(s.psi, S)
+    xi, M = O.ace_projectors(s.psi, S, W=Wx)
+    asym = np.linalg.norm(M - M.T) / np.linalg.norm(M)
+    assert 0 < asym < 1e-2
+    V = O.ace_apply(xi, s.psi, S)
+    assert _rel(V, Wx) < 2 * asym
+    # algebra: with L L^T = -Ms (Ms the symmetric part of M), V_ACE psi_a = sum_i W_i (Ms^-1 M^T)_ia,
+    # which reduces to W_a exactly when M is symmetric
+    Ms = 0.5 * (M + M.T)
+    B = np.linalg.solve(Ms, M.T)
+    assert _rel(V, np.tensordot(B, Wx, axes=(0, 0))) < 1e-10
