@@ -28,6 +28,11 @@ L = sum_t mu_t (x)_d (A_td U_d^T), so that phi_ij = L rho_ij:
     grad_tgt_k   = - sum_j psi_j * L^T(Wbar_k * psi_j)
     grad_occ_j   = - sum_k Wbar_k * phi_kj - sum_k psi_k * L^T(Wbar_k * psi_j)
 
+The adaptively compressed exchange operator built from W (section "ACE implementation",
+Eqs. eta, ace1): M_ij = <psi_i, W_j>_w, M = -L L^T, xi_k = sum_i W_i (L^-1)_ki and
+V_ACE psi = - sum_k xi_k <xi_k, psi>_w (M symmetrised first where a truncated rank leaves it
+slightly asymmetric).
+
 Independent references used by the pins (brute force and closed forms) are at the end.
 """
 from __future__ import annotations
