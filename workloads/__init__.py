@@ -23,7 +23,8 @@ import numpy as np
 __all__ = [
     "uniform_grid", "fcc_cluster", "rutile_cluster", "gaussian_sum_orbitals",
     "lowdin_orthonormalise", "density_hosvd_basis", "exp_sum_inverse_r",
-    "System", "make_system", "CONFIGS", "batched_system_specs",
+    "System", "make_system", "make_system_on_device", "config_tio2_on_device", "CONFIGS",
+    "batched_system_specs",
 ]
 
 
@@ -243,6 +244,75 @@ def make_system(name: str, n: int, L: float, n_orb: int, rank: int, T: int, seed
     theta, mu, ferr = exp_sum_inverse_r(T, r1, r2)
     return System(name, xs, ws, U, theta, mu, psi, ferr,
                   meta=dict(seed=seed, L=L, n_orb=n_orb, rank=rank, fit_range=(r1, r2)))
+
+
+def make_system_on_device(name: str, n: int, L: float, n_orb: int, rank: int, T: int, seed: int,
+                          centres: np.ndarray, n_gauss_per_centre: int, exp_range, centres_per_orbital=None,
+                          device="cuda", chunk=1 << 20):
+    """make_system with the orbital arithmetic on a torch device, for blocks too large for the
+    host (the TiO2-shaped block: 1842 orbitals of 160^3 points, 60 GB in float64): the same
+    seeded draws, Gaussian sums, Loewdin orthonormalisation and density HOSVD, in float64 on the
+    device.  Returns (System with psi=None, psi as a float32 device tensor [N, n, n, n])."""
+    import torch
+    rng = np.random.default_rng(seed)
+    x, w = uniform_grid(n, L)
+    xs, ws = [x, x.copy(), x.copy()], [w, w.copy(), w.copy()]
+    C = centres.shape[0]
+    if centres_per_orbital is None:
+        idx = np.broadcast_to(np.arange(C), (n_orb, C))
+    else:
+        idx = np.stack([rng.choice(C, size=centres_per_orbital, replace=False) for _ in range(n_orb)])
+    k = idx.shape[1] * n_gauss_per_centre
+    cen = np.repeat(centres[idx], n_gauss_per_centre, axis=1).reshape(n_orb, k, 3)
+    exps = rng.uniform(exp_range[0], exp_range[1], size=(n_orb, k))
+    coefs = rng.standard_normal(size=(n_orb, k))
+    f64 = dict(dtype=torch.float64, device=device)
+    xg = torch.tensor(x, **f64)
+    N3 = n ** 3
+    P = torch.empty((n_orb, N3), **f64)
+    for i in range(n_orb):
+        a = torch.tensor(exps[i], **f64)[:, None]
+        c = torch.tensor(cen[i], **f64)
+        ex = torch.tensor(coefs[i], **f64)[:, None] * torch.exp(-a * (xg[None, :] - c[:, 0:1]) ** 2)
+        ey = torch.exp(-a * (xg[None, :] - c[:, 1:2]) ** 2)
+        ez = torch.exp(-a * (xg[None, :] - c[:, 2:3]) ** 2)
+        t = (ex[:, :, None] * ey[:, None, :]).reshape(k, -1)
+        P[i] = (t.T @ ez).reshape(-1)
+    wg = torch.tensor(w, **f64)
+    w3d = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]).reshape(-1)
+    S = torch.zeros((n_orb, n_orb), **f64)
+    for c0 in range(0, N3, chunk):
+        Pc = P[:, c0:c0 + chunk]
+        S += (Pc * w3d[None, c0:c0 + chunk]) @ Pc.T
+    ev, V = torch.linalg.eigh(0.5 * (S + S.T))
+    if float(ev.min()) <= 1e-12 * float(ev.max()):
+        raise ValueError("orbitals are numerically linearly dependent")
+    X = (V * ev[None, :] ** -0.5) @ V.T
+    psi = torch.empty((n_orb, N3), dtype=torch.float32, device=device)
+    for c0 in range(0, N3, chunk):
+        psi[:, c0:c0 + chunk] = (X @ P[:, c0:c0 + chunk]).to(torch.float32)
+    del P
+    psi = psi.reshape(n_orb, n, n, n)
+    rho = torch.zeros((n, n, n), **f64)
+    for p in psi:
+        rho += p.to(torch.float64) ** 2
+    Us = []
+    for d in range(3):
+        M = torch.movedim(rho, d, 0).reshape(n, -1)
+        evd, Vd = torch.linalg.eigh(M @ M.T)
+        Vd = Vd.flip(1)[:, :rank].cpu().numpy()
+        sgn = np.sign(Vd[np.argmax(np.abs(Vd), axis=0), np.arange(Vd.shape[1])])
+        Us.append(np.ascontiguousarray(Vd * sgn[None, :]))
+    r1, r2 = _fit_range(xs, (L, L, L))
+    theta, mu, ferr = exp_sum_inverse_r(T, r1, r2)
+    return (System(name, xs, ws, Us, theta, mu, None, ferr,
+                   meta=dict(seed=seed, L=L, n_orb=n_orb, rank=rank, fit_range=(r1, r2))), psi)
+
+
+def config_tio2_on_device(n=160, L=16.0, n_orb=1842, rank=64, T=45, seed=4, device="cuda"):
+    """The TiO2-shaped block of config_tio2, generated on a torch device."""
+    return make_system_on_device("tio2", n, L, n_orb, rank, T, seed, rutile_cluster(240), 2, (0.2, 3.0),
+                                 centres_per_orbital=16, device=device)
 
 
 def _small(seed=0, n=32, n_orb=4, rank=16, T=30, L=8.0, full_rank=False):
