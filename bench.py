@@ -320,8 +320,8 @@ def dtype_name(prec):
 
 # DRAM bytes (read + write) per distinct pair of the dominant kernel, from one ncu capture of
 # the current kernel on the same block with 8 orbitals (36 pairs in one launch), scaled by the
-# pairs a bench launch processes (traffic grows in proportion to pairs).  Source and command:
-# profiles/k_consume_tp_pt8_bf16.md.  None where no capture of the current kernel exists.
+# pairs a bench launch processes (traffic grows in proportion to pairs).  None where no capture
+# of the current kernel exists.
 DRAM_BYTES_PER_PAIR = {("tc_consume", "bf16"): (711.658752e6 + 83.418368e6) / 36}
 
 

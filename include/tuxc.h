@@ -264,9 +264,36 @@ size_t tx_workspace_bytes(const tx_ctx* ctx);
 /* Upper bound on the workspace (default 2 GiB); larger calls are split into pair batches. */
 int tx_set_workspace_limit(tx_ctx* ctx, size_t bytes);
 
-/* Reads and clears the device-side error word (bounded waits that gave up); synchronises
- * the context's last stream.  Returns TX_OK or TX_ERR_TIMEOUT. */
+/* Reads and clears the device-side error word (bounded waits that gave up, and best-effort
+ * drains of in-flight copies that gave up); synchronises the context's last stream.  Returns
+ * TX_OK or TX_ERR_TIMEOUT (the message names the wait that gave up). */
 int tx_check_device_error(tx_ctx* ctx);
+
+/* Time limit of every bounded device-side wait in this context's kernels (no counterpart in the
+ * paper): a wait that has not completed after `ns` nanoseconds gives up, records where, and its
+ * kernel unwinds (releasing its TMEM) so that the context stays usable; the host sees
+ * TX_ERR_TIMEOUT from tx_check_device_error.  0 restores the default of 2 s.  Synchronises the
+ * context's last stream.  TX_ERR_INVALID_ARG outside 1 us .. 60 s. */
+int tx_set_wait_limit(tx_ctx* ctx, uint64_t ns);
+
+/* Self-test of the bounded wait (no counterpart in the paper): launches one warp on `stream` that
+ * (if hold_tmem != 0) allocates 32 TMEM columns and then waits on an mbarrier that nothing ever
+ * completes.  After the context's wait limit the wait gives up exactly as a pipeline kernel's
+ * would: it records the timeout in the context's error word, frees its TMEM and returns.  A
+ * following tx_check_device_error returns TX_ERR_TIMEOUT and clears the word; the context then
+ * works as before.  Nothing faults or hangs. */
+int tx_selftest_wait(tx_ctx* ctx, int hold_tmem, tx_stream_t stream);
+
+/*
+ * tx_exchange_energy_from_w -- E = 1/2 sum_i sum_r w(r) psi_i(r) W_i(r) for given orbitals and
+ * their exchange potentials W_i = K psi_i (the exchange term of S[phi] with alpha = 1, summed
+ * over the n orbitals given).  Used to add up the energy of a target block applied on its own
+ * (for instance one shard of the targets): the shards' values add up to E_x.
+ *   psi, W  device float32 [n][n1][n2][n3];  e_dev  device float64 scalar
+ * Reduced in float64 in a fixed order (deterministic).
+ */
+int tx_exchange_energy_from_w(tx_ctx* ctx, const float* psi, const float* W, int n, double* e_dev,
+                              tx_stream_t stream);
 
 /*
  * Self-check of the tensor-core GEMM building block used by every tensor-core precision (no

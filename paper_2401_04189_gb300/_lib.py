@@ -26,7 +26,8 @@ EXPORTED = [
     "tx_reset_launch_count", "tx_exchange_apply_energy", "tx_profile_enable", "tx_profile_reset",
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
     "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
-    "tx_exchange_apply_static", "tx_describe_expansion_plan",
+    "tx_exchange_apply_static", "tx_describe_expansion_plan", "tx_set_wait_limit", "tx_selftest_wait",
+    "tx_exchange_energy_from_w",
 ]
 
 
@@ -119,6 +120,12 @@ def lib():
     L.tx_set_workspace_limit.restype = _I
     L.tx_check_device_error.argtypes = [_P]
     L.tx_check_device_error.restype = _I
+    L.tx_set_wait_limit.argtypes = [_P, ctypes.c_uint64]
+    L.tx_set_wait_limit.restype = _I
+    L.tx_selftest_wait.argtypes = [_P, _I, _P]
+    L.tx_selftest_wait.restype = _I
+    L.tx_exchange_energy_from_w.argtypes = [_P, _P, _P, _I, _P, _P]
+    L.tx_exchange_energy_from_w.restype = _I
     L.tx_status_string.argtypes = [_I]
     L.tx_status_string.restype = ctypes.c_char_p
     L.tx_last_error_message.argtypes = []
@@ -203,6 +210,10 @@ class Context:
     def check_device_error(self):
         _check(lib().tx_check_device_error(self.handle), "tx_check_device_error")
 
+    def set_wait_limit(self, ns):
+        """Time limit (ns) of the kernels' bounded device waits; 0 restores the default (2 s)."""
+        _check(lib().tx_set_wait_limit(self.handle, int(ns)), "tx_set_wait_limit")
+
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().tx_destroy(self._h)
@@ -256,6 +267,24 @@ def tx_exchange_apply_energy(ctx: Context, psi_occ, out=None, e_out=None, stream
                                         _stream(stream))
     _check(st, "tx_exchange_apply_energy")
     return out, e_out
+
+
+def tx_exchange_energy_from_w(ctx: Context, psi, W, e_out=None, stream=None):
+    """1/2 sum_i sum_x w(x) psi_i(x) W_i(x) as a float64 device scalar."""
+    ctx._block(psi, "psi")
+    ctx._block(W, "W")
+    if W.shape[0] != psi.shape[0]:
+        raise ValueError("psi and W must hold the same number of orbitals")
+    if e_out is None:
+        e_out = torch.empty((), dtype=torch.float64, device=psi.device)
+    st = lib().tx_exchange_energy_from_w(ctx.handle, _ptr(psi), _ptr(W), psi.shape[0], _ptr(e_out), _stream(stream))
+    _check(st, "tx_exchange_energy_from_w")
+    return e_out
+
+
+def tx_selftest_wait(ctx: Context, hold_tmem=True, stream=None):
+    """Launches the bounded-wait self-test (a wait nothing completes); see include/tuxc.h."""
+    _check(lib().tx_selftest_wait(ctx.handle, 1 if hold_tmem else 0, _stream(stream)), "tx_selftest_wait")
 
 
 def tx_profile_enable(enable=True):

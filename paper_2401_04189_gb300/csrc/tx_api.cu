@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "tx_internal.h"
@@ -64,15 +66,35 @@ static int check_ctx(const tx_ctx* c) {
     return TX_OK;
 }
 
-static int use_device(const tx_ctx* c) {
-    int cur = -1;
-    TX_TRY_CUDA(cudaGetDevice(&cur));
-    if (cur != c->device) TX_TRY_CUDA(cudaSetDevice(c->device));
-    return TX_OK;
+// ---- context registry (liveness and buffer generation) ---------------------------------
+static std::mutex g_ctx_mu;
+static std::unordered_map<const tx_ctx*, uint64_t> g_ctx_gen;
+static uint64_t g_gen_counter = 0;
+
+void ctx_register(tx_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    c->gen = ++g_gen_counter;
+    g_ctx_gen[c] = c->gen;
+}
+void ctx_unregister(const tx_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    g_ctx_gen.erase(c);
+}
+void bump_gen(tx_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    c->gen = ++g_gen_counter;
+    auto it = g_ctx_gen.find(c);
+    if (it != g_ctx_gen.end()) it->second = c->gen;
+}
+uint64_t ctx_generation(const tx_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    auto it = g_ctx_gen.find(c);
+    return it == g_ctx_gen.end() ? 0 : it->second;
 }
 
 int ensure_workspace(tx_ctx* c, size_t bytes) {
     if (bytes <= c->ws_bytes) return TX_OK;
+    bump_gen(c);
     if (c->ws) {
         cudaError_t e = cudaFree(c->ws);   // synchronises the device
         c->ws = nullptr;
@@ -91,6 +113,7 @@ int ensure_workspace(tx_ctx* c, size_t bytes) {
 
 int ensure_ebatch(tx_ctx* c, int nb) {
     if (nb <= c->ebatch_cap) return TX_OK;
+    bump_gen(c);
     if (c->d_ebatch) cudaFree(c->d_ebatch);
     c->d_ebatch = nullptr;
     int cap = std::max(nb, 64);
@@ -142,6 +165,7 @@ static int validate_setup(const int n[3], const double* const x[3], const double
 
 static void free_ctx(tx_ctx* c) {
     if (!c) return;
+    ctx_unregister(c);
     for (int d = 0; d < 3; ++d) {
         cudaFree(c->d_x[d]);
         cudaFree(c->d_w[d]);
@@ -191,6 +215,7 @@ extern "C" int tx_tucker_setup(tx_ctx** out, const int n[3], const double* x1, c
         delete c;
         return fail(TX_ERR_CUDA, "no CUDA device");
     }
+    ctx_register(c);
     c->T = T;
     c->prec = TX_PREC_FP32;
     c->ws_limit = (size_t)2 << 30;
@@ -229,10 +254,10 @@ extern "C" int tx_tucker_setup(tx_ctx** out, const int n[3], const double* x1, c
     }
     SETUP_TRY(dalloc(&c->d_theta, T));
     SETUP_TRY(dalloc(&c->d_mu, T));
-    SETUP_TRY(dalloc(&c->d_err, 4));
+    SETUP_TRY(dalloc(&c->d_err, kErrWords));
     if (cudaMemcpy(c->d_theta, gauss_exponents, sizeof(double) * T, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_mu, gauss_weights, sizeof(double) * T, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(int) * 4) != cudaSuccess)
+        cudaMemset(c->d_err, 0, sizeof(int) * kErrWords) != cudaSuccess)
         SETUP_TRY(fail(TX_ERR_CUDA, "set-up copy failed"));
     SETUP_TRY(setup_factor_matrices(c, s));
     SETUP_TRY(tx_set_precision(c, precision, stream));
@@ -244,7 +269,8 @@ extern "C" int tx_tucker_setup(tx_ctx** out, const int n[3], const double* x1, c
 
 extern "C" int tx_set_precision(tx_ctx* c, int precision, tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     if (precision < TX_PREC_FP32 || precision > TX_PREC_BF16X3)
         return fail(TX_ERR_UNSUPPORTED_PRECISION, "unknown precision");
     if (precision == TX_PREC_FP32) {
@@ -266,12 +292,10 @@ extern "C" int tx_set_precision(tx_ctx* c, int precision, tx_stream_t stream) {
 
 extern "C" void tx_destroy(tx_ctx* c) {
     if (!c || c->magic != kMagic) return;
-    int cur = -1;
-    cudaGetDevice(&cur);
-    cudaSetDevice(c->device);
+    DeviceGuard dg;
+    if (dg.use(c->device) != TX_OK) return;
     cudaDeviceSynchronize();
     free_ctx(c);
-    if (cur >= 0) cudaSetDevice(cur);
 }
 
 extern "C" size_t tx_workspace_bytes(const tx_ctx* c) { return (c && c->magic == kMagic) ? c->ws_bytes : 0; }
@@ -285,15 +309,38 @@ extern "C" int tx_set_workspace_limit(tx_ctx* c, size_t bytes) {
 
 extern "C" int tx_check_device_error(tx_ctx* c) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     int h[4] = {0, 0, 0, 0};
     TX_TRY_CUDA(cudaStreamSynchronize(c->last_stream));
     TX_TRY_CUDA(cudaMemcpy(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost));
-    TX_TRY_CUDA(cudaMemset(c->d_err, 0, sizeof(h)));
+    TX_TRY_CUDA(cudaMemset(c->d_err, 0, sizeof(h)));   // words 4..5 (the wait limit) are kept
     if (h[0] != 0)
         return fail(TX_ERR_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(h[0]) + ", where " +
-                                        std::to_string(h[1]) + ")");
+                                        std::to_string(h[1]) + "; drains that gave up: " + std::to_string(h[2]) + ")");
+    if (h[2] != 0)
+        return fail(TX_ERR_TIMEOUT, "a best-effort drain of in-flight copies gave up " + std::to_string(h[2]) + " time(s)");
     return TX_OK;
+}
+
+extern "C" int tx_set_wait_limit(tx_ctx* c, uint64_t ns) {
+    TX_TRY(check_ctx(c));
+    if (ns != 0 && (ns < 1000ull || ns > 60000000000ull))
+        return fail(TX_ERR_INVALID_ARG, "wait limit must be 0 (default 2 s) or between 1 us and 60 s");
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
+    TX_TRY_CUDA(cudaStreamSynchronize(c->last_stream));
+    TX_TRY_CUDA(cudaMemcpy(c->d_err + 4, &ns, sizeof(ns), cudaMemcpyHostToDevice));
+    return TX_OK;
+}
+
+extern "C" int tx_selftest_wait(tx_ctx* c, int hold_tmem, tx_stream_t stream) {
+    TX_TRY(check_ctx(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    return tc_wait_selftest(c, hold_tmem, s);
 }
 
 extern "C" const char* tx_status_string(int s) {
@@ -378,7 +425,8 @@ static void classify_targets(const tx_ctx* c, const float* occ, int n_occ, const
 extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
                                  float* out, tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     TX_TRY(check_block(psi_occ, n_occ, "psi_occ"));
     if (!psi_tgt) n_tgt = n_occ;
     else TX_TRY(check_block(psi_tgt, n_tgt, "psi_tgt"));
@@ -407,7 +455,8 @@ extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, con
 extern "C" int tx_exchange_apply_energy(tx_ctx* c, const float* psi_occ, int n_occ, float* out, double* e_dev,
                                         tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     TX_TRY(check_block(psi_occ, n_occ, "psi_occ"));
     TX_TRY(check_block(out, n_occ, "out"));
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
@@ -428,7 +477,8 @@ extern "C" int tx_exchange_apply_energy(tx_ctx* c, const float* psi_occ, int n_o
 
 extern "C" int tx_exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     TX_TRY(check_block(psi_occ, n_occ, "psi_occ"));
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
     if (!e_dev) return fail(TX_ERR_INVALID_ARG, "e_dev is NULL");
@@ -447,7 +497,8 @@ extern "C" int tx_exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, do
 extern "C" int tx_exchange_energy_grad(tx_ctx* c, const float* psi_occ, int n_occ, float* grad, double* e_dev,
                                        tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     TX_TRY(check_block(psi_occ, n_occ, "psi_occ"));
     TX_TRY(check_block(grad, n_occ, "grad"));
     if (n_occ < 1) return fail(TX_ERR_INVALID_ARG, "n_occ must be >= 1");
@@ -469,7 +520,8 @@ extern "C" int tx_exchange_energy_grad(tx_ctx* c, const float* psi_occ, int n_oc
 extern "C" int tx_exchange_apply_vjp(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
                                      const float* grad_out, float* grad_occ, float* grad_tgt, tx_stream_t stream) {
     TX_TRY(check_ctx(c));
-    TX_TRY(use_device(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
     TX_TRY(check_block(psi_occ, n_occ, "psi_occ"));
     if (!psi_tgt) return fail(TX_ERR_INVALID_ARG, "psi_tgt must be a separate target block");
     TX_TRY(check_block(psi_tgt, n_tgt, "psi_tgt"));
@@ -498,4 +550,25 @@ extern "C" int tx_exchange_apply_vjp(tx_ctx* c, const float* psi_occ, int n_occ,
     cs.out0 = grad_occ;
     cs.out1 = grad_tgt;
     return run_call(c, cs, s);
+}
+
+extern "C" int tx_exchange_energy_from_w(tx_ctx* c, const float* psi, const float* W, int n, double* e_dev,
+                                         tx_stream_t stream) {
+    TX_TRY(check_ctx(c));
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
+    TX_TRY(check_block(psi, n, "psi"));
+    TX_TRY(check_block(W, n, "W"));
+    if (n < 0) return fail(TX_ERR_INVALID_ARG, "n must be >= 0");
+    if (!e_dev) return fail(TX_ERR_INVALID_ARG, "e_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    if (n == 0) {
+        TX_TRY_CUDA(cudaMemsetAsync(e_dev, 0, sizeof(double), s));
+        return TX_OK;
+    }
+    const long total = (long)n * c->n[0] * c->n[1] * c->n[2];
+    const int nblocks = (int)std::max<long>(1, std::min<long>(1024, (total + 8191) / 8192));
+    TX_TRY(ensure_ebatch(c, nblocks + 1));
+    return weighted_dot(c, psi, W, n, c->d_ebatch, nblocks, 0.5, e_dev, s);
 }

@@ -34,6 +34,7 @@ struct tx_plan {
     cudaEvent_t fork;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    std::vector<uint64_t> captured_gen;    // generation of each item's context when the graph was captured
 };
 
 static constexpr uint32_t kPlanMagic = 0x54555031u;
@@ -265,6 +266,9 @@ extern "C" int tx_batch_plan(tx_plan** out, const tx_batch_item* items, int n_it
 
 extern "C" int tx_batch_launch(tx_plan* p, tx_stream_t stream) {
     if (!p || p->magic != kPlanMagic) return fail(TX_ERR_NOT_SETUP, "plan is NULL or was destroyed");
+    for (size_t i = 0; i < p->items.size(); ++i)
+        if (ctx_generation(p->items[i].ctx) == 0)
+            return fail(TX_ERR_NOT_SETUP, "batch item " + std::to_string(i) + ": its context was destroyed");
     cudaStream_t s = (cudaStream_t)stream;
     TX_TRY_CUDA(cudaEventRecord(p->fork, s));
     for (auto ss : p->streams) TX_TRY_CUDA(cudaStreamWaitEvent(ss, p->fork, 0));
@@ -288,6 +292,8 @@ extern "C" int tx_batch_capture(tx_plan* p, tx_stream_t stream) {
         cudaGraphDestroy(p->graph);
         p->graph = nullptr;
     }
+    p->captured_gen.clear();
+    for (const auto& it : p->items) p->captured_gen.push_back(ctx_generation(it.ctx));
     TX_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     const int st = tx_batch_launch(p, stream);
     cudaGraph_t g = nullptr;
@@ -296,6 +302,12 @@ extern "C" int tx_batch_capture(tx_plan* p, tx_stream_t stream) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
+    // the capture itself must not have replaced a buffer (the plan's warm-up sized them all)
+    for (size_t i = 0; i < p->items.size(); ++i)
+        if (ctx_generation(p->items[i].ctx) != p->captured_gen[i]) {
+            if (g) cudaGraphDestroy(g);
+            return fail(TX_ERR_NOT_SETUP, "a context buffer was replaced during capture");
+        }
     if (e != cudaSuccess) return fail(TX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     p->graph = g;
     TX_TRY_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
@@ -305,6 +317,15 @@ extern "C" int tx_batch_capture(tx_plan* p, tx_stream_t stream) {
 extern "C" int tx_batch_replay(tx_plan* p, tx_stream_t stream) {
     if (!p || p->magic != kPlanMagic) return fail(TX_ERR_NOT_SETUP, "plan is NULL or was destroyed");
     if (!p->exec) return fail(TX_ERR_NOT_SETUP, "no captured graph (call tx_batch_capture first)");
+    // the graph holds raw device pointers of its contexts' workspaces and operand copies:
+    // refuse to replay it once any of them was freed, replaced or destroyed
+    for (size_t i = 0; i < p->items.size(); ++i) {
+        const uint64_t g = ctx_generation(p->items[i].ctx);
+        if (g == 0 || i >= p->captured_gen.size() || g != p->captured_gen[i])
+            return fail(TX_ERR_NOT_SETUP, "batch item " + std::to_string(i) +
+                                              ": its context was destroyed or a buffer it uses was replaced since "
+                                              "the capture (call tx_batch_capture again)");
+    }
     count_launch();
     TX_TRY_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
     return TX_OK;

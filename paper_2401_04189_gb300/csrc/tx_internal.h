@@ -109,11 +109,43 @@ struct tx_ctx {
     int tile_bx, tile_nstage;   // forced expansion tile plan (0 = built-in choice)
     int acc_chunk;              // split precisions: Gaussian terms per phi accumulation chunk (0 = default)
     int consume_form;           // single-pass expansion: 0 = automatic (persistent where it applies), 1 = one CTA per item
+    uint64_t gen;               // bumped whenever a device buffer a captured launch may use is freed or replaced
 };
 
 namespace tx {
 
 constexpr uint32_t kMagic = 0x54554331u;
+
+// Device error block of a context (int words): [0] code of the first bounded wait that gave up
+// (1 = time limit), [1] where, [2] number of best-effort drains that gave up, [4..5] the wait
+// limit in ns as a 64-bit value (0 = the built-in 2 s).
+constexpr int kErrWords = 8;
+
+// Liveness and buffer generation of contexts: a captured batch graph holds raw device
+// pointers of its contexts, so replaying it is refused once any of them was freed or replaced.
+void ctx_register(tx_ctx* c);
+void ctx_unregister(const tx_ctx* c);
+void bump_gen(tx_ctx* c);
+// current generation of a live context; 0 if the context was destroyed (or never existed)
+uint64_t ctx_generation(const tx_ctx* c);
+
+// Makes a context's device current for the duration of one entry point and restores the
+// caller's device on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    int use(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return fail(TX_ERR_CUDA, "cudaGetDevice failed");
+        if (prev != dev) {
+            if (cudaSetDevice(dev) != cudaSuccess) return fail(TX_ERR_CUDA, "cudaSetDevice failed");
+            switched = true;
+        }
+        return TX_OK;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
 
 // ------------------------------------------------------------------------------------
 // SIMT (float32 CUDA-core) building blocks -- tx_simt.cu
@@ -152,12 +184,17 @@ int simt_adjoint_r(const tx_ctx* c, const PairRec* recs, int p0, int np, const F
 // energy reductions
 int reduce_energy_batch(const double* epart, long count, double* dst, cudaStream_t s);
 int finalize_energy(const double* batches, int nb, double scale, double* e_dev, cudaStream_t s);
+// e_dev = scale * sum_i sum_x w(x) A_i(x) B_i(x) over `count` orbitals, reduced in a fixed order
+// through partial[0 .. nblocks] (nblocks + 1 doubles of device scratch)
+int weighted_dot(const tx_ctx* c, const float* A, const float* B, int count, double* partial, int nblocks, double scale,
+                 double* e_dev, cudaStream_t s);
 
 // setup -- tx_setup.cu
 int setup_factor_matrices(tx_ctx* c, cudaStream_t s);
 
 // tensor-core path -- tx_tc.cu
 int tc_prepare(tx_ctx* c, cudaStream_t s);
+int tc_wait_selftest(tx_ctx* c, int hold_tmem, cudaStream_t s);
 void tc_release(tx_ctx* c);
 bool tc_supported(const tx_ctx* c, std::string* why);
 

@@ -86,9 +86,8 @@ extern "C" int tx_exchange_apply_static(tx_ctx* c, const float* psi_occ, int n_o
         const uintptr_t a = (uintptr_t)psi_occ, b = (uintptr_t)out;
         if (a < b + bytes && b < a + bytes) return fail(TX_ERR_INVALID_ARG, "out overlaps psi_occ");
     }
-    int cur = -1;
-    TX_TRY_CUDA(cudaGetDevice(&cur));
-    if (cur != c->device) TX_TRY_CUDA(cudaSetDevice(c->device));
+    DeviceGuard dg;   // the caller's current device is restored on return
+    TX_TRY(dg.use(c->device));
     void* base = nullptr;
     TX_TRY(static_scratch(c->device, &base));
     cudaStream_t s = (cudaStream_t)stream;

@@ -335,6 +335,33 @@ __global__ void k_finalize(const double* __restrict__ batches, int nb, double sc
     *e_dev = scale * s;
 }
 
+// partial[b] = sum over block b's share of the flat index (i, x, y, z) of w(x, y, z) a[i] b[i]:
+// float32 within groups of 32 products, float64 across groups and threads
+__global__ void __launch_bounds__(256) k_weighted_dot(const float* __restrict__ A, const float* __restrict__ B,
+                                                      const float* __restrict__ w1, const float* __restrict__ w2,
+                                                      const float* __restrict__ w3, int n1, int n2, int n3, long total,
+                                                      double* partial) {
+    __shared__ double red[8];
+    const long N23 = (long)n2 * n3, N3 = (long)n1 * N23;
+    const long stride = (long)gridDim.x * 256;
+    double s = 0.0;
+    float f = 0.f;
+    int cnt = 0;
+    for (long i = blockIdx.x * 256L + threadIdx.x; i < total; i += stride) {
+        const long r = i % N3;
+        const int x = (int)(r / N23), yz = (int)(r - x * N23), y = yz / n3, z = yz - y * n3;
+        f += w1[x] * w2[y] * w3[z] * A[i] * B[i];
+        if (++cnt == 32) {
+            s += (double)f;
+            f = 0.f;
+            cnt = 0;
+        }
+    }
+    s += (double)f;
+    const double tot = block_sum(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
 int smem_attr(const void* fn, size_t bytes) {
     if (bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -419,6 +446,17 @@ int reduce_energy_batch(const double* epart, long count, double* dst, cudaStream
     k_reduce<<<1, 256, 0, s>>>(epart, count, dst);
     TX_LAUNCHED();
     return TX_OK;
+}
+
+int weighted_dot(const tx_ctx* c, const float* A, const float* B, int count, double* partial, int nblocks, double scale,
+                 double* e_dev, cudaStream_t s) {
+    const long total = (long)count * c->n[0] * c->n[1] * c->n[2];
+    k_weighted_dot<<<nblocks, 256, 0, s>>>(A, B, c->f_w[0], c->f_w[1], c->f_w[2], c->n[0], c->n[1], c->n[2], total,
+                                           partial);
+    TX_LAUNCHED();
+    k_reduce<<<1, 256, 0, s>>>(partial, nblocks, partial + nblocks);
+    TX_LAUNCHED();
+    return finalize_energy(partial + nblocks, 1, scale, e_dev, s);
 }
 
 int finalize_energy(const double* batches, int nb, double scale, double* e_dev, cudaStream_t s) {

@@ -41,7 +41,39 @@ __global__ void k_static_operand(const double* __restrict__ src, long rows, int 
     }
 }
 
+// Self-test of the bounded device wait: one warp holds TMEM columns (when asked) and waits on an
+// mbarrier that nothing ever completes.  The wait gives up after the context's limit, records
+// the timeout in the error block, and the warp frees its TMEM and returns: the same unwinding
+// every pipeline kernel of this library goes through when one of its waits gives up.
+__global__ void __launch_bounds__(32, 1) k_wait_selftest(int* err, int hold_tmem) {
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_barrier_init();
+    }
+    __syncwarp();
+    if (hold_tmem) {
+        tc::tmem_alloc(&tbase, 32);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncwarp();
+    tc::tc_fence_after();
+    const bool ok = tc::mbar_wait(&bar, 0, err, 90);   // phase 0 never completes
+    (void)__all_sync(0xffffffffu, ok);
+    tc::tc_fence_before();
+    __syncwarp();
+    if (hold_tmem) tc::tmem_dealloc(tbase, 32);
+}
+
 }  // namespace
+
+int tc_wait_selftest(tx_ctx* c, int hold_tmem, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(c->d_err, hold_tmem ? 1 : 0);
+    TX_LAUNCHED();
+    return TX_OK;
+}
 
 TcScratch tc_scratch(const tx_ctx* c) {
     TcScratch s;
@@ -78,6 +110,7 @@ bool tc_supported(const tx_ctx* c, std::string* why) {
 
 void tc_release(tx_ctx* c) {
     if (!c->tc) return;
+    bump_gen(c);
     cudaFree(c->tc->buf);
     if (c->tc->img) cudaFree(c->tc->img);
     delete c->tc;
@@ -86,6 +119,7 @@ void tc_release(tx_ctx* c) {
 
 int tc_prepare(tx_ctx* c, cudaStream_t s) {
     tc_release(c);
+    bump_gen(c);
     TcOperands* op = new TcOperands();
     op->prec = c->prec;
     op->tf32 = c->prec == TX_PREC_TF32 || c->prec == TX_PREC_TF32X3;

@@ -10,8 +10,15 @@
 namespace tx {
 namespace tc {
 
-// a device-side wait gives up after this long, records where, and lets the kernel unwind
+// a device-side wait gives up after this long (unless the context sets another limit),
+// records where, and lets the kernel unwind
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+// The limit in force: words 4..5 of the context's error block (0 there = the default).
+__device__ __forceinline__ uint64_t wait_limit_ns(const int* err) {
+    const uint64_t v = *(const volatile unsigned long long*)(err + 4);
+    return v ? v : kWaitLimitNs;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -53,12 +60,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
+    const uint64_t lim = wait_limit_ns(err);
     while (true) {
 #pragma unroll 1
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (*(volatile int*)err != 0) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) {
+        if (globaltimer() - t0 > lim) {
             if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
             return false;
         }
@@ -81,9 +89,10 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 }
 __device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, int* err, int site) {
     const uint64_t t0 = globaltimer();
+    const uint64_t lim = wait_limit_ns(err);
     while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
         if (*(volatile int*)err != 0) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) {
+        if (globaltimer() - t0 > lim) {
             if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
             return false;
         }
@@ -91,12 +100,17 @@ __device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, i
     return true;
 }
 
-// Used on the error path only: waits (at most 100 ms, ignoring the error word) for copies
-// already issued into a stage, so that the CTA never exits with a TMA write in flight.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+// Best-effort wait (at most 100 ms, ignoring the error word) for copies or MMAs already issued
+// against a barrier, so that a CTA does not normally exit with a TMA write or an MMA in flight.
+// It is bounded, so it cannot guarantee that: a drain that gives up is counted in err[2], and
+// the host reports it as TX_ERR_TIMEOUT (tx_check_device_error).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* err) {
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > 100000000ull) return;
+        if (globaltimer() - t0 > 100000000ull) {
+            atomicAdd(err + 2, 1);
+            return;
+        }
 }
 
 // ---------------------------------------------------------------------------------------

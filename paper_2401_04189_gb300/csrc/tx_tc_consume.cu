@@ -358,7 +358,7 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
     }
     // never leave with a load in flight (error path)
     for (int set = 0; set < kEpiSets; ++set)
-        if (pending[set]) mbar_drain(&ebar[set], use[set] & 1);
+        if (pending[set]) mbar_drain(&ebar[set], use[set] & 1, a.err);
     if (lane == 0) bulk_wait_all();
     __syncwarp();
     return e;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok)
                 for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t)
-                    mbar_drain(&full_bar[t % NL], (t / NL) & 1);
+                    mbar_drain(&full_bar[t % NL], (t / NL) & 1, a.err);
         }
     } else if (warp == 9) {
         // ------------------------------ MMA issuer ------------------------------
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (fresh) {
                         since = now;
                         fresh = false;
-                    } else if (now - since > kWaitLimitNs) {
+                    } else if (now - since > wait_limit_ns(a.err)) {
                         if (atomicCAS(a.err, 0, 1) == 0) atomicExch(a.err + 1, 32);
                         ok = false;
                         break;
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(&phidone);
             // on the error path nobody else waits: keep the CTA (and its TMEM) until the MMAs
             // already issued have finished
-            if (!ok) mbar_drain(&phidone, 0);
+            if (!ok) mbar_drain(&phidone, 0, a.err);
         }
     } else {
         // ------------------------------ converters (warps 0-7) ------------------------------
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
             if (++s == NL) { s = 0; ph ^= 1; }
         }
         if (!ok)
-            for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1);
+            for (int t = (issued > NL ? issued - NL : 0); t < issued; ++t) mbar_drain(&full_bar[t % NL], (t / NL) & 1, a.err);
     } else if (warp == 10) {
         // ------------------- stage-3 producer: mu_t A_t3, and the Z prefetches -------------------
         // The slab's planes of one term are contiguous in Z: one L2 prefetch per term, issued
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
             if (++s == NL3) { s = 0; ph ^= 1; }
         }
         if (!ok)
-            for (int t = (issued > NL3 ? issued - NL3 : 0); t < issued; ++t) mbar_drain(&full3[t % NL3], (t / NL3) & 1);
+            for (int t = (issued > NL3 ? issued - NL3 : 0); t < issued; ++t) mbar_drain(&full3[t % NL3], (t / NL3) & 1, a.err);
     } else if (warp == 9) {
         // ------------------------------ stage-2 MMA issuer ------------------------------
         // descriptors are built once and advanced by adds: +32 bytes (2 units of the
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
         }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s2fin);
-        mbar_drain(&s2fin, 0);
+        mbar_drain(&s2fin, 0, a.err);
     } else {
         // ---------------- stage-3 MMA issuers (warps 0..nS3-1), then the epilogue ----------------
         // Issuing one tcgen05.mma costs a warp more time than the tensor pipe needs to run it at
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
             tc_fence_after();
             e = consume_epilogue_tma(a, em, rec, smem, ebar[warp], tPhi, x0, warp, lane);
         } else if (warp < a.ns3) {
-            mbar_drain(&phidone, 0);
+            mbar_drain(&phidone, 0, a.err);
         }
         if (a.flags & EPI_ENERGY) {
             for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -1139,7 +1139,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             }
         }
         if (!ok)
-            for (int g = (issued > NL ? issued - NL : 0); g < issued; ++g) mbar_drain(&full_bar[g % NL], (g / NL) & 1);
+            for (int g = (issued > NL ? issued - NL : 0); g < issued; ++g) mbar_drain(&full_bar[g % NL], (g / NL) & 1, a.err);
     } else if (warp == 10) {
         // ---------------- stage-3 producer: mu_t A_t3, and the Z L2 prefetches ----------------
         const size_t zterm = (size_t)a.n1 * a.z_plane;
@@ -1169,7 +1169,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 if (++s == NL3) { s = 0; ph ^= 1; }
             }
         if (!ok)
-            for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q) mbar_drain(&full3[q % NL3], (q / NL3) & 1);
+            for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q) mbar_drain(&full3[q % NL3], (q / NL3) & 1, a.err);
     } else if (warp == 9) {
         // ------------------------------ stage-2 MMA issuer ------------------------------
         const uint64_t d0 = sdesc_sw128(0);
@@ -1206,7 +1206,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s3fin[0]);
-        mbar_drain(&s3fin[0], 0);
+        mbar_drain(&s3fin[0], 0, a.err);
     } else if (warp == 11) {
         // ---------------- stage-3 MMA issuer: every plane and y tile ----------------
         const uint64_t d0 = sdesc_sw128(0);
@@ -1239,7 +1239,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s3fin[1]);
-        mbar_drain(&s3fin[1], 0);
+        mbar_drain(&s3fin[1], 0, a.err);
     } else {
         // ---------------- epilogue warps 0-7: one tile (plane / y tile) per warp ----------------
         const int q = warp & 3, jt = warp >> 2;
@@ -1385,7 +1385,7 @@ __global__ void __launch_bounds__(32, 1)
     __syncwarp();
     const bool ok = mbar_wait(&bar, 0, g.err, 47);
     if (!__all_sync(0xffffffffu, ok)) {
-        mbar_drain(&bar, 0);
+        mbar_drain(&bar, 0, g.err);
         return;
     }
     const uint4* src = (const uint4*)smem;
@@ -1667,6 +1667,7 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
 int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
     TcOperands* op = c->tc;
     if (op->img) {
+        bump_gen(c);
         cudaFree(op->img);
         op->img = nullptr;
     }

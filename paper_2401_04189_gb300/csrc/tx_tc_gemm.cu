@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128, 1)
         // do not leave the kernel with copies in flight
         if (!ok)
             for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-                mbar_drain(&full_bar[kb % kStages], (kb / kStages) & 1);
+                mbar_drain(&full_bar[kb % kStages], (kb / kStages) & 1, g.err);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = TF32 ? idesc_tf32(kBM, BN) : idesc_bf16(kBM, BN);
@@ -483,9 +483,9 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
             if (++s == 2) { s = 0; ph ^= 1; }
         }
         // do not leave the kernel with copies in flight
-        mbar_drain(&bbar, 0);
+        mbar_drain(&bbar, 0, g.err);
         if (!ok)
-            for (int j = (issued > 2 ? issued - 2 : 0); j < issued; ++j) mbar_drain(&afull[j & 1], (j >> 1) & 1);
+            for (int j = (issued > 2 ? issued - 2 : 0); j < issued; ++j) mbar_drain(&afull[j & 1], (j >> 1) & 1, g.err);
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = TF32 ? idesc_tf32(kBM, BN) : idesc_bf16(kBM, BN);
@@ -684,8 +684,8 @@ extern "C" int tx_selftest_gemm(int precision, int batch, int M, int N, int K, c
     g.a_z1 = 1; g.b_z1 = 1;
     g.C = D; g.c_m = N; g.c_n = 1; g.c_b1 = (long)M * N; g.c_type = TC_OUT_F32; g.alpha = 1.f;
     static int* d_err = nullptr;
-    if (!d_err) TX_TRY_CUDA(cudaMalloc(&d_err, 4 * sizeof(int)));
-    TX_TRY_CUDA(cudaMemsetAsync(d_err, 0, 4 * sizeof(int), s));
+    if (!d_err) TX_TRY_CUDA(cudaMalloc(&d_err, kErrWords * sizeof(int)));
+    TX_TRY_CUDA(cudaMemsetAsync(d_err, 0, kErrWords * sizeof(int), s));
     g.err = d_err;
     int st = tc_gemm_launch(oa, ob, g, tf32, split, "selftest", s);
     cudaStreamSynchronize(s);

@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok && threadIdx.x == 0) {
         mma_commit(&done_bar);
         // do not exit with copies in flight: wait (bounded) for every issued stage
-        for (int kb = (issued > 2 ? issued - 2 : 0); kb < issued; ++kb) mbar_drain(&full_bar[kb & 1], (kb >> 1) & 1);
-        mbar_drain(&u_bar, 0);
+        for (int kb = (issued > 2 ? issued - 2 : 0); kb < issued; ++kb) mbar_drain(&full_bar[kb & 1], (kb >> 1) & 1, a.err);
+        mbar_drain(&u_bar, 0, a.err);
     }
     __syncwarp();
     // epilogue: S1[p][gamma][x][y]
@@ -315,9 +315,9 @@ __global__ void __launch_bounds__(kP3Threads, 1)
             }
         }
         // do not leave the kernel with copies in flight
-        mbar_drain(&u_bar, 0);
+        mbar_drain(&u_bar, 0, a.err);
         if (!ok)
-            for (int q = (issued > 2 ? issued - 2 : 0); q < issued; ++q) mbar_drain(&pfull[q & 1], (q >> 1) & 1);
+            for (int q = (issued > 2 ? issued - 2 : 0); q < issued; ++q) mbar_drain(&pfull[q & 1], (q >> 1) & 1, a.err);
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = TF32 ? idesc_tf32(128, a.N3p) : idesc_bf16(128, a.N3p);

@@ -19,13 +19,11 @@ def target_range(n_tgt: int, world: int, rank: int):
     return start, start + base + (1 if rank < extra else 0)
 
 
-def energy_share(psi_tgt: torch.Tensor, W_tgt: torch.Tensor, w1, w2, w3) -> torch.Tensor:
-    """1/2 sum_i sum_x w(x) psi_i(x) W_i(x) over the given targets, in float64 (0-d tensor);
-    w1, w2, w3 are the 1-D quadrature weights, w(x) their tensor product."""
-    dev = psi_tgt.device
-    w1, w2, w3 = (torch.as_tensor(v, dtype=torch.float64, device=dev) for v in (w1, w2, w3))
-    w = w1[:, None, None] * w2[None, :, None] * w3[None, None, :]
-    return 0.5 * (psi_tgt.double() * W_tgt.double() * w).sum()
+def energy_share(ctx, psi_tgt: torch.Tensor, W_tgt: torch.Tensor) -> torch.Tensor:
+    """This rank's share 1/2 sum_i sum_x w(x) psi_i(x) W_i(x) over its targets, computed by the
+    library (tx_exchange_energy_from_w) as a float64 device scalar."""
+    from ._lib import tx_exchange_energy_from_w
+    return tx_exchange_energy_from_w(ctx, psi_tgt, W_tgt)
 
 
 def combine_energy(e_local: torch.Tensor, group=None) -> torch.Tensor:

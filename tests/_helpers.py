@@ -1,4 +1,7 @@
 """Shared helpers for the GPU parity tests (the oracle is the reference everywhere)."""
+import json
+import os
+
 import numpy as np
 
 import oracle as O
@@ -13,6 +16,45 @@ import oracle as O
 # every 5 Gaussian terms.  Measured worst cases: tf32x3 2.9e-6 (Pt-shaped block), bf16x3 5e-6.
 W_TOL = {"fp32": 2e-6, "tf32x3": 5e-6, "bf16x3": 1e-5, "tf32": 5e-3, "bf16": 2e-2}
 E_TOL = {"fp32": 1e-6, "tf32x3": 5e-6, "bf16x3": 1e-5, "tf32": 5e-3, "bf16": 1e-2}
+
+
+# Elementwise bound: max |W_gpu - W_ref| / max |W_ref| over the compared block, per GEMM
+# arithmetic.  The largest errors sit where |W| is largest, so this is of the order of the
+# Frobenius error; the bound catches a wrong ragged tile or a dropped slab that carries little
+# of the norm, which the Frobenius check alone would let through.
+# Measured worst cases over the parity suite (GB300): fp32 4.4e-7 (8.0e-7 for gradients, which
+# take 5x the bound), bf16 7.7e-3, tf32 2.0e-3, tf32x3 3.3e-6, bf16x3 7.2e-6.
+ELEM_TOL = {"fp32": 2e-6, "tf32x3": 8e-6, "bf16x3": 1.5e-5, "tf32": 5e-3, "bf16": 1.6e-2}
+
+
+def elem_rel(a, b):
+    """(max |a - b| / max |b|, index of the largest |a - b|)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.abs(a - b)
+    k = int(np.argmax(d))
+    return float(d.ravel()[k] / np.abs(b).max()), np.unravel_index(k, d.shape)
+
+
+def _log(entry):
+    path = os.environ.get("TX_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(entry) + "\n")
+
+
+def assert_close(got, ref, prec, what="W", scale=1.0):
+    """Frobenius and elementwise parity against the oracle at the precision's tolerances
+    (times `scale`); the message names the worst element."""
+    fr = rel(got, ref)
+    el, idx = elem_rel(got, ref)
+    _log(dict(what=what, prec=prec, frob=fr, elem=el))
+    assert fr < scale * W_TOL[prec], f"{what} [{prec}]: Frobenius error {fr:.3e} >= {scale * W_TOL[prec]:.1e}"
+    assert el < scale * ELEM_TOL[prec], (
+        f"{what} [{prec}]: elementwise error {el:.3e} >= {scale * ELEM_TOL[prec]:.1e} at index {tuple(int(v) for v in idx)}"
+        f" (got {np.asarray(got).ravel()[np.ravel_multi_index(idx, np.shape(got))]:.6e},"
+        f" oracle {np.asarray(ref).ravel()[np.ravel_multi_index(idx, np.shape(ref))]:.6e})")
+    return fr, el
 
 
 def rel(a, b):

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _helpers import E_TOL, W_TOL, max_row_rel, rel, to_gpu
+from _helpers import E_TOL, W_TOL, assert_close, max_row_rel, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,7 @@ def test_apply_small_config_matches_oracle(prec):
     S = O.Setup.from_system(s)
     ref = O.exchange_apply(s.psi, S)
     got = gpu_apply(s, prec, "self")
-    assert rel(got, ref) < W_TOL[prec]
+    assert_close(got, ref, prec, "small")
     assert max_row_rel(got, ref) < 2 * W_TOL[prec]
 
 
@@ -95,7 +95,7 @@ def test_apply_ragged_shapes(prec, targets):
         tgt = (s.psi[:3] * 0.7 + 0.2 * rng.standard_normal(s.psi[:3].shape) * np.abs(s.psi[:3]).max()).astype(np.float32)
         ref = O.exchange_apply(s.psi, S, psi_tgt=tgt)
         got = gpu_apply(s, prec, tgt)
-    assert rel(got, ref) < W_TOL[prec]
+    assert_close(got, ref, prec, f"ragged-{targets}")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -110,14 +110,14 @@ def test_pair_batching_does_not_change_the_result(prec):
 def test_single_orbital_single_term(prec):
     s = W.config_small(n=16, n_orb=1, rank=6, T=1, L=5.0)
     S = O.Setup.from_system(s)
-    assert rel(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S)) < W_TOL[prec]
+    assert_close(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S), prec, "single")
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_full_rank_operator(prec):
     s = W.config_small(n=16, n_orb=3, rank=16, T=6, L=5.0, full_rank=True)
     S = O.Setup.from_system(s)
-    assert rel(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S)) < W_TOL[prec]
+    assert_close(gpu_apply(s, prec, "self"), O.exchange_apply(s.psi, S), prec, "full-rank")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -129,7 +129,7 @@ def test_energy_gradient_matches_oracle(prec):
     ctx = P.Context.from_system(s, precision=prec)
     e, g = P.tx_exchange_energy_grad(ctx, to_gpu(s.psi))
     assert abs(float(e.item()) - E_ref) / abs(E_ref) < E_TOL[prec]
-    assert rel(g.cpu().numpy(), g_ref) < 5 * W_TOL[prec]
+    assert_close(g.cpu().numpy(), g_ref, prec, "grad", scale=5)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -143,8 +143,8 @@ def test_apply_vjp_matches_oracle(prec):
     go_ref, gt_ref = O.exchange_apply_vjp(s.psi, tgt, cot, S)
     ctx = P.Context.from_system(s, precision=prec)
     go, gt = P.tx_exchange_apply_vjp(ctx, to_gpu(s.psi), to_gpu(tgt), to_gpu(cot))
-    assert rel(go.cpu().numpy(), go_ref) < 5 * W_TOL[prec]
-    assert rel(gt.cpu().numpy(), gt_ref) < 5 * W_TOL[prec]
+    assert_close(go.cpu().numpy(), go_ref, prec, "vjp-occ", scale=5)
+    assert_close(gt.cpu().numpy(), gt_ref, prec, "vjp-tgt", scale=5)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -156,7 +156,7 @@ def test_pt_shaped_block_sampled_rows(prec):
     got = gpu_apply(s, prec, "self")
     for i in (0, 37):
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[i:i + 1])
-        assert rel(got[i:i + 1], ref) < W_TOL[prec]
+        assert_close(got[i:i + 1], ref, prec, f"pt-row{i}")
 
 
 def test_invalid_alignment_and_null_are_rejected():
@@ -267,12 +267,12 @@ def test_expansion_forms_agree(prec, system):
     assert abs(energies[0] - energies[1]) <= 1e-5 * abs(energies[1])
     if system != "pt8":
         ref = O.exchange_apply(s.psi, S)
-        assert rel(outs[0], ref) < W_TOL[prec]
+        assert_close(outs[0], ref, prec, f"forms-{system}")
         e_ref = O.exchange_energy(s.psi, S)
         assert abs(energies[0] - e_ref) / abs(e_ref) < E_TOL[prec]
     else:
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
-        assert rel(outs[0][3:4], ref) < W_TOL[prec]
+        assert_close(outs[0][3:4], ref, prec, "forms-pt8")
     with pytest.raises(P.TuckerExchangeError):
         P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
 
@@ -294,7 +294,7 @@ def test_large_grid_two_y_tiles(prec, rank, kernel):
     got = P.tx_exchange_apply(ctx, occ).cpu().numpy()
     e = float(P.tx_exchange_energy(ctx, occ).item())
     ctx.check_device_error()
-    assert rel(got, ref) < W_TOL[prec]
+    assert_close(got, ref, prec, f"n160-r{rank}")
     e_ref = O.exchange_energy(s.psi, S)
     assert abs(e - e_ref) / abs(e_ref) < E_TOL[prec]
 
@@ -316,7 +316,7 @@ def test_sharded_apply_matches_oracle(prec):
             ctx.check_device_error()
             assert Wl.shape[0] == b - a
             if b > a:
-                assert rel(Wl.cpu().numpy(), ref[a:b]) < W_TOL[prec]
+                assert_close(Wl.cpu().numpy(), ref[a:b], prec, "sharded")
 
 
 @pytest.fixture(scope="module")
@@ -340,7 +340,7 @@ def test_energy_gradient_differentiation_workload(prec, diff_case):
     ctx.check_device_error()
     assert abs(float(e.item()) - E_ref) / abs(E_ref) < E_TOL[prec]
     g = g.cpu().numpy()
-    assert rel(g, g_ref) < 5 * W_TOL[prec]
+    assert_close(g, g_ref, prec, "grad-diff", scale=5)
     x = psi.clone().requires_grad_(True)
     E = P.exchange_energy(ctx, x)
     E.backward()

@@ -2,8 +2,9 @@
 a library call cudaMalloc: applications whose device memory belongs to their own arena or pool
 allocator, and loops that cannot afford the device-wide synchronisation cudaMalloc may cause.
 It keeps all scratch in one fixed device array, so it must give the same result as the regular
-entry point on consecutive calls (the array keeps the previous call's contents), and it must
-refuse sizes whose scratch does not fit.  This file is collected last on purpose."""
+entry point on consecutive calls (the array keeps the previous call's contents), allocate
+nothing (the context's workspace stays empty and the device's free memory does not change),
+and refuse sizes whose scratch does not fit.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -33,19 +34,29 @@ def test_static_scratch_apply_matches_regular_apply_twice(prec):
     import torch
     import paper_2401_04189_gb300 as P
     s = W.config_small()
-    ctx = P.Context.from_system(s, precision=prec)
     psi = to_gpu(s.psi)
-    ctx.set_precision("fp32")                  # the reference: the regular float32 entry point
-    ref = P.tx_exchange_apply(ctx, psi).cpu().numpy()
-    ctx.set_precision(prec)                    # the static entry point runs float32 kernels anyway
+    # the reference: the regular float32 entry point, on a context of its own
+    ref_ctx = P.Context.from_system(s, precision="fp32")
+    ref = P.tx_exchange_apply(ref_ctx, psi).cpu().numpy()
+    ref_ctx.destroy()
+    # a fresh context that never runs the regular apply (so it holds no workspace)
+    ctx = P.Context.from_system(s, precision=prec)
+    assert ctx.workspace_bytes() == 0
     out = torch.empty_like(psi)
-    for call in range(2):
+    torch.cuda.synchronize()
+    for call in range(3):
         out.fill_(7.0)                          # stale output must not leak into the result
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = _call(P, ctx, psi, out)
         assert st == 0, P.lib().tx_last_error_message()
         torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
         ctx.check_device_error()
         assert rel(out.cpu().numpy(), ref) < W_TOL["fp32"], f"call {call}"
+        assert ctx.workspace_bytes() == 0, "the static entry point sized the context workspace"
+        if call > 0:                            # after the first call every kernel is loaded
+            assert free_after == free_before, f"call {call}: device free memory changed by {free_before - free_after}"
 
 
 def test_static_scratch_apply_rejects_too_large_sizes():
@@ -62,3 +73,4 @@ def test_static_scratch_apply_rejects_too_large_sizes():
     assert st == -9
     msg = P.lib().tx_last_error_message().decode()
     assert "bytes of scratch" in msg and "33554432" in msg
+    assert ctx.workspace_bytes() == 0
