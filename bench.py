@@ -1,18 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark: orbital-pair exchange applications per second on the Pt-cluster-shaped block.
+"""Benchmark: orbital-pair exchange applications per second (K psi_i = -sum_j psi_j phi_ij).
 
-Workload (synthetic, seeded): 96^3 uniform grid on [-12,12]^3, 64 orthonormal Gaussian-sum
-orbitals over 8 fcc centres (spacing 2.6 bohr), shared Tucker rank 40 per mode from the
-density HOSVD, 40-term Gaussian sum of 1/r.  One step = one tx_exchange_apply_energy call:
-K psi_i = -sum_j psi_j phi_ij for all 64 targets against all 64 occupied orbitals (4096
-ordered pair applications, 2080 distinct pair potentials) plus E_x in the same epilogue.
-psi (226 MB) and W (226 MB) are larger than L2 (129 MB), so no flush is needed between steps.
+Default workload, the largest configuration (synthetic, seeded, generated on the device): the
+TiO2-cluster-shaped block, a 160^3 uniform grid on [-16,16]^3 with 1842 occupied orbitals
+(Gaussian sums over 16 of 240 rutile-like centres, 2 exponents U[0.2,3] each, orthonormalised in
+float64), shared Tucker rank 64 per mode from the density HOSVD, a 45-term Gaussian sum of 1/r.
+One step = one tx_exchange_apply of the first 256 orbitals (the targets) against all 1842:
+471,552 ordered pair applications, 438,912 distinct pair potentials (a pair of two targets is
+computed once).  psi (30.2 GB) and W (4.2 GB) are far larger than L2 (129 MB): no flush needed.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32x3|fp32|...]
-  python bench.py --impl reference     # the FP64 oracle on the host cores, same metric
+`--workload pt` runs the Pt-cluster-shaped block instead (96^3, 64 orbitals, rank 40, 40 terms,
+one tx_exchange_apply_energy of all 64 against all 64 per step); the default run also reports it
+in `secondary` (bf16, the split-precision tf32x3 form and the float32 CUDA-core form).
 
-Under torchrun each rank applies K to its own copy of the block (independent replicas,
-weak scaling, no collective on the data path); rank 0 prints one JSON line.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32x3|fp32|...] [--workload tio2|pt]
+  python bench.py --impl reference     # the FP64 oracle on the host cores, same metric and workload
+
+Under torchrun each rank applies K to its own copy of the block (independent replicas, weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -30,22 +35,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "orbital-pair exchange applications/s"
-WORKLOAD = dict(workload="Pt-cluster-shaped block", n=96, box="[-12,12]^3", orbitals=64, rank=40, terms=40,
-                pairs_ordered=64 * 64, pairs_unique=64 * 65 // 2, seed=1)
+WORKLOADS = {
+    "tio2": dict(workload="TiO2-cluster-shaped block", n=160, box="[-16,16]^3", occupied=1842, targets=256,
+                 rank=64, terms=45, seed=4),
+    "pt": dict(workload="Pt-cluster-shaped block", n=96, box="[-12,12]^3", occupied=64, targets=64, rank=40,
+               terms=40, seed=1),
+}
+DEFAULT_STEPS = {"tio2": 2, "pt": 10}
+TIO2_SAMPLE_OCC = 32        # oracle sample: 1 target against this many occupied orbitals
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto")
+    ap.add_argument("--workload", default="tio2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--orbitals", type=int, default=64,
-                    help="use only the first N orbitals of the block (smaller cases for profiling)")
-    return ap.parse_args()
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--occupied", type=int, default=None,
+                    help="use only the first N occupied orbitals of the block (smaller cases for profiling)")
+    ap.add_argument("--targets", type=int, default=None, help="TiO2-shaped block: number of target orbitals")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = DEFAULT_STEPS[a.workload]
+    return a
 
 
 def flops_per_pair(n, r, T):
@@ -53,59 +70,90 @@ def flops_per_pair(n, r, T):
     return (T + 1) * P + 3 * n ** 3
 
 
+def pair_counts(n_occ, n_tgt, subset=True):
+    """(ordered pair applications, distinct pair potentials) of targets = the first n_tgt
+    occupied orbitals (a pair of two targets is one potential)."""
+    ordered = n_occ * n_tgt
+    return ordered, ordered - (n_tgt * (n_tgt - 1) // 2 if subset else 0)
+
+
 # ----------------------------------------------------------------------------------------
-# oracle timing (the CPU baseline and the reference arm)
+# oracle timing (the CPU baseline and the reference arm): a subprocess on all host cores
 # ----------------------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
-import json, os, sys, time
+import json, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
 import oracle as O, workloads as W
-s = W.config_pt()
+d = np.load({inp!r})
+s = W.System("sample", [d["x1"], d["x2"], d["x3"]], [d["w1"], d["w2"], d["w3"]], [d["U1"], d["U2"], d["U3"]],
+             d["theta"], d["mu"], d["occ"], 0.0)
 S = O.Setup.from_system(s)
-targets = {targets!r}
 t0 = time.perf_counter()
-Wrows = O.exchange_apply(s.psi, S, psi_tgt=s.psi[targets])
+Wrows = O.exchange_apply(d["occ"], S, psi_tgt=d["tgt"])
 dt = time.perf_counter() - t0
 np.save({out!r}, Wrows)
-print(json.dumps(dict(seconds=dt, pairs=len(targets) * s.psi.shape[0])))
+print(json.dumps(dict(seconds=dt, pairs=int(d["tgt"].shape[0] * d["occ"].shape[0]))))
 """
 
 
-def run_oracle_sample(targets, out_path):
+def run_oracle(s, occ, tgt, workdir):
+    """The oracle's rows K tgt against occ for system s (its grid, basis and Gaussian sum), timed
+    in a subprocess on every host core: (W rows, seconds, ordered pairs, cores)."""
+    import numpy as np
     cores = os.cpu_count() or 1
+    inp = os.path.join(workdir, "oracle_in.npz")
+    out = os.path.join(workdir, "oracle_out.npy")
+    np.savez(inp, x1=s.x[0], x2=s.x[1], x3=s.x[2], w1=s.w[0], w2=s.w[1], w3=s.w[2], U1=s.U[0], U2=s.U[1],
+             U3=s.U[2], theta=s.theta, mu=s.mu, occ=np.asarray(occ, dtype=np.float32),
+             tgt=np.asarray(tgt, dtype=np.float32))
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
-    code = ORACLE_SNIPPET.format(root=ROOT, targets=list(targets), out=out_path)
+    code = ORACLE_SNIPPET.format(root=ROOT, inp=inp, out=out)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if p.returncode != 0:
         raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
     res = json.loads(p.stdout.strip().splitlines()[-1])
-    res["cores"] = cores
-    return res
+    return np.load(out), res["seconds"], res["pairs"], cores
+
+
+def oracle_sample_system(workload):
+    """Host inputs for the oracle's bounded sample: the Pt-shaped block itself, or a TiO2-shaped
+    block of 1 + TIO2_SAMPLE_OCC orbitals generated on the host with the same grid, rank, terms
+    and orbital recipe (the oracle's cost per pair does not depend on the orbital values)."""
+    import workloads as W
+    if workload == "pt":
+        s = W.config_pt()
+        return s, s.psi, s.psi[0:1], "1 target x 64 occupied orbitals of the Pt-shaped block"
+    cfg = WORKLOADS["tio2"]
+    s = W.make_system("tio2", cfg["n"], 16.0, 1 + TIO2_SAMPLE_OCC, cfg["rank"], cfg["terms"], cfg["seed"],
+                      W.rutile_cluster(240), 2, (0.2, 3.0), centres_per_orbital=16)
+    return (s, s.psi[1:], s.psi[0:1],
+            f"1 target x {TIO2_SAMPLE_OCC} occupied orbitals of a TiO2-shaped block (160^3, rank 64, 45 terms) "
+            f"generated on the host")
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    targets = [0]
+    s, occ, tgt, what = oracle_sample_system(args.workload)
+    times = []
     with tempfile.TemporaryDirectory() as td:
-        times = []
         for i in range(args.warmup + args.steps):
-            res = run_oracle_sample(targets, os.path.join(td, "w.npy"))
+            _, sec, pairs, cores = run_oracle(s, occ, tgt, td)
             if i >= args.warmup:
-                times.append(res["seconds"])
-    units = res["pairs"]
+                times.append(sec)
     tot = sum(times)
-    value = units * len(times) / tot
+    value = pairs * len(times) / tot
+    cfg = dict(WORKLOADS[args.workload])
     line = dict(impl="reference", metric=METRIC, value=value, unit="pairs/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000 * tot / len(times), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(WORKLOAD, sample=f"{len(targets)} target x 64 occupied orbitals per step"),
-                cpu_baseline=dict(value=value, unit="pairs/s", cores=res["cores"], kind="oracle",
-                                  sample=f"{units} ordered pairs (target 0 against all 64 orbitals) per step"),
+                config=dict(cfg, sample=f"{what} per step"),
+                cpu_baseline=dict(value=value, unit="pairs/s", cores=cores, kind="oracle",
+                                  sample=f"{pairs} ordered pairs per step: {what}"),
                 e2e=dict(value=value, unit="pairs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -152,15 +200,19 @@ class ClockSampler:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
-                    reasons=reasons, samples=len(rows))
+                    power_w_max=max(pw) if pw else None, reasons=reasons, samples=len(rows))
 
 
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
+PROFILED = ("consume", "project", "gemm", "tc_consume", "tc_zprod", "tc_project", "tc_proj2", "tc_proj1")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -188,24 +240,41 @@ def main():
     prec = args.precision
     if prec == "auto":
         prec = getattr(P, "DEFAULT_BENCH_PRECISION", "fp32")
-    s = W.config_pt()
-    if args.orbitals != s.psi.shape[0]:
-        s.psi = s.psi[: args.orbitals].copy()
+    cfg = dict(WORKLOADS[args.workload])
+    t_setup = time.perf_counter()
+    if args.workload == "tio2":
+        n_occ = args.occupied or cfg["occupied"]
+        s, psi = W.config_tio2_on_device(n_orb=n_occ, device=dev)
+        n_tgt = min(args.targets or cfg["targets"], n_occ)
+        l2 = f"inputs larger than L2 (psi {psi.numel() * 4 / 1e9:.1f} GB, W {n_tgt * psi[0].numel() * 4 / 1e9:.1f} GB)"
+    else:
+        s = W.config_pt()
+        if args.occupied and args.occupied < s.psi.shape[0]:
+            s.psi = s.psi[: args.occupied].copy()
+        psi = torch.from_numpy(s.psi).to(dev)
+        n_occ = n_tgt = psi.shape[0]
+        l2 = "inputs larger than L2 (psi 226 MB, W 226 MB)"
+    setup_s = time.perf_counter() - t_setup
     n, r, T = s.n[0], s.r[0], s.T
-    N = s.psi.shape[0]
+    ordered, unique = pair_counts(n_occ, n_tgt)
     stream = torch.cuda.current_stream()
     ctx = P.Context.from_system(s, precision=prec)
-    psi_host = torch.from_numpy(s.psi).pin_memory()
-    psi = psi_host.to(dev, non_blocking=False)
-    out = torch.empty_like(psi)
+    ctx.set_workspace_limit(16 << 30)          # pair batches of up to 16 GiB of intermediates
+    out = torch.empty((n_tgt,) + tuple(psi.shape[1:]), dtype=torch.float32, device=dev)
     e = torch.empty((), dtype=torch.float64, device=dev)
+    tio2 = args.workload == "tio2"
 
-    def step():
-        P.tx_exchange_apply_energy(ctx, psi, out=out, e_out=e)
+    def step(src=None):
+        src = psi if src is None else src
+        if tio2:
+            P.tx_exchange_apply(ctx, src, src[:n_tgt], out=out)
+        else:
+            P.tx_exchange_apply_energy(ctx, src, out=out, e_out=e)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    ctx.check_device_error()
 
     def barrier():
         if world > 1:
@@ -230,88 +299,145 @@ def main():
     ck = clocks.stop()
     P.tx_profile_enable(False)
     launches = P.tx_launch_count()
+    ctx.check_device_error()
     ms = ev0.elapsed_time(ev1) / args.steps
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    pairs = N * N
-    value = world * pairs / (ms_max / 1000.0)
+    value = world * ordered / (ms_max / 1000.0)
 
     # ---- dominant kernel: live per-launch device time from the profiling events
     prof = {}
-    for name in ("consume", "project", "gemm", "tc_consume", "tc_zprod", "tc_project", "tc_g"):
+    for name in PROFILED:
         k, kms = P.tx_profile_read(name)
         if k:
             prof[name] = (k, kms)
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    roof = roofline(dom, prof, n, r, T, N, args.steps, prec, peaks, ck)
+    roof = roofline(dom, prof, n, r, T, unique, args.steps, prec, peaks, ck, args.workload)
 
-    # ---- end to end through the public API with host buffers (pinned), copies timed
+    # ---- end to end through the public API with host buffers (pinned), copies timed: the
+    # occupied block goes up and W (and E_x) comes down in every step
     e2e = None
     if not args.no_e2e:
-        out_host = torch.empty_like(psi_host).pin_memory()
-        e_host = torch.empty((), dtype=torch.float64).pin_memory()
+        psi_host = torch.empty(psi.shape, dtype=torch.float32, pin_memory=True)
+        psi_host.copy_(psi)
+        out_host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        e_host = torch.empty((), dtype=torch.float64, pin_memory=True)
         psi_e2e = torch.empty_like(psi)
-        for _ in range(2):
+
+        def e2e_step():
             psi_e2e.copy_(psi_host, non_blocking=True)
-            P.tx_exchange_apply_energy(ctx, psi_e2e, out=out, e_out=e)
+            step(psi_e2e)
             out_host.copy_(out, non_blocking=True)
-            e_host.copy_(e, non_blocking=True)
+            if not tio2:
+                e_host.copy_(e, non_blocking=True)
+
+        e2e_steps = 1 if tio2 else args.steps
+        if not tio2:
+            for _ in range(2):
+                e2e_step()
         barrier()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        for _ in range(args.steps):
-            psi_e2e.copy_(psi_host, non_blocking=True)
-            P.tx_exchange_apply_energy(ctx, psi_e2e, out=out, e_out=e)
-            out_host.copy_(out, non_blocking=True)
-            e_host.copy_(e, non_blocking=True)
+        for _ in range(e2e_steps):
+            e2e_step()
         a1.record(stream)
         barrier()
-        ems = a0.elapsed_time(a1) / args.steps
+        ems = a0.elapsed_time(a1) / e2e_steps
         te = torch.tensor([ems], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = dict(value=world * pairs / (float(te.item()) / 1000.0), unit="pairs/s",
-                   h2d_bytes_per_step=psi.numel() * 4, d2h_bytes_per_step=out.numel() * 4 + 8,
-                   ms_per_step=float(te.item()))
+        e2e = dict(value=world * ordered / (float(te.item()) / 1000.0), unit="pairs/s",
+                   h2d_bytes_per_step=psi.numel() * 4, d2h_bytes_per_step=out.numel() * 4 + (0 if tio2 else 8),
+                   ms_per_step=float(te.item()), steps=e2e_steps)
+        del psi_e2e, psi_host, out_host
 
-    # ---- accuracy of this run against the FP64 oracle (sampled target rows), rank 0 only
+    # ---- accuracy of this run against the FP64 oracle, and the oracle's own rate (rank 0)
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline and N == 64:
+    secondary = None
+    if rank == 0 and not args.no_cpu_baseline:
         with tempfile.TemporaryDirectory() as td:
-            targets = [0, 37]
-            res = run_oracle_sample(targets, os.path.join(td, "w.npy"))
-            ref = np.load(os.path.join(td, "w.npy"))
-        got = out[targets].double().cpu().numpy()
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        cpu = dict(value=res["pairs"] / res["seconds"], unit="pairs/s", cores=res["cores"], kind="oracle",
-                   sample=f"{res['pairs']} ordered pairs (targets 0 and 37 against all 64 orbitals), "
-                          f"{res['seconds']:.2f} s of FP64 numpy")
+            if tio2:
+                # the kernels on TiO2-shaped data: targets 0 and 5 against the first 8 occupied
+                # orbitals of the bench block, GPU and oracle on the same float32 inputs
+                occ8 = psi[:8]
+                got = P.tx_exchange_apply(ctx, occ8, occ8[[0, 5]].contiguous()).double().cpu().numpy()
+                ref, _, _, _ = run_oracle(s, occ8.cpu().numpy(), occ8[[0, 5]].cpu().numpy(), td)
+                err_what = "targets 0 and 5 against the first 8 occupied orbitals of the block"
+            else:
+                ref, _, _, _ = run_oracle(s, s.psi, s.psi[[0, 37]], td)
+                got = out[[0, 37]].double().cpu().numpy()
+                err_what = "rows 0 and 37 of the timed run"
+            err = dict(rel_frobenius=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                       rel_max_abs=float(np.abs(got - ref).max() / np.abs(ref).max()), sample=err_what)
+            so, occ_h, tgt_h, what = oracle_sample_system(args.workload)
+            _, sec, pairs, cores = run_oracle(so, occ_h, tgt_h, td)
+        cpu = dict(value=pairs / sec, unit="pairs/s", cores=cores, kind="oracle",
+                   sample=f"{pairs} ordered pairs ({what}), {sec:.2f} s of FP64 numpy")
+        if tio2 and not args.no_secondary:
+            secondary = pt_secondary(P, W, dev, run_oracle)
     if world > 1:
         dist.barrier()
     if rank == 0:
-        fl = flops_per_pair(n, r, T) * (N * (N + 1) // 2)
+        fl = flops_per_pair(n, r, T) * unique
         line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms_max, higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype=dtype_name(prec), data="synthetic",
-                    config=dict(WORKLOAD, orbitals=N, pairs_ordered=N * N, pairs_unique=N * (N + 1) // 2,
-                                precision=prec, l2="inputs larger than L2 (psi 226 MB, W 226 MB)",
-                                parallelism=f"replicas x{world}"),
-                    unique_pair_potentials_per_s=world * (N * (N + 1) // 2) / (ms_max / 1000.0),
+                    config=dict(cfg, occupied=n_occ, targets=n_tgt, pairs_ordered=ordered, pairs_unique=unique,
+                                precision=prec, l2=l2, parallelism=f"replicas x{world}",
+                                input_setup_s=round(setup_s, 1)),
+                    unique_pair_potentials_per_s=world * unique / (ms_max / 1000.0),
                     algorithmic_tflops=world * fl / (ms_max / 1000.0) / 1e12,
-                    err_vs_oracle=err, energy=float(e.item()),
-                    roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                    algorithmic_frac_of_peak=(world * fl / (ms_max / 1000.0) / 1e12) / roof["peak"] if roof else None,
+                    err_vs_oracle=err, roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
                     kernels={k: dict(launches=v[0], ms_total=round(v[1], 4)) for k, v in prof.items()},
-                    clocks=ck)
+                    clocks=ck, secondary=secondary)
+        if not tio2:
+            line["energy"] = float(e.item())
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def pt_secondary(P, W, dev, run_oracle_fn):
+    """The Pt-shaped block (96^3, 64 orbitals, rank 40, 40 terms; one tx_exchange_apply_energy of
+    all 64 against all 64 per step) in bf16, the split-precision tf32x3 form and the float32
+    CUDA-core form: rate and error of row 0 against the oracle."""
+    import numpy as np
+    import torch
+    s = W.config_pt()
+    psi = torch.from_numpy(s.psi).to(dev)
+    out = torch.empty_like(psi)
+    e = torch.empty((), dtype=torch.float64, device=dev)
+    with tempfile.TemporaryDirectory() as td:
+        ref, _, _, _ = run_oracle_fn(s, s.psi, s.psi[0:1], td)
+    res = {}
+    for prec, steps in (("bf16", 5), ("tf32x3", 2), ("fp32", 2)):
+        ctx = P.Context.from_system(s, precision=prec)
+        for _ in range(3):
+            P.tx_exchange_apply_energy(ctx, psi, out=out, e_out=e)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(steps):
+            P.tx_exchange_apply_energy(ctx, psi, out=out, e_out=e)
+        a1.record()
+        torch.cuda.synchronize()
+        ctx.check_device_error()
+        ms = a0.elapsed_time(a1) / steps
+        got = out[0:1].double().cpu().numpy()
+        res[prec] = dict(value=64 * 64 / (ms / 1000.0), unit="pairs/s", ms_per_step=ms, steps=steps,
+                         err_vs_oracle=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        ctx.destroy()
+    return dict(workload="Pt-cluster-shaped block", n=96, orbitals=64, rank=40, terms=40,
+                err_sample="row 0 against all 64 orbitals", results=res)
 
 
 def dtype_name(prec):
@@ -319,18 +445,17 @@ def dtype_name(prec):
 
 
 # DRAM bytes (read + write) per distinct pair of the dominant kernel, from one ncu capture of
-# the current kernel on the same block with 8 orbitals (36 pairs in one launch), scaled by the
-# pairs a bench launch processes (traffic grows in proportion to pairs).  None where no capture
-# of the current kernel exists.
-DRAM_BYTES_PER_PAIR = {("tc_consume", "bf16"): (711.658752e6 + 83.418368e6) / 36}
+# the current kernel on a smaller case of the same shape (traffic grows in proportion to the
+# pairs), scaled by the pairs a bench launch processes.  Keyed by (kernel, precision, workload);
+# None where no capture of the current kernel exists.
+DRAM_BYTES_PER_PAIR = {}
 
 
-def roofline(dom, prof, n, r, T, N, steps, prec, peaks, ck):
+def roofline(dom, prof, n, r, T, unique, steps, prec, peaks, ck, workload="pt"):
     """Achieved algorithmic FLOP/s of the dominant kernel over its live launch time."""
     if dom is None:
         return None
     k, kms = prof[dom]
-    unique = N * (N + 1) // 2
     if dom in ("consume", "tc_consume"):
         per_pair = T * 2 * (n ** 2 * r ** 2 + n ** 3 * r) + 3 * n ** 3
     elif dom in ("tc_zprod",):
@@ -353,7 +478,7 @@ def roofline(dom, prof, n, r, T, N, steps, prec, peaks, ck):
         bound = "tensor"
         src = ("measured sustained bf16" if measured else "fallback bf16") + (
             " x 0.5 (nominal tf32/bf16 ratio)" if ratio != 1.0 else "")
-    bpp = DRAM_BYTES_PER_PAIR.get((dom, prec))
+    bpp = DRAM_BYTES_PER_PAIR.get((dom, prec, workload))
     traffic = bpp * unique * steps / k if bpp else None     # bytes per launch
     return dict(kernel=dom, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                 traffic=traffic, traffic_unit="bytes per launch (ncu dram read + write, scaled)" if traffic else None,

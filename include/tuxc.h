@@ -203,11 +203,13 @@ void tx_plan_destroy(tx_plan* plan);
  * those ranges and TX_ERR_UNSUPPORTED_SHAPE if the plan does not fit SMEM / TMEM. */
 int tx_set_tile_plan(tx_ctx* ctx, int bx, int nstage);
 
-/* Split precisions (TF32x3, BF16x3): phi = sum_t mu_t G x_d A_td (final contraction of the
- * expansion) is accumulated on the tensor core in chunks of `terms` Gaussian terms, each chunk
- * folded into the outputs in float32.  The tensor core rounds its float32 accumulator at every
- * MMA, so shorter chunks give a smaller error and cost one extra fold pass per chunk.  0 restores
- * the default (5 terms).  No effect on the single-pass precisions.  TX_ERR_INVALID_ARG if < 0. */
+/* Split precisions (TF32x3, BF16x3): phi = sum_t mu_t G x_d A_td (the final contraction of the
+ * expansion, Eq. final) is accumulated on the tensor core for `terms` Gaussian terms at a time
+ * and then added into a float32 accumulator held in registers (round to nearest).  The tensor
+ * core rounds its float32 accumulator toward zero after every MMA, so the error grows with the
+ * length of each tensor-core chunk; the hi*hi and the cross products (hi*lo + lo*hi) are
+ * accumulated separately.  0 restores the default (1 term, the most accurate).  No effect on the
+ * single-pass precisions.  TX_ERR_INVALID_ARG if < 0. */
 int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
 
 /* Single-pass precisions (BF16, TF32): form of the expansion kernel (the final contraction of

@@ -67,6 +67,26 @@ __global__ void __launch_bounds__(32, 1) k_wait_selftest(int* err, int hold_tmem
     if (hold_tmem) tc::tmem_dealloc(tbase, 32);
 }
 
+// Z of the split precisions: the float32 first-mode product Zf[p][t][x][g][b] (b < r2) rounded
+// into the expansion's operand layout Z[p][t][(x, g)][ld_b] as hi + lo parts (lo after the
+// batch's hi part), with the b padding zero
+__global__ void k_split_z(const float* __restrict__ Zf, long rows, int r2, int ld_b, int tf32, void* Z, size_t lo_elems) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= rows * ld_b) return;
+    const long row = i / ld_b;
+    const int b = (int)(i - row * ld_b);
+    const float v = b < r2 ? Zf[row * r2 + b] : 0.f;
+    if (tf32) {
+        const float h = tc::tf32_hi(v);
+        ((float*)Z)[i] = h;
+        ((float*)Z)[i + lo_elems] = tc::tf32_hi(v - h);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        ((__nv_bfloat16*)Z)[i] = h;
+        ((__nv_bfloat16*)Z)[i + lo_elems] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
 }  // namespace
 
 int tc_wait_selftest(tx_ctx* c, int hold_tmem, cudaStream_t s) {
@@ -183,11 +203,48 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     return TX_OK;
 }
 
+// float32 scratch of the split precisions' projection and first expansion mode (elements per pair)
+struct SplitF32 {
+    size_t s2, g, z;
+};
+static SplitF32 split_f32(const tx_ctx* c) {
+    const size_t n1 = c->n[0], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2];
+    return SplitF32{n1 * r3 * r2, r3 * r2 * r1, (size_t)c->T * n1 * r3 * r2};
+}
+
 size_t tc_batch_bytes_per_pair(const tx_ctx* c, int kind) {
     (void)kind;
     const TcScratch sc = tc_scratch(c);
     const TcOperands* op = c->tc;
-    return (sc.s1 + sc.s2 + sc.g + sc.z) * op->esize * (op->split ? 2 : 1) + 1024;
+    if (op->split) {
+        const SplitF32 f = split_f32(c);
+        return (f.s2 + f.g + f.z) * sizeof(float) + sc.z * op->esize * 2 + 1024;
+    }
+    return (sc.s1 + sc.s2 + sc.g + sc.z) * op->esize + 1024;
+}
+
+// G[p][(g,b)][a] = sum_x S2[p][x][(g,b)] U1[x][a]  (float32, mode 1 of the projection)
+static int f32_mode1_project(const tx_ctx* c, const float* S2, float* G, int np, cudaStream_t s) {
+    const int n1 = c->n[0], r1 = c->r[0], rr = c->r[1] * c->r[2];
+    GemmArgs g{};
+    g.M = rr; g.N = r1; g.K = n1;
+    g.A = S2; g.a_m = 1; g.a_k = rr; g.a_b2 = (long)n1 * rr;
+    g.B = c->f_U[0]; g.b_k = r1; g.b_n = 1;
+    g.C = G; g.c_m = r1; g.c_n = 1; g.c_b2 = (long)rr * r1;
+    g.nb1 = 1; g.nb2 = np; g.alpha = 1.f;
+    return simt_gemm(g, s);
+}
+
+// Zf[p][t][x][(g,b)] = sum_a A_t1[x][a] G[p][(g,b)][a]  (float32, mode 1 of the expansion, every term)
+static int f32_mode1_expand(const tx_ctx* c, const float* G, float* Z, int np, cudaStream_t s) {
+    const int n1 = c->n[0], r1 = c->r[0], rr = c->r[1] * c->r[2], T = c->T;
+    GemmArgs g{};
+    g.M = n1; g.N = rr; g.K = r1;
+    g.A = c->f_A[0]; g.a_m = r1; g.a_k = 1; g.a_b1 = (long)n1 * r1;
+    g.B = G; g.b_k = 1; g.b_n = r1; g.b_b2 = (long)rr * r1;
+    g.C = Z; g.c_m = rr; g.c_n = 1; g.c_b1 = (long)n1 * rr; g.c_b2 = (long)T * n1 * rr;
+    g.nb1 = T; g.nb2 = np; g.alpha = 1.f;
+    return simt_gemm(g, s);
 }
 
 long tc_epart_per_pair(const tx_ctx* c) { return tc_consume_blocks(c); }
@@ -200,14 +257,49 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
     const int np = b.np;
     const int eb = op->esize, mult = op->split ? 2 : 1;
     const int n1 = c->n[0], n2 = c->n[1], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2], T = c->T;
+    const bool subset = cs.mode == PAIRS_SUBSET;
+    const float* SA = subset ? cs.occ : cs.tgt;
+    const int nA = subset ? cs.n_occ : cs.n_tgt;
+    int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
+    if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
+    // OUT rows: the call's targets (apply only; the energy call writes no W)
+    const int nout = cs.out0 ? cs.n_tgt : 0;
+    const OrbCounts cnt{nA, cs.n_occ, cs.n_occ, cs.n_occ, nout, nout};
+    if (op->split) {
+        // Split precisions: the projection onto the core and the first expansion mode run in
+        // float32 on the CUDA cores (13% of the flops on the Pt-shaped block), so that the core
+        // and Z carry full float32 precision into the hi + lo split; modes 2 and 3 and the sum
+        // over terms run on the tensor cores (tc_consume).
+        const SplitF32 f = split_f32(c);
+        float* S2f = (float*)b.scratch;
+        float* Gf = S2f + (size_t)np * f.s2;
+        float* Zf = Gf + (size_t)np * f.g;
+        char* Z = (char*)(Zf + (size_t)np * f.z);
+        Z = (char*)(((uintptr_t)Z + 255) & ~(uintptr_t)255);
+        FieldArgs fa{};
+        fa.SA = SA;
+        fa.SB = cs.occ;
+        TX_TRY(simt_project_s2(c, b.recs, b.p0, np, fa, 0, S2f, s));
+        TX_TRY(f32_mode1_project(c, S2f, Gf, np, s));
+        TX_TRY(f32_mode1_expand(c, Gf, Zf, np, s));
+        const long rows = (long)np * T * n1 * r3;
+        const long nz = rows * sc.ld_b;
+        k_split_z<<<(unsigned)((nz + 255) / 256), 256, 0, s>>>(Zf, rows, r2, sc.ld_b, op->tf32 ? 1 : 0, Z,
+                                                              (size_t)np * sc.z);
+        TX_LAUNCHED();
+        TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, b.epart, s,
+                          subset));
+        (void)r1;
+        (void)n2;
+        (void)mult;
+        (void)eb;
+        return TX_OK;
+    }
     char* S1 = b.scratch;
     char* S2 = S1 + (size_t)np * sc.s1 * eb * mult;
     char* G = S2 + (size_t)np * sc.s2 * eb * mult;
     char* Z = G + (size_t)np * sc.g * eb * mult;
-    const int out_type = op->tf32 ? (op->split ? TC_OUT_F32_SPLIT : TC_OUT_F32) : (op->split ? TC_OUT_BF16_SPLIT : TC_OUT_BF16);
-    const bool subset = cs.mode == PAIRS_SUBSET;
-    const float* SA = subset ? cs.occ : cs.tgt;
-    const int nA = subset ? cs.n_occ : cs.n_tgt;
+    const int out_type = op->tf32 ? TC_OUT_F32 : TC_OUT_BF16;
     auto lo_of = [&](const void* hi, size_t per_pair) -> const void* {
         return op->split ? (const char*)hi + (size_t)np * per_pair * eb : nullptr;
     };
@@ -255,12 +347,7 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
         TX_TRY(tc_rows_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
     }
     // 5. modes 2 and 3 for every term, phi accumulated in TMEM, Hadamard / energy epilogue
-    int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
-    if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
-    // symmetric pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers
-    // OUT rows: the call's targets (apply only; the energy call writes no W)
-    const int nout = cs.out0 ? cs.n_tgt : 0;
-    const OrbCounts cnt{nA, cs.n_occ, cs.n_occ, cs.n_occ, nout, nout};
+    // (symmetric pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers)
     TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, b.epart, s,
                       subset));
     (void)r1;

@@ -73,6 +73,7 @@ struct ConsumeArgs {
     int zone;                  // 1: the slab's Z planes load as one box (gs == r3, bx * r3 <= 256 rows)
     // persistent single-pass kernel: work items (pair, slab), slabs per pair, epilogue region
     int nitems, nslab;
+    int nyi;                   // persistent kernel: work items per slab (1, or one per y tile of 128 rows)
     uint32_t epi_off;
 };
 
@@ -364,64 +365,44 @@ __device__ __forceinline__ double consume_epilogue_tma(const ConsumeArgs& a, con
     return e;
 }
 
-// Fold of phi into the outputs and the energy sum without shared memory (the pipeline
-// buffers are still in use): each thread takes its TMEM lane, i.e. one grid row (x, y), and
-// 16 z columns per load; the two warps of a lane quadrant take alternate column blocks.
-template <typename Rows>
-__device__ __forceinline__ double consume_fold_direct(const ConsumeArgs& a, const PairRec& rec, uint32_t tPhi,
-                                                      int nTiles, int warp, int lane, Rows rows) {
-    const int q = warp & 3, h = warp >> 2;
-    const long N3 = (long)a.n1 * a.n2 * a.n3;
-    const float* mul0 = a.MUL0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
-    const float* mul1 = a.MUL1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
-    float* out0 = (a.OUT0 && rec.o0 >= 0) ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
-    float* out1 = (a.OUT1 && rec.o1 >= 0) ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
-    const float* sa = a.SA + (long)rec.ia * N3;
-    const float* sb = a.SB + (long)rec.ib * N3;
-    const bool en = (a.flags & EPI_ENERGY) != 0;
-    const bool o0 = (a.flags & EPI_OUT) && out0, o1 = (a.flags & EPI_OUT) && out1;
-    double e = 0.0;
-    for (int jt = 0; jt < nTiles; ++jt) {
-        int x = 0, y = 0;
-        const bool in = rows(jt, q * 32 + lane, x, y);
-        const float wxy = in ? a.w1[x] * a.w2[y] : 0.f;
-        const int rowbase = in ? (x * a.n2 + y) * a.n3 : 0;
-        for (int c = h; c < a.n3p / 16; c += 2) {
-            uint32_t r[16];
-            tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + 16 * c), r);
-            tmem_ld_wait();
-            if (!in) continue;
-            float eb = 0.f;
+// Split precisions: phi of one accumulation chunk (main = hi*hi products, cross = hi*lo + lo*hi
+// products, each in its own TMEM columns) is added in float32 into this thread's share of the
+// register accumulator `mst`.  Thread (quadrant q, half h) owns TMEM lanes 32q..32q+31 and the
+// 16-column groups g = h, h + 2, ... of the nT3 * n3p concatenated phi columns (group g, local
+// index g / 2, values mst[16 * (g / 2) + j]).
+template <int MG>
+__device__ __forceinline__ void fold_chunk(uint32_t tPhi, uint32_t tPhiC, int q, int h, int ngroups, float (&mst)[MG * 16]) {
 #pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-                const int z = 16 * c + j;
-                if (z >= a.n3) break;                   // n3 % 4 == 0
-                const int idx = rowbase + z;
-                const float4 phi = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                const float4 w3 = *(const float4*)(a.w3 + z);
-                const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
-                float4 f = phi;
-                if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
-                if (o0) {
-                    const float4 m0 = __ldg((const float4*)(mul0 + idx));
-                    atomicAdd((float4*)(out0 + idx), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
-                }
-                if (o1) {
-                    const float4 m1 = __ldg((const float4*)(mul1 + idx));
-                    atomicAdd((float4*)(out1 + idx), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
-                }
-                if (en) {
-                    const float4 va = __ldg((const float4*)(sa + idx)), vb = __ldg((const float4*)(sb + idx));
-                    eb += wv.x * va.x * vb.x * phi.x + wv.y * va.y * vb.y * phi.y + wv.z * va.z * vb.z * phi.z +
-                          wv.w * va.w * vb.w * phi.w;
-                }
-            }
-            e += (double)eb;     // float32 within a 16-column block, float64 across blocks
-        }
+    for (int gi = 0; gi < MG; ++gi) {
+        const int g = h + 2 * gi;
+        if (g >= ngroups) break;
+        uint32_t rm[16], rc[16];
+        const uint32_t off = ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * g);
+        tmem_ld16(tPhi + off, rm);
+        tmem_ld16(tPhiC + off, rc);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mst[16 * gi + j] += __uint_as_float(rm[j]) + __uint_as_float(rc[j]);
     }
-    return e;
 }
+// ... and written back into the main phi columns for the epilogue
+template <int MG>
+__device__ __forceinline__ void store_master(uint32_t tPhi, int q, int h, int ngroups, const float (&mst)[MG * 16]) {
+#pragma unroll
+    for (int gi = 0; gi < MG; ++gi) {
+        const int g = h + 2 * gi;
+        if (g >= ngroups) break;
+        uint32_t r[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(mst[16 * gi + j]);
+        tmem_st16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * g), r);
+    }
+    tmem_st_wait();
+}
+
+// Register share of the split precisions' phi accumulator: at most 4 groups of 16 columns per
+// thread, i.e. nT3 * n3p <= 128 (the plan enforces it)
+constexpr int kMasterGroups = 4;
 
 template <bool TF32, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -442,14 +423,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
     const int NL = a.nload, NA = a.na3, BX = a.bx;
-    // phi is accumulated in TMEM over chunks of C terms and folded into the outputs after each
-    // chunk: the tensor core rounds its float32 accumulator at every MMA, and restarting it
-    // bounds that error by the chunk length (the folds add in float32, rounding to nearest)
-    const int C = a.chunk > 0 ? a.chunk : a.nt;
-    // Gaussian terms in the order of the exponential sum (theta ascending: wide terms first).
-    // Measured against the float64 oracle, this order gives about half the split-precision
-    // error of the reverse order: the tensor core's float32 accumulator rounds each partial
-    // sum, and starting from the large, smooth wide-term part keeps later steps small.
+    // Split precisions: the tensor core rounds its float32 accumulator after every MMA, toward
+    // zero, so the error of a long accumulation grows with its length.  The hi*hi products and
+    // the cross products (hi*lo + lo*hi, 2^-11 smaller) go to separate accumulators, and phi is
+    // accumulated on the tensor core over chunks of C terms only (default 1): after each chunk
+    // the converter warps add both accumulators into a float32 register accumulator (round to
+    // nearest) and the tensor core restarts.  Single-pass precisions accumulate every term.
+    const int C = SPLIT ? (a.chunk > 0 ? a.chunk : 1) : a.nt;
+    // Gaussian terms in the order of the exponential sum (theta ascending: wide terms first)
     auto term_of = [&](int t) { return t; };
 
     // load stage s: [A_t2 tile][Z tile][A_t3 tile], each hi then lo; then the NA stage-3 operands
@@ -489,7 +470,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t tY = tmem, tPhi = tmem + a.y_cols;
+    // TMEM: [Y][phi] for the single-pass precisions; [Y][Y cross][phi][phi cross] for the split ones
+    const uint32_t phi_cols = (uint32_t)(a.nT3 * a.n3p);
+    const uint32_t tY = tmem, tYc = tmem + a.y_cols;
+    const uint32_t tPhi = tmem + (SPLIT ? 2u : 1u) * a.y_cols, tPhiC = tPhi + phi_cols;
     const uint32_t ya_sub = a.ya_rows * 32u;                  // one K-step sub-tile of each operand
     const uint32_t z_sub = a.z_rows * 32u;
     const uint32_t a3_sub = (uint32_t)a.nT3 * 128u * 32u;
@@ -537,13 +521,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
             const uint32_t id3 = TF32 ? idesc_tf32(128, a.n3p) : idesc_bf16(128, a.n3p);
-            // Event-driven issue: stage 2 of (term t2, plane p2) as soon as its load stage has
-            // landed and the converters have released the plane's TMEM columns; stage 3 of term
-            // t3 as soon as its operand is converted.  Neither waits for the other, so a load
-            // stage is released (by stage 3) without waiting for the next stage's data.
-            // all planes of a term in one MMA per K step (N = planes x Nz, in chunks of <= 256).
-            // Descriptors are built once and advanced by adds, so that issuing an MMA costs less
-            // than the ~50 cycles it occupies the tensor pipe.
+            // Event-driven issue: stage 2 of term t2 as soon as its load stage has landed and the
+            // converters have released Y; stage 3 of term t3 as soon as its operand is converted
+            // (and, at the start of an accumulation chunk, the previous chunk has been folded).
+            // All planes of a term go in one MMA per K step (N = planes x Nz, in chunks of <= 256).
+            // Descriptors are built once and advanced by adds.
             const uint64_t d0 = sdesc_sw32(0);
             const uint64_t ya_step = ya_sub >> 4, z_step = z_sub >> 4, b3_step = (uint32_t)a.n3p * 2u;
             const uint64_t a3_step = a3_sub >> 4, ya_lo = a.ya_bytes >> 4, z_lo = a.z_bytes >> 4;
@@ -555,13 +537,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int p0 = 0; p0 < BX; p0 += a.npc) {
                         const int N = min(a.npc, BX - p0) * a.Nz;
                         const uint32_t id2 = TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
-                        const uint32_t d = tY + (uint32_t)((i * BX + p0) * a.Nz);
+                        const uint32_t col = (uint32_t)((i * BX + p0) * a.Nz);
                         uint64_t ad = ya + (uint32_t)i * 256u, bd = zb + (uint32_t)(p0 * a.Nz) * 2u;
                         for (int k = 0; k < a.ks2; ++k) {
-                            mma_ss<TF32>(d, ad, bd, id2, k > 0 ? 1u : 0u);
+                            mma_ss<TF32>(tY + col, ad, bd, id2, k > 0 ? 1u : 0u);
                             if constexpr (SPLIT) {
-                                mma_ss<TF32>(d, ad, bd + z_lo, id2, 1u);
-                                mma_ss<TF32>(d, ad + ya_lo, bd, id2, 1u);
+                                mma_ss<TF32>(tYc + col, ad, bd + z_lo, id2, k > 0 ? 1u : 0u);
+                                mma_ss<TF32>(tYc + col, ad + ya_lo, bd, id2, 1u);
                             }
                             ad += ya_step;
                             bd += z_step;
@@ -572,13 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             auto stage3 = [&](int t) {
                 const int s = t % NL, b = t % NA;
                 const uint64_t a3 = d0 + (smem_u32(A3s(b)) >> 4), b3 = d0 + (smem_u32(B3s(s)) >> 4);
+                const bool first = (t % C) == 0;
                 for (int j = 0; j < a.nT3; ++j) {
                     uint64_t ad = a3 + (uint32_t)j * 256u, bd = b3;
                     for (int k = 0; k < a.ks3; ++k) {
-                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, (t % C > 0 || k > 0) ? 1u : 0u);
+                        const uint32_t acc = (!first || k > 0) ? 1u : 0u;
+                        mma_ss<TF32>(tPhi + j * a.n3p, ad, bd, id3, acc);
                         if constexpr (SPLIT) {
-                            mma_ss<TF32>(tPhi + j * a.n3p, ad, bd + b3_lo, id3, 1u);
-                            mma_ss<TF32>(tPhi + j * a.n3p, ad + a3_lo, bd, id3, 1u);
+                            mma_ss<TF32>(tPhiC + j * a.n3p, ad, bd + b3_lo, id3, acc);
+                            mma_ss<TF32>(tPhiC + j * a.n3p, ad + a3_lo, bd, id3, 1u);
                         }
                         ad += a3_step;
                         bd += b3_step;
@@ -605,7 +589,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     (t3 % C != 0 || t3 == 0 || mbar_try_wait(&phifree, (t3 / C - 1) & 1))) {
                     tc_fence_after();
                     stage3(t3);
-                    if ((t3 + 1) % C == 0 && t3 + 1 < a.nt) mma_commit(&chunkdone);
+                    if constexpr (SPLIT)
+                        if ((t3 + 1) % C == 0 || t3 + 1 == a.nt) mma_commit(&chunkdone);
                     ++t3;
                     prog = true;
                 }
@@ -644,6 +629,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             x = x0 + xl;
             return m3 < a.R && x < a.n1;
         };
+        const int ngroups = (int)phi_cols / 16;
+        float mst[kMasterGroups * 16];
+#pragma unroll
+        for (int j = 0; j < kMasterGroups * 16; ++j) mst[j] = 0.f;
         for (int t = 0; t < a.nt && ok; ++t) {
             const int b = t % NA;
             if (t >= NA && !mbar_wait(&a3free[b], ((t - NA) / NA) & 1, a.err, 36)) { ok = false; break; }
@@ -664,6 +653,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int c = 0; c < 4; ++c)
                                 if (c < nck) tmem_ld16(col + g0 + 16 * c, r[c]);
                             tmem_ld_wait();
+                            if constexpr (SPLIT) {
+                                // Y = main + cross accumulator
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if (c < nck) {
+                                        uint32_t rc[16];
+                                        tmem_ld16(col + a.y_cols + g0 + 16 * c, rc);
+                                        tmem_ld_wait();
+#pragma unroll
+                                        for (int j = 0; j < 16; ++j)
+                                            r[c][j] = __float_as_uint(__uint_as_float(r[c][j]) + __uint_as_float(rc[j]));
+                                    }
+                            }
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 if (c >= nck) break;
@@ -693,20 +695,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&a3full[b]);
-            // end of an accumulation chunk: fold phi into the outputs, then free the accumulator
-            if ((t + 1) % C == 0 && t + 1 < a.nt) {
-                if (!mbar_wait(&chunkdone, (t / C) & 1, a.err, 38)) { ok = false; break; }
-                tc_fence_after();
-                e += consume_fold_direct(a, rec, tPhi, a.nT3, warp, lane, rows_of);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&phifree);
+            if constexpr (SPLIT) {
+                // end of an accumulation chunk: fold phi into the register accumulator and let
+                // the tensor core restart
+                if ((t + 1) % C == 0 || t + 1 == a.nt) {
+                    if (!mbar_wait(&chunkdone, (t / C) & 1, a.err, 38)) { ok = false; break; }
+                    tc_fence_after();
+                    fold_chunk<kMasterGroups>(tPhi, tPhiC, q, h, ngroups, mst);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&phifree);
+                }
             }
         }
         // ------------------------------ epilogue ------------------------------
         if (ok && mbar_wait_idle(&phidone, 0, a.err, 37) && *(volatile int*)a.err == 0) {
             tc_fence_after();
+            if constexpr (SPLIT) {
+                // the register accumulator goes back into the main phi columns for the epilogue,
+                // which every converter warp reads for its whole lane quadrant
+                store_master<kMasterGroups>(tPhi, q, h, ngroups, mst);
+                tc_fence_before();
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            tc_fence_after();
             e += consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, rows_of);
+        } else {
+            asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight warps meet here on every path
         }
         if (a.flags & EPI_ENERGY) {
             for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -1063,10 +1078,15 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NL = a.nload, NL3 = a.nload3, NYB = a.nyb, BX = a.bx, NT = a.nt;
     const int nmine = (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto item_of = [&](int k, int& pl, int& slab) {
+    // item it = ((pair * nslab) + slab) * nyi + iy: with nyi > 1 an item covers one 128-row y
+    // tile (iy) of its slab's planes (a.nY is then 1), so that phi and the Y buffers of grids
+    // with more than 128 rows per plane fit TMEM
+    auto item_of = [&](int k, int& pl, int& slab, int& iy) {
         const int it = (int)blockIdx.x + k * (int)gridDim.x;
-        pl = it / a.nslab;
-        slab = it - pl * a.nslab;
+        const int ps = it / a.nyi;
+        iy = it - ps * a.nyi;
+        pl = ps / a.nslab;
+        slab = ps - pl * a.nslab;
     };
     auto YAs = [&](int s) { return smem + s * a.load_bytes; };
     auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
@@ -1115,8 +1135,8 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         uint32_t ph = 0;
         bool ok = true;
         for (int k = 0; k < nmine && ok; ++k) {
-            int pl, slab;
-            item_of(k, pl, slab);
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
             const int x0 = slab * BX;
             for (int t = 0; t < NT; ++t) {
                 ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[s], ph ^ 1, a.err, 41));
@@ -1147,8 +1167,8 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         auto prefetch = [&](int g) {
             const int k = g / NT, t = g - k * NT;
             if (k >= nmine) return;
-            int pl, slab;
-            item_of(k, pl, slab);
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
             const int x0 = slab * BX;
             const int np_ = min(BX, a.n1 - x0);
             bulk_prefetch_l2_w(a.zsrc + ((size_t)pl * NT * a.n1 + x0) * a.z_plane + (size_t)t * zterm,
@@ -1179,7 +1199,9 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         int s = 0, yb = 0, g = 0;
         uint32_t ph = 0, yph = 0;
         bool ok = true;
-        for (int k = 0; k < nmine && ok; ++k)
+        for (int k = 0; k < nmine && ok; ++k) {
+            int pl_, slab_, iy;
+            item_of(k, pl_, slab_, iy);
             for (int t = 0; t < NT; ++t, ++g) {
                 bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
                 // Y buffer yb was last read by stage 3 of term g - nyb
@@ -1187,7 +1209,8 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 ok = __all_sync(0xffffffffu, w);
                 if (!ok) break;
                 tc_fence_after();
-                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4), zb = d0 + (smem_u32(Zs(s)) >> 4);
+                // the item's first y tile: rows iy * 128 of the A_t2 tile (1024 descriptor units)
+                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4) + (uint32_t)iy * 1024u, zb = d0 + (smem_u32(Zs(s)) >> 4);
                 const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
                 s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
                 if (more2)
@@ -1204,6 +1227,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 if (++s == NL) { s = 0; ph ^= 1; }
                 if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
+        }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s3fin[0]);
         mbar_drain(&s3fin[0], 0, a.err);
@@ -1241,8 +1265,15 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         mma_commit_w(&s3fin[1]);
         mbar_drain(&s3fin[1], 0, a.err);
     } else {
-        // ---------------- epilogue warps 0-7: one tile (plane / y tile) per warp ----------------
-        const int q = warp & 3, jt = warp >> 2;
+        // ---------------- epilogue warps 0-7 ----------------
+        // With two tiles per item, warp (q, h) takes tile h; with one tile, the two warps of a
+        // lane quadrant split its 32-column chunks (h, h + 2, ...).  Either way a lane holds at
+        // most kTpMaxZ columns of its row.
+        const int q = warp & 3, h = warp >> 2;
+        const bool csplit = a.nT3 == 1;
+        const int jt = csplit ? 0 : h;
+        const int cbase = csplit ? h : 0, cstep = csplit ? 2 : 1;
+        auto chunk_of = [&](int j) { return cbase + cstep * j; };   // global 32-column chunk
         uint8_t* b0 = smem + a.epi_off + warp * 2 * kEpiBox;
         uint8_t* b1 = b0 + kEpiBox;
         uint32_t eph = 0;
@@ -1251,26 +1282,29 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             // barrier below once per item, so none of them is left waiting there
             const bool live = mbar_wait_idle(&phidone, (uint32_t)(k & 1), a.err, 45);
             tc_fence_after();
-            int pl, slab;
-            item_of(k, pl, slab);
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
             const int x0 = slab * BX;
             const PairRec rec = a.recs[a.p0 + pl];
-            // phi of this lane's row of tile jt, into registers; then release the accumulator
+            // phi of this lane's row of tile jt (its chunks), into registers; then release the
+            // accumulator
             uint32_t phr[kTpMaxZ];
             const bool has = live && jt < a.nT3;
             if (has) {
 #pragma unroll
-                for (int c = 0; c < kTpMaxZ / 16; ++c)
-                    if (16 * c < a.n3p)
-                        tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + 16 * c),
+                for (int c = 0; c < kTpMaxZ / 16; ++c) {
+                    const int col = 32 * chunk_of(c >> 1) + 16 * (c & 1);
+                    if (col < a.n3p)
+                        tmem_ld16(tPhi + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * a.n3p + col),
                                   *(uint32_t(*)[16]) & phr[16 * c]);
+                }
                 tmem_ld_wait();
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&phifree);
             double e = 0.0;
-            const int p = jt / a.nY, x = x0 + p, y0 = (jt - p * a.nY) * 128 + q * 32;
+            const int p = jt / a.nY, x = x0 + p, y0 = (iy + jt - p * a.nY) * 128 + q * 32;
             const bool en = (a.flags & EPI_ENERGY) != 0;
             const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0;
             const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
@@ -1284,7 +1318,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 uint8_t* s1 = need0 ? b1 : b0;
 #pragma unroll
                 for (int ch = 0; ch < kTpMaxZ / 32; ++ch) {
-                    const int zc = 32 * ch;
+                    const int zc = 32 * chunk_of(ch);
                     if (zc >= a.n3) break;
                     if (lane == 0) {
                         mbar_arrive_expect_tx(&ebar[warp], (uint32_t)nbx * kEpiBox);
@@ -1299,8 +1333,8 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                     for (int c = 0; c < 8; ++c) {
                         const int z = zc + 4 * c;
                         const uint32_t off = (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4);
-                        float4 phi = make_float4(__uint_as_float(phr[zc + 4 * c]), __uint_as_float(phr[zc + 4 * c + 1]),
-                                                 __uint_as_float(phr[zc + 4 * c + 2]), __uint_as_float(phr[zc + 4 * c + 3]));
+                        float4 phi = make_float4(__uint_as_float(phr[32 * ch + 4 * c]), __uint_as_float(phr[32 * ch + 4 * c + 1]),
+                                                 __uint_as_float(phr[32 * ch + 4 * c + 2]), __uint_as_float(phr[32 * ch + 4 * c + 3]));
                         if (z >= a.n3p) phi = make_float4(0.f, 0.f, 0.f, 0.f);     // registers past the tile
                         const float4 w3 = (rowin && z < a.n3) ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
                         const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
@@ -1338,7 +1372,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             if ((a.flags & EPI_ENERGY) && warp == 0 && lane == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < 8; ++w) sum += red[k & 1][w];
-                a.epart[(long)pl * a.nslab + slab] = sum;
+                a.epart[((long)pl * a.nslab + slab) * a.nyi + iy] = sum;
             }
         }
         if (lane == 0) bulk_wait_all();
@@ -1398,11 +1432,11 @@ __global__ void __launch_bounds__(32, 1)
 // ======================================================================================
 // host side: tile plan and launch
 // ======================================================================================
-// Gaussian terms per phi accumulation chunk of the split precisions (see k_consume)
-constexpr int kDefaultSplitChunk = 5;
 
 struct ConsumePlan {
     bool ts;                 // single-pass kernel (stage 3 from TMEM) instead of the converter kernel
+    bool ysplit;             // single-pass, persistent only: one work item per 128-row y tile
+    int nyi;                 // work items per slab (nY with ysplit, else 1)
     int bx, nY, Nz, npc, nT3, n2p, n3p, ks2, ks3, nq, nload, na3, nyb, gs, ycol_tile;
     uint32_t ya_rows, z_rows, ya, zb, b3, a3, load, a3_off, tmem_cols, y_cols;
     int nload3;              // single-pass: stages of the stage-3 (mu_t A_t3) ring
@@ -1410,8 +1444,10 @@ struct ConsumePlan {
     size_t smem;
 };
 
-// Single-pass plan: bx planes, nload load stages and as many stage-2 output buffers in TMEM
-static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* p) {
+// Single-pass plan: bx planes, nload load stages and as many stage-2 output buffers in TMEM.
+// With ysplit every work item covers one 128-row y tile of its planes (persistent kernel only),
+// so that phi and the stage-2 buffers of planes with more than 128 rows fit TMEM.
+static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* p, bool ysplit = false) {
     const int MK2 = tf32 ? 8 : 16;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
     if (bx < 1 || bx > n1 || bx > tcc::kMaxPlanes || nload < 2 || nload > tcc::kMaxLoad) return false;
@@ -1423,6 +1459,13 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->gs = pad8(r3);                          // TMEM columns (and Z tile rows) per plane
     if (p->n2p > 256 || p->n3p > 256 || p->gs > 256) return false;
     p->nY = (n2 + 127) / 128;
+    p->nyi = 1;
+    if (ysplit) {
+        if (p->nY < 2 || bx > 2) return false;
+        p->ysplit = true;
+        p->nyi = p->nY;
+        p->nY = 1;
+    }
     p->npc = std::min(bx, 256 / p->gs);
     p->ks2 = (r2 + MK2 - 1) / MK2;
     p->ks3 = (r3 + 7) / 8;
@@ -1456,6 +1499,14 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->load3 = (p->b3 + 1023) & ~1023u;
     p->nload = nload;
     p->a3_off = p->load * (uint32_t)nload;
+    // y-tile items run in the persistent kernel only: its smallest split (two stages of each
+    // ring and the epilogue boxes) must fit, and an epilogue lane must hold its share of a phi
+    // row (the whole row with two tiles per item, every other 32-column chunk with one)
+    if (ysplit) {
+        if (2 * (size_t)p->load + 2 * (size_t)p->load3 + tcc::kTpEpiBytes + 1024 > 226 * 1024) return false;
+        const int lane_cols = p->nT3 == 1 ? 32 * (((p->n3p + 31) / 32 + 1) / 2) : p->n3p;
+        if (p->nT3 > 2 || lane_cols > tcc::kTpMaxZ || p->nyb < 2) return false;
+    }
     for (p->nload3 = tcc::kMaxLoad; p->nload3 >= 2; --p->nload3) {
         p->smem = std::max((size_t)p->a3_off + (size_t)p->load3 * p->nload3 + 16384, (size_t)tcc::kEpiBytes) + 1024;
         if (p->smem <= 226 * 1024) return true;
@@ -1473,16 +1524,22 @@ static double ts_cost(const ConsumePlan& p) {
 
 static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p);
 
-// single-pass shapes that fit no TMEM plan (large n with large r) use the converter kernel
-static bool ts_possible(const tx_ctx* c, bool tf32) {
+// single-pass shapes whose planes fit no TMEM plan (large n with large r) take one work item per
+// y tile in the persistent kernel (unless the one-CTA-per-item form is forced); failing that,
+// the converter kernel
+static bool ts_fits(const tx_ctx* c, bool tf32, bool ysplit) {
     ConsumePlan p;
     for (int nl = 2; nl <= tcc::kMaxLoad; ++nl)
-        if (plan_ts(c, tf32, 1, nl, &p)) return true;
+        if (plan_ts(c, tf32, 1, nl, &p, ysplit)) return true;
     return false;
 }
+static bool ts_ysplit(const tx_ctx* c, bool tf32) {
+    return !ts_fits(c, tf32, false) && c->consume_form != 1 && ts_fits(c, tf32, true);
+}
+static bool ts_possible(const tx_ctx* c, bool tf32) { return ts_fits(c, tf32, false) || ts_ysplit(c, tf32); }
 
 static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p) {
-    if (!split && ts_possible(c, tf32)) return plan_ts(c, tf32, bx, nload, p);
+    if (!split && ts_possible(c, tf32)) return plan_ts(c, tf32, bx, nload, p, ts_ysplit(c, tf32));
     return plan_cv(c, tf32, split, bx, nload, na3, p);
 }
 
@@ -1505,8 +1562,11 @@ static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, i
     p->ks2 = (r2 + MK - 1) / MK;
     p->ks3 = (r3 + MK - 1) / MK;
     p->y_cols = (uint32_t)(bx * p->nY * p->Nz);
-    const uint32_t cols = p->y_cols + (uint32_t)(p->nT3 * p->n3p);
+    // split precisions keep the cross products in accumulators of their own (twice the columns)
+    const uint32_t cols = (split ? 2u : 1u) * (p->y_cols + (uint32_t)(p->nT3 * p->n3p));
     if (cols > 512) return false;
+    // ... and fold phi into registers: kMasterGroups x 16 columns per converter thread
+    if (split && p->nT3 * p->n3p > 2 * 16 * tcc::kMasterGroups) return false;
     p->tmem_cols = 32;
     while (p->tmem_cols < cols) p->tmem_cols <<= 1;
     const int m = split ? 2 : 1;
@@ -1533,11 +1593,12 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
     }
     double best_score = -1;
     if (!split && ts_possible(c, tf32)) {
+        const bool ysplit = ts_ysplit(c, tf32);
         // least tensor-pipe time per plane and term, then the deepest load pipeline
         for (int nl = tcc::kMaxLoad; nl >= 2; --nl)
             for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx) {
                 ConsumePlan p;
-                if (!plan_ts(c, tf32, bx, nl, &p)) continue;
+                if (!plan_ts(c, tf32, bx, nl, &p, ysplit)) continue;
                 const double score = 1.0 / ts_cost(p) * (0.8 + 0.05 * nl);
                 if (score > best_score * 1.0001) {
                     best_score = score;
@@ -1608,7 +1669,7 @@ long tc_consume_blocks(const tx_ctx* c) {
     ConsumePlan p;
     const TcOperands* op = c->tc;
     if (!op || !choose_plan(c, op->tf32, op->split, &p)) return 1;
-    return (c->n[0] + p.bx - 1) / p.bx;
+    return (long)((c->n[0] + p.bx - 1) / p.bx) * (p.ts ? p.nyi : 1);
 }
 
 // Persistent form of the single-pass kernel (the epilogue of one item overlaps the main loop of
@@ -1624,14 +1685,21 @@ struct TpSplit {
 
 static TpSplit tp_split(const tx_ctx* c, const ConsumePlan& p, bool energy, bool emul) {
     TpSplit t{};
-    t.on = p.ts && c->consume_form != 1 && p.nT3 <= 2 && p.bx <= 2 && p.n3p <= tcc::kTpMaxZ && p.nyb >= 2 &&
-           (!energy || emul);
+    // columns of one phi row an epilogue lane holds: the whole row with two tiles per item, every
+    // other 32-column chunk with one
+    const int lane_cols = p.nT3 == 1 ? 32 * (((p.n3p + 31) / 32 + 1) / 2) : p.n3p;
+    t.on = p.ts && (c->consume_form != 1 || p.ysplit) && p.nT3 <= 2 && p.bx <= 2 && lane_cols <= tcc::kTpMaxZ &&
+           p.nyb >= 2 && (!energy || emul);
     if (!t.on) return t;
-    t.nl1 = std::min(p.nload, 4);
-    t.a3_off = p.load * (uint32_t)t.nl1;
-    int nl3 = tcc::kMaxLoad;
-    while (nl3 >= 2 && (size_t)t.a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 > 226 * 1024) --nl3;
-    if (nl3 < 2) {
+    // a stage-2 ring of at most four stages, shallower where the stage-3 ring needs the room
+    int nl3 = 1;
+    for (t.nl1 = std::min(p.nload, 4); t.nl1 >= 2; --t.nl1) {
+        t.a3_off = p.load * (uint32_t)t.nl1;
+        for (nl3 = tcc::kMaxLoad; nl3 >= 2; --nl3)
+            if ((size_t)t.a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 <= 226 * 1024) break;
+        if (nl3 >= 2) break;
+    }
+    if (t.nl1 < 2 || nl3 < 2) {
         t.on = false;
         return t;
     }
@@ -1659,7 +1727,7 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
                        p.ks2,
                        p.ks3,
                        p.n3p,
-                       (c->n[0] + p.bx - 1) / p.bx};
+                       (c->n[0] + p.bx - 1) / p.bx * (p.ts ? p.nyi : 1)};
     for (int i = 0; i < nout && i < 12; ++i) out[i] = v[i];
     return TX_OK;
 }
@@ -1673,8 +1741,9 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
     }
     ConsumePlan p;
     if (op->split || !ts_possible(c, op->tf32)) return TX_OK;
+    const bool ysplit = ts_ysplit(c, op->tf32);
     for (int nl = 2; nl <= tcc::kMaxLoad; ++nl)
-        if (plan_ts(c, op->tf32, 1, nl, &p)) break;
+        if (plan_ts(c, op->tf32, 1, nl, &p, ysplit)) break;
     // the tile shapes below depend on (n, r, precision) only, not on the slab or the stages
     const int n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T, eb = op->esize;
     op->img_stride = p.ya + p.b3;
@@ -1736,7 +1805,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     a.SA = SA; a.SB = SB; a.MUL0 = MUL0; a.MUL1 = MUL1; a.OUT0 = OUT0; a.OUT1 = OUT1;
     a.w1 = c->f_w[0]; a.w2 = c->f_w[1]; a.w3 = c->f_w[2];
     a.flags = flags; a.epart = epart; a.err = c->d_err;
-    a.chunk = c->acc_chunk > 0 ? c->acc_chunk : (op->split ? kDefaultSplitChunk : T);
+    a.chunk = c->acc_chunk;     // split precisions: terms per tensor-core accumulation chunk (0: 1)
     a.emul = (SA == MUL1 && SB == MUL0 && emul) ? 1 : 0;
     const int eb = op->esize;
     const uint32_t MK = op->tf32 ? 8 : 16;
@@ -1777,6 +1846,9 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
         const TpSplit tps = tp_split(c, p, (flags & EPI_ENERGY) != 0, a.emul != 0);
         const bool tp = tps.on;
+        if (p.ysplit && !tp)
+            return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion: this grid needs the persistent kernel's y-tile items, "
+                                                  "which do not apply to this call");
         size_t smem = p.smem;
         if (tp) {
             a.nload = tps.nl1;
@@ -1805,7 +1877,8 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
 #undef TX_TS_CASE
         }
         a.nslab = (int)grid.x;
-        a.nitems = (int)grid.x * np;
+        a.nyi = p.nyi;
+        a.nitems = (int)grid.x * np * p.nyi;
         if (tp) {
             int dev = 0, nsm = 148;
             cudaGetDevice(&dev);

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _helpers import E_TOL, W_TOL, assert_close, max_row_rel, rel, to_gpu
+from _helpers import E_TOL, W_TOL, _log, assert_close, log_energy, max_row_rel, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -75,6 +75,7 @@ def test_energy_small_config_matches_oracle(prec):
     ref = O.exchange_energy(s.psi, S)
     ctx = P.Context.from_system(s, precision=prec)
     e = float(P.tx_exchange_energy(ctx, to_gpu(s.psi)).item())
+    log_energy(prec, "small", e, ref)
     assert ref < 0
     assert abs(e - ref) / abs(ref) < E_TOL[prec]
 
@@ -222,21 +223,26 @@ def test_tensor_core_precisions_reject_unaligned_rows(prec):
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
 def test_accumulation_chunk_bounds_the_accumulator_error(prec):
-    """Shorter accumulation chunks of the final contraction do not increase the error (the
-    tensor core's float32 accumulator is restarted and the chunks are added in float32), and
-    every chunk length gives the same result within the precision's tolerance."""
+    """The final contraction accumulates on the tensor core for `chunk` Gaussian terms before it
+    is folded into the float32 register accumulator.  The default (a fold after every term) and
+    an explicit chunk of 1 meet the precision's tolerance; longer chunks let the tensor core's
+    truncating accumulator run longer and are not more accurate than a fold after every term."""
     P = _P()
     s = W.config_small()
     S = O.Setup.from_system(s)
     ref = O.exchange_apply(s.psi, S)
     errs = {}
-    for ch in (0, 1000, 7, 1):
+    for ch in (0, 1, 7, 1000):
         ctx = P.Context.from_system(s, precision=prec)
         P.tx_set_accumulation_chunk(ctx, ch)
         got = P.tx_exchange_apply(ctx, to_gpu(s.psi)).cpu().numpy()
         ctx.check_device_error()
         errs[ch] = rel(got, ref)
-        assert errs[ch] < W_TOL[prec], (ch, errs[ch])
+        _log(dict(what=f"chunk{ch}", prec=prec, frob=errs[ch], elem=0.0))
+        assert errs[ch] < (1 if ch in (0, 1) else 10) * W_TOL[prec], (ch, errs[ch])
+    # the default is one term per chunk (W is summed over pairs in an unordered float32 order, so
+    # two runs differ in the last bits)
+    assert abs(errs[0] - errs[1]) <= 0.05 * errs[1]
     assert errs[1] <= errs[1000] * 1.02
     with pytest.raises(P.TuckerExchangeError):
         P.tx_set_accumulation_chunk(P.Context.from_system(s, precision=prec), -1)
@@ -277,13 +283,15 @@ def test_expansion_forms_agree(prec, system):
         P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
 
 
-@pytest.mark.parametrize("rank,kernel", [(64, "converter"), (48, "per_item")])
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent"), (64, "tf32", "converter"),
+                                              (48, "bf16", "per_item"), (48, "tf32", "per_item")])
 def test_large_grid_two_y_tiles(prec, rank, kernel):
-    """n = 160: two 128-row y tiles per plane and n3 past the persistent kernel's 96 columns.
-    At rank 64 (the TiO2-shaped workload) two stage-2 output buffers (2 x 128 TMEM columns) and
-    phi (2 x 160) exceed TMEM's 512 columns, so the converter kernel runs; at rank 48 the
-    one-CTA-per-item kernel with stage 3 read from TMEM.  Apply and energy against the oracle."""
+    """n = 160: two 128-row y tiles per plane.  At rank 64 (the TiO2-shaped workload) a whole
+    plane's stage-2 output buffers (2 x 128 TMEM columns) and phi (2 x 160) exceed TMEM's 512
+    columns: bf16 runs the persistent kernel with one work item per y tile (phi 160 columns,
+    four 64-column Y buffers), TF32 (whose load stages are twice as large) the converter kernel;
+    at rank 48 the one-CTA-per-item kernel with stage 3 read from TMEM.  Apply and energy against
+    the oracle."""
     P = _P()
     assert P.tx_describe_expansion_plan((160, 160, 160), (rank,) * 3, 6, prec)["kernel"] == kernel
     s = W.config_small(n=160, n_orb=2, rank=rank, T=6, L=16.0)
@@ -296,6 +304,7 @@ def test_large_grid_two_y_tiles(prec, rank, kernel):
     ctx.check_device_error()
     assert_close(got, ref, prec, f"n160-r{rank}")
     e_ref = O.exchange_energy(s.psi, S)
+    log_energy(prec, f"n160-r{rank}", e, e_ref)
     assert abs(e - e_ref) / abs(e_ref) < E_TOL[prec]
 
 
@@ -347,3 +356,25 @@ def test_energy_gradient_differentiation_workload(prec, diff_case):
     ctx.check_device_error()
     assert abs(float(E.detach().item()) - E_ref) / abs(E_ref) < E_TOL[prec]
     assert rel(x.grad.cpu().numpy(), g) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def tio2_case():
+    """The TiO2-shaped workload's grid, rank and Gaussian sum (160^3 on [-16,16]^3, rank 64, 45
+    terms; orbitals as in that workload: Gaussian sums over 16 of 240 rutile-like centres) with 8
+    orbitals, so that the oracle's rows take seconds."""
+    s = W.make_system("tio2", 160, 16.0, 8, 64, 45, 4, W.rutile_cluster(240), 2, (0.2, 3.0),
+                      centres_per_orbital=16)
+    S = O.Setup.from_system(s)
+    refs = {i: O.exchange_apply(s.psi, S, psi_tgt=s.psi[i:i + 1]) for i in (0, 5)}
+    return s, refs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+def test_tio2_shaped_block_45_terms(prec, tio2_case):
+    """Full target rows of the TiO2-shaped grid at all 45 terms against the oracle (the largest
+    configuration's grid, rank and terms; the bench runs its full 256 x 1842 block)."""
+    s, refs = tio2_case
+    got = gpu_apply(s, prec, "self")
+    for i, ref in refs.items():
+        assert_close(got[i:i + 1], ref, prec, f"tio2-row{i}")

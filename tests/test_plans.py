@@ -37,8 +37,24 @@ def test_pt_shaped_bf16_plan_matches_the_profiled_launch():
 
 def test_split_precisions_use_the_converter_kernel():
     for prec in ("tf32x3", "bf16x3"):
-        assert P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, prec)["kernel"] == "converter"
+        d = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, prec)
+        assert d["kernel"] == "converter"
+        # separate cross-product accumulators double the TMEM columns of Y and phi, and phi of a
+        # slab (one plane: 96 rows of a 128-row tile, 96 columns) fits the converter warps'
+        # float32 register accumulator (at most 128 columns per lane quadrant)
+        assert d["planes"] == 1 and d["tmem_cols"] == 512
     assert P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "fp32")["kernel"] == "float32"
+
+
+def test_tio2_shaped_bf16_plan_takes_one_y_tile_per_item():
+    """160^3, rank 64, 45 terms, bf16: a whole plane (two y tiles) would need 576 TMEM columns, so
+    the persistent kernel takes one item per (pair, plane, y tile): phi 160 + four Y buffers of
+    64 columns; the one-CTA-per-item form (form 1) falls back to the converter kernel."""
+    d = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16")
+    assert d["kernel"] == "persistent" and d["planes"] == 1 and d["items_per_pair"] == 320
+    assert d["ybuffers"] == 4 and d["tmem_cols"] == 512
+    assert d["stages2"] >= 2 and d["stages3"] >= 2
+    assert P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=1)["kernel"] == "converter"
 
 
 SIZES = [(16, 16, 16), (20, 27, 36), (32, 32, 32), (48, 64, 80), (64, 64, 64), (96, 96, 96), (112, 112, 112),
@@ -63,7 +79,11 @@ def test_every_plan_respects_the_hardware_limits(prec):
         key = (n, rr, T, form, d)
         assert 0 < d["smem_bytes"] <= MAX_DYN_SMEM, key
         assert d["tmem_cols"] in (32, 64, 128, 256, 512), key
-        assert d["planes"] >= 1 and d["items_per_pair"] == -(-n[0] // d["planes"]), key
+        slabs = -(-n[0] // d["planes"])
+        yi = d["items_per_pair"] // slabs       # work items per slab: 1, or one per 128-row y tile
+        assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
+        if yi > 1:
+            assert d["kernel"] == "persistent" and form == 0, key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -77,8 +97,11 @@ def test_every_plan_respects_the_hardware_limits(prec):
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
         if d["kernel"] == "persistent":
             assert form == 0 and d["threads"] == 384, key
-            assert d["planes"] <= 2 and d["n3p"] <= 96 and d["stages2"] <= 4, key
-            assert d["planes"] * -(-n[1] // 128) <= 2, key       # one phi tile per epilogue warp
+            assert d["planes"] <= 2 and d["stages2"] <= 4, key
+            tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
+            assert tiles <= 2, key                                  # at most one phi tile per epilogue warp
+            # an epilogue lane holds its row of phi (two tiles) or every other 32-column chunk (one)
+            assert (d["n3p"] <= 96) if tiles == 2 else (32 * ((-(-d["n3p"] // 32) + 1) // 2) <= 96), key
         else:
             assert d["kernel"] == "per_item" and d["threads"] == 352, key
     assert planned > 50
