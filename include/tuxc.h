@@ -57,7 +57,8 @@ enum tx_status {
     TX_ERR_TIMEOUT = -7,              /* a bounded device-side wait gave up (see tx_check_device_error) */
     TX_ERR_NOT_SETUP = -8,            /* NULL or destroyed context */
     TX_ERR_UNSUPPORTED_SHAPE = -9,    /* shape outside what the selected precision's kernels handle */
-    TX_ERR_ALIGNMENT = -10            /* a device pointer is not 16-byte aligned */
+    TX_ERR_ALIGNMENT = -10,           /* a device pointer is not 16-byte aligned */
+    TX_ERR_NOT_DEFINITE = -11         /* ACE: the exchange matrix is not negative definite */
 };
 
 /* Arithmetic of the mode-product GEMMs.  Accumulation is float32 in every mode; set-up
@@ -228,7 +229,8 @@ int tx_set_expansion_form(tx_ctx* ctx, int form);
  * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 12)
  * values to out:
  *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
- *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items)
+ *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items), 4 persistent with
+ *       stage 3 in bf16 as well (bf16 precision)
  *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
@@ -259,6 +261,34 @@ int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precis
  *   psi_occ / out: device float32 [n_occ][n1][n2][n3]; out is overwritten.
  */
 int tx_exchange_apply_static(tx_ctx* ctx, const float* psi_occ, int n_occ, float* out, tx_stream_t stream);
+
+/*
+ * Adaptively compressed exchange, the step after the exchange potentials ("ACE implementation"
+ * section, Eqs. ace1 and eta).  With W_j = K psi_j (Eq. ace1: tx_exchange_apply of the occupied
+ * block onto itself) and M_ij = <psi_i, W_j>_w (the grid's quadrature weights), the ACE operator is
+ * V_ACE = - sum_k xi_k xi_k^T with xi_k = sum_i (L^-1)_ki W_i and -M = L L^T (Cholesky).
+ *
+ * tx_ace_projectors -- xi from psi_occ and W.
+ *   psi_occ, W   device float32 [n_occ][n1][n2][n3] (W = K psi_occ, in any precision)
+ *   xi           device float32 [n_occ][n1][n2][n3], overwritten (must not overlap the inputs)
+ *   M            device float64 [n_occ][n_occ], receives M_ij = <psi_i, W_j>_w as computed; or NULL
+ * M is formed with float32 products summed in float64; at a truncated Tucker rank it is slightly
+ * asymmetric (the paper is silent on this), and its symmetric part (M + M^T) / 2 is factorised in
+ * float64.  1 <= n_occ <= 4096.  The call synchronises `stream` to read the factorisation's outcome:
+ * TX_ERR_NOT_DEFINITE if the symmetric part of M is not negative definite (xi is then invalid).
+ * Scratch comes from the context's workspace (it may grow).
+ */
+int tx_ace_projectors(tx_ctx* ctx, const float* psi_occ, int n_occ, const float* W, float* xi, double* M,
+                      tx_stream_t stream);
+
+/*
+ * tx_ace_apply -- out_a = V_ACE psi_a = - sum_k xi_k <xi_k, psi_a>_w for a block of n orbitals
+ * (Eq. eta applied to a block).
+ *   xi    device float32 [n_xi][n1][n2][n3] (from tx_ace_projectors)
+ *   psi   device float32 [n][n1][n2][n3];  out  device float32 [n][n1][n2][n3], overwritten
+ * Asynchronous; scratch from the context's workspace.
+ */
+int tx_ace_apply(tx_ctx* ctx, const float* xi, int n_xi, const float* psi, int n, float* out, tx_stream_t stream);
 
 /* Size in bytes of the device workspace the context currently holds. */
 size_t tx_workspace_bytes(const tx_ctx* ctx);

@@ -17,7 +17,7 @@ TX_OK = 0
 STATUS = {
     0: "TX_OK", -1: "TX_ERR_INVALID_ARG", -2: "TX_ERR_SHAPE", -3: "TX_ERR_NOT_ORTHONORMAL",
     -4: "TX_ERR_UNSUPPORTED_PRECISION", -5: "TX_ERR_CUDA", -6: "TX_ERR_OOM", -7: "TX_ERR_TIMEOUT",
-    -8: "TX_ERR_NOT_SETUP", -9: "TX_ERR_UNSUPPORTED_SHAPE", -10: "TX_ERR_ALIGNMENT",
+    -8: "TX_ERR_NOT_SETUP", -9: "TX_ERR_UNSUPPORTED_SHAPE", -10: "TX_ERR_ALIGNMENT", -11: "TX_ERR_NOT_DEFINITE",
 }
 EXPORTED = [
     "tx_tucker_setup", "tx_destroy", "tx_set_precision", "tx_exchange_apply", "tx_exchange_energy",
@@ -27,7 +27,7 @@ EXPORTED = [
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
     "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
     "tx_exchange_apply_static", "tx_describe_expansion_plan", "tx_set_wait_limit", "tx_selftest_wait",
-    "tx_exchange_energy_from_w",
+    "tx_exchange_energy_from_w", "tx_ace_projectors", "tx_ace_apply",
 ]
 
 
@@ -126,6 +126,10 @@ def lib():
     L.tx_selftest_wait.restype = _I
     L.tx_exchange_energy_from_w.argtypes = [_P, _P, _P, _I, _P, _P]
     L.tx_exchange_energy_from_w.restype = _I
+    L.tx_ace_projectors.argtypes = [_P, _P, _I, _P, _P, _P, _P]
+    L.tx_ace_projectors.restype = _I
+    L.tx_ace_apply.argtypes = [_P, _P, _I, _P, _I, _P, _P]
+    L.tx_ace_apply.restype = _I
     L.tx_status_string.argtypes = [_I]
     L.tx_status_string.restype = ctypes.c_char_p
     L.tx_last_error_message.argtypes = []
@@ -282,6 +286,35 @@ def tx_exchange_energy_from_w(ctx: Context, psi, W, e_out=None, stream=None):
     return e_out
 
 
+def tx_ace_projectors(ctx: Context, psi_occ, W=None, stream=None):
+    """(xi, M): the ACE projection vectors and M_ij = <psi_i, W_j>_w (float64 device tensor).
+    W = K psi_occ is computed with the context's precision when not given."""
+    ctx._block(psi_occ, "psi_occ")
+    if W is None:
+        W = tx_exchange_apply(ctx, psi_occ, stream=stream)
+    ctx._block(W, "W")
+    if W.shape[0] != psi_occ.shape[0]:
+        raise ValueError("psi_occ and W must hold the same number of orbitals")
+    xi = torch.empty_like(psi_occ)
+    M = torch.empty((psi_occ.shape[0], psi_occ.shape[0]), dtype=torch.float64, device=psi_occ.device)
+    st = lib().tx_ace_projectors(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(W), _ptr(xi), _ptr(M),
+                                 _stream(stream))
+    _check(st, "tx_ace_projectors")
+    return xi, M
+
+
+def tx_ace_apply(ctx: Context, xi, psi, out=None, stream=None):
+    """V_ACE psi = - sum_k xi_k <xi_k, psi>_w for every orbital of the block psi."""
+    ctx._block(xi, "xi")
+    ctx._block(psi, "psi")
+    if out is None:
+        out = torch.empty_like(psi)
+    ctx._block(out, "out")
+    st = lib().tx_ace_apply(ctx.handle, _ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], _ptr(out), _stream(stream))
+    _check(st, "tx_ace_apply")
+    return out
+
+
 def tx_selftest_wait(ctx: Context, hold_tmem=True, stream=None):
     """Launches the bounded-wait self-test (a wait nothing completes); see include/tuxc.h."""
     _check(lib().tx_selftest_wait(ctx.handle, 1 if hold_tmem else 0, _stream(stream)), "tx_selftest_wait")
@@ -429,7 +462,7 @@ def tx_set_expansion_form(ctx, form):
 
 PLAN_FIELDS = ("kernel", "planes", "stages2", "stages3", "ybuffers", "tmem_cols", "smem_bytes", "threads",
                "ksteps2", "ksteps3", "n3p", "items_per_pair")
-PLAN_KERNELS = {0: "float32", 1: "converter", 2: "per_item", 3: "persistent"}
+PLAN_KERNELS = {0: "float32", 1: "converter", 2: "per_item", 3: "persistent", 4: "persistent_bf16"}
 
 
 def tx_describe_expansion_plan(n, r, T, precision, form=0):

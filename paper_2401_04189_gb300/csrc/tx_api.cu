@@ -356,6 +356,7 @@ extern "C" const char* tx_status_string(int s) {
         case TX_ERR_NOT_SETUP: return "TX_ERR_NOT_SETUP";
         case TX_ERR_UNSUPPORTED_SHAPE: return "TX_ERR_UNSUPPORTED_SHAPE";
         case TX_ERR_ALIGNMENT: return "TX_ERR_ALIGNMENT";
+        case TX_ERR_NOT_DEFINITE: return "TX_ERR_NOT_DEFINITE";
         default: return "TX_ERR_UNKNOWN";
     }
 }

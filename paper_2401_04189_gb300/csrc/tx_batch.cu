@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "tx_internal.h"
+#include "tx_tc_ops.h"
 #include "tx_paths.h"
 
 namespace tx {
@@ -20,6 +21,7 @@ int tc_feasible_plans(const tx_ctx* c, int* bx, int* ns, int cap);
 bool tc_current_plan(const tx_ctx* c, int* bx, int* ns);
 bool tc_plan_fits(const tx_ctx* c, int bx, int ns);
 int tc_describe_plan(const tx_ctx* c, int* out, int nout);
+int tc_build_operand_image(tx_ctx* c, cudaStream_t s);
 }  // namespace tx
 
 using namespace tx;
@@ -113,7 +115,10 @@ extern "C" int tx_set_accumulation_chunk(tx_ctx* c, int terms) {
 extern "C" int tx_set_expansion_form(tx_ctx* c, int form) {
     if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
     if (form < 0 || form > 1) return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic) or 1 (one CTA per item)");
+    if (form == c->consume_form) return TX_OK;
     c->consume_form = form;
+    // the two forms' kernels read per-term operator images of different layouts
+    if (c->tc && !c->tc->split) return tc_build_operand_image(c, c->last_stream);
     return TX_OK;
 }
 

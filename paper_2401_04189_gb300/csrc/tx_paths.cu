@@ -121,11 +121,19 @@ int simt_batch(tx_ctx* c, const CallSpec& cs, const PairRec* recs, const PairRec
 
 }  // namespace
 
+int simt_adjoint_mode1(const tx_ctx* c, const float* R, float* H, int np, cudaStream_t s) {
+    return gemm_mode1_adjoint(c, R, H, np, s);
+}
+int simt_expand_mode1(const tx_ctx* c, const float* G, const float* M1, int nt, float* Z, int np, cudaStream_t s) {
+    return gemm_mode1_expand(c, G, M1, nt, Z, np, s);
+}
+
 int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     const long N3 = (long)c->n[0] * c->n[1] * c->n[2];
     const long P = pair_count(cs.mode, cs.n_occ, cs.n_tgt);
-    // the tensor-core kernels cover the forward path; gradients run the float32 kernels
-    const bool tc = c->prec != TX_PREC_FP32 && (cs.kind == CALL_APPLY || cs.kind == CALL_ENERGY);
+    // every call kind of a tensor-core precision runs the tensor-core kernels (the adjoint's
+    // first-mode sum over the terms and its single-term expansion run in float32)
+    const bool tc = c->prec != TX_PREC_FP32;
     const int ntables = cs.kind == CALL_VJP ? 2 : 1;
     const size_t recs_bytes = align_up(sizeof(PairRec) * (size_t)P, 256) * ntables;
     size_t per_pair;

@@ -33,6 +33,11 @@ struct BatchBuffers {
     double* epart;            // energy partials of this batch
 };
 size_t tc_batch_bytes_per_pair(const tx_ctx* c, int kind);
+// float32 building blocks shared with the tensor-core adjoint (tx_paths.cu):
+// H[p][(g,b)][a] = sum_{t,x} R[p][t][x][(g,b)] A_t1[x][a]
+int simt_adjoint_mode1(const tx_ctx* c, const float* R, float* H, int np, cudaStream_t s);
+// Z[p][t][x][(g,b)] = sum_a M1_t[x][a] G[p][(g,b)][a]  (nt terms of M1 = [nt][n1][r1])
+int simt_expand_mode1(const tx_ctx* c, const float* G, const float* M1, int nt, float* Z, int np, cudaStream_t s);
 long tc_epart_per_pair(const tx_ctx* c);
 int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "tx_paths.h"
@@ -151,8 +152,9 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     const size_t e_u3 = (size_t)r3 * ldk(n3, eb), e_u2 = (size_t)r2 * ldk(n2, eb), e_u1 = (size_t)r1 * ldk(n1, eb);
     const size_t e_a1 = (size_t)T * n1 * ldk(r1, eb), e_a2 = (size_t)T * n2 * ldk(r2, eb);
     const size_t e_a3 = (size_t)T * n3 * ldk(r3, eb), e_a3f = (size_t)T * n3 * pad8(r3);
+    const size_t e_a3t = (size_t)T * r3 * ldk(n3, eb), e_a2t = (size_t)T * r2 * ldk(n2, eb);
     auto al = [](size_t e) { return (e + 127) & ~(size_t)127; };   // 256-byte aligned pieces
-    const size_t tot = al(e_u3) + al(e_u2) + al(e_u1) + al(e_a1) + al(e_a2) + al(e_a3);
+    const size_t tot = al(e_u3) + al(e_u2) + al(e_u1) + al(e_a1) + al(e_a2) + al(e_a3) + al(e_a3t) + al(e_a2t);
     // bf16 single pass: the stage-3 B operand also in float32 (TF32), after everything else
     const bool a3f_extra = !op->split && !op->tf32;
     const size_t bytes = tot * op->esize * (op->split ? 2 : 1) + (a3f_extra ? al(e_a3f) * 4 : 0);
@@ -175,6 +177,8 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     op->st.A1s = take(e_a1);
     op->st.A2 = take(e_a2);
     op->st.A3 = take(e_a3);
+    op->st.A3T = take(e_a3t);
+    op->st.A2T = take(e_a2t);
     op->st.off_lo = tot * op->esize;
     op->st.A3f = a3f_extra ? (void*)(op->buf + tot * op->esize) : (op->split ? nullptr : op->st.A3);
     const size_t lo = tot;   // element offset of every lo copy
@@ -193,6 +197,13 @@ int tc_prepare(tx_ctx* c, cudaStream_t s) {
     TX_TRY(conv(c->d_A64[0], (long)T * n1, r1, r1, 1, ldk(r1, eb), op->st.A1s));
     TX_TRY(conv(c->d_A64[1], (long)T * n2, r2, r2, 1, ldk(r2, eb), op->st.A2));
     TX_TRY(conv(c->d_A64[2], (long)T * n3, r3, r3, 1, ldk(r3, eb), op->st.A3));
+    // the adjoint's transposed operators, one term at a time: rows gamma (beta), K = z (y)
+    for (int t = 0; t < T; ++t) {
+        TX_TRY(conv(c->d_A64[2] + (size_t)t * n3 * r3, r3, n3, 1, r3, ldk(n3, eb),
+                    (char*)op->st.A3T + (size_t)t * r3 * ldk(n3, eb) * op->esize));
+        TX_TRY(conv(c->d_A64[1] + (size_t)t * n2 * r2, r2, n2, 1, r2, ldk(n2, eb),
+                    (char*)op->st.A2T + (size_t)t * r2 * ldk(n2, eb) * op->esize));
+    }
     if (a3f_extra) {
         const long n = (long)T * n3 * r3;
         k_static_operand<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->d_A64[2], (long)T * n3, r3, r3, 1, pad8(r3), 1, 0,
@@ -212,15 +223,20 @@ static SplitF32 split_f32(const tx_ctx* c) {
     return SplitF32{n1 * r3 * r2, r3 * r2 * r1, (size_t)c->T * n1 * r3 * r2};
 }
 
+size_t tc_adjoint_bytes_per_pair(const tx_ctx* c);
+
 size_t tc_batch_bytes_per_pair(const tx_ctx* c, int kind) {
-    (void)kind;
     const TcScratch sc = tc_scratch(c);
     const TcOperands* op = c->tc;
+    size_t fwd;
     if (op->split) {
         const SplitF32 f = split_f32(c);
-        return (f.s2 + f.g + f.z) * sizeof(float) + sc.z * op->esize * 2 + 1024;
+        fwd = (f.s2 + f.g + f.z) * sizeof(float) + sc.z * op->esize * 2 + 1024;
+    } else {
+        fwd = (sc.s1 + sc.s2 + sc.g + sc.z) * op->esize + 1024;
     }
-    return (sc.s1 + sc.s2 + sc.g + sc.z) * op->esize + 1024;
+    if (kind == CALL_GRAD || kind == CALL_VJP) return std::max(fwd, tc_adjoint_bytes_per_pair(c));
+    return fwd;
 }
 
 // G[p][(g,b)][a] = sum_x S2[p][x][(g,b)] U1[x][a]  (float32, mode 1 of the projection)
@@ -249,22 +265,17 @@ static int f32_mode1_expand(const tx_ctx* c, const float* G, float* Z, int np, c
 
 long tc_epart_per_pair(const tx_ctx* c) { return tc_consume_blocks(c); }
 
-int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStream_t s) {
-    if (cs.kind != CALL_APPLY && cs.kind != CALL_ENERGY)
-        return fail(TX_ERR_UNSUPPORTED_PRECISION, "tensor-core batches run the forward path only");
+// The forward hot path of one pair batch (Eq. final, Eq. hadam): pair densities SA[ia] * SB[ib]
+// projected onto the core, expanded over every Gaussian term, and out0[o0] -= mul0[m0] * phi,
+// out1[o1] -= mul1[m1] * phi (and the energy sums) in the expansion's epilogue.
+static int tc_forward(tx_ctx* c, const BatchBuffers& b, const PairRec* recs, const float* SA, int nA, const float* SB,
+                      int nB, const float* MUL0, const float* MUL1, float* OUT0, float* OUT1, const OrbCounts& cnt,
+                      int flags, bool subset, cudaStream_t s) {
     const TcOperands* op = c->tc;
     const TcScratch sc = tc_scratch(c);
     const int np = b.np;
-    const int eb = op->esize, mult = op->split ? 2 : 1;
+    const int eb = op->esize;
     const int n1 = c->n[0], n2 = c->n[1], r1 = c->r[0], r2 = c->r[1], r3 = c->r[2], T = c->T;
-    const bool subset = cs.mode == PAIRS_SUBSET;
-    const float* SA = subset ? cs.occ : cs.tgt;
-    const int nA = subset ? cs.n_occ : cs.n_tgt;
-    int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
-    if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
-    // OUT rows: the call's targets (apply only; the energy call writes no W)
-    const int nout = cs.out0 ? cs.n_tgt : 0;
-    const OrbCounts cnt{nA, cs.n_occ, cs.n_occ, cs.n_occ, nout, nout};
     if (op->split) {
         // Split precisions: the projection onto the core and the first expansion mode run in
         // float32 on the CUDA cores (13% of the flops on the Pt-shaped block), so that the core
@@ -278,8 +289,8 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
         Z = (char*)(((uintptr_t)Z + 255) & ~(uintptr_t)255);
         FieldArgs fa{};
         fa.SA = SA;
-        fa.SB = cs.occ;
-        TX_TRY(simt_project_s2(c, b.recs, b.p0, np, fa, 0, S2f, s));
+        fa.SB = SB;
+        TX_TRY(simt_project_s2(c, recs, b.p0, np, fa, 0, S2f, s));
         TX_TRY(f32_mode1_project(c, S2f, Gf, np, s));
         TX_TRY(f32_mode1_expand(c, Gf, Zf, np, s));
         const long rows = (long)np * T * n1 * r3;
@@ -287,71 +298,164 @@ int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStrea
         k_split_z<<<(unsigned)((nz + 255) / 256), 256, 0, s>>>(Zf, rows, r2, sc.ld_b, op->tf32 ? 1 : 0, Z,
                                                               (size_t)np * sc.z);
         TX_LAUNCHED();
-        TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, b.epart, s,
-                          subset));
-        (void)r1;
-        (void)n2;
-        (void)mult;
-        (void)eb;
-        return TX_OK;
+        return tc_consume(c, recs, b.p0, np, Z, SA, SB, MUL0, MUL1, OUT0, OUT1, cnt, flags, b.epart, s, subset);
     }
     char* S1 = b.scratch;
-    char* S2 = S1 + (size_t)np * sc.s1 * eb * mult;
-    char* G = S2 + (size_t)np * sc.s2 * eb * mult;
-    char* Z = G + (size_t)np * sc.g * eb * mult;
+    char* S2 = S1 + (size_t)np * sc.s1 * eb;
+    char* G = S2 + (size_t)np * sc.s2 * eb;
+    char* Z = G + (size_t)np * sc.g * eb;
     const int out_type = op->tf32 ? TC_OUT_F32 : TC_OUT_BF16;
-    auto lo_of = [&](const void* hi, size_t per_pair) -> const void* {
-        return op->split ? (const char*)hi + (size_t)np * per_pair * eb : nullptr;
-    };
 
     // 1. S1 = rho x3 U3^T (rho = psi_a psi_b formed in the kernel)
-    TX_TRY(tc_project_mode3(c, b.recs, b.p0, np, SA, nA, cs.occ, cs.n_occ, 0, S1, s));
+    TX_TRY(tc_project_mode3(c, recs, b.p0, np, SA, nA, SB, nB, 0, S1, s));
 
     // 2. S2[p][g][b][x] = sum_y S1[p][(g,x)][y] U2T[b][y], b < ld_b: the columns past r2 read
     //    rows of U2^T past its end (zero-filled), so the b padding is exact zeros and stays zero
     //    through G and Z (whose rows TMA reads along b in whole 32-byte sectors)
     {
-        TcOperand A{S1, lo_of(S1, sc.s1), (uint64_t)n2, (uint64_t)r3 * n1, (uint64_t)np, (uint64_t)sc.ld_y, sc.s1};
-        TcOperand B{op->st.U2T, op->split ? (const char*)op->st.U2T + op->st.off_lo : nullptr, (uint64_t)ldk(n2, eb),
-                    (uint64_t)r2, 1, (uint64_t)ldk(n2, eb), 0};
+        TcOperand A{S1, nullptr, (uint64_t)n2, (uint64_t)r3 * n1, (uint64_t)np, (uint64_t)sc.ld_y, sc.s1};
+        TcOperand B{op->st.U2T, nullptr, (uint64_t)ldk(n2, eb), (uint64_t)r2, 1, (uint64_t)ldk(n2, eb), 0};
         TcGemmArgs g{};
         g.M = r3 * n1; g.N = sc.ld_b; g.K = n2; g.nb1 = np; g.nb2 = 1;
         g.a_z1 = 1;
         g.C = S2; g.rdiv = n1; g.c_mh = (long)sc.ld_b * sc.ld_x; g.c_m = 1; g.c_n = sc.ld_x; g.c_b1 = (long)sc.s2;
-        g.c_lo = (long)np * sc.s2; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
-        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj2", s));
+        g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, false, "tc_proj2", s));
     }
     // 3. G[p][(g,b)][a] = sum_x S2[p][(g,b)][x] U1T[a][x]  (rows (g, b < ld_b), a < ld_a: the
     //    columns past r1 read rows of U1^T past its end, so G's a padding is zeros too)
     {
-        TcOperand A{S2, lo_of(S2, sc.s2), (uint64_t)n1, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_x, sc.s2};
-        TcOperand B{op->st.U1T, op->split ? (const char*)op->st.U1T + op->st.off_lo : nullptr, (uint64_t)ldk(n1, eb),
-                    (uint64_t)r1, 1, (uint64_t)ldk(n1, eb), 0};
+        TcOperand A{S2, nullptr, (uint64_t)n1, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_x, sc.s2};
+        TcOperand B{op->st.U1T, nullptr, (uint64_t)ldk(n1, eb), (uint64_t)r1, 1, (uint64_t)ldk(n1, eb), 0};
         TcGemmArgs g{};
         g.M = r3 * sc.ld_b; g.N = sc.ld_a; g.K = n1; g.nb1 = np; g.nb2 = 1;
         g.a_z1 = 1;
         g.C = G; g.c_m = sc.ld_a; g.c_n = 1; g.c_b1 = (long)sc.g;
-        g.c_lo = (long)np * sc.g; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
-        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_proj1", s));
+        g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, false, "tc_proj1", s));
     }
     // 4. Z[p][(t,x)][(g,b)] = sum_a A1s[(t,x)][a] G[p][(g,b)][a]  (b < ld_b, padding included)
     {
-        TcOperand A{op->st.A1s, op->split ? (const char*)op->st.A1s + op->st.off_lo : nullptr, (uint64_t)ldk(r1, eb),
-                    (uint64_t)T * n1, 1, (uint64_t)ldk(r1, eb), 0};
-        TcOperand B{G, lo_of(G, sc.g), (uint64_t)sc.ld_a, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_a, sc.g};
+        TcOperand A{op->st.A1s, nullptr, (uint64_t)ldk(r1, eb), (uint64_t)T * n1, 1, (uint64_t)ldk(r1, eb), 0};
+        TcOperand B{G, nullptr, (uint64_t)sc.ld_a, (uint64_t)r3 * sc.ld_b, (uint64_t)np, (uint64_t)sc.ld_a, sc.g};
         TcGemmArgs g{};
         g.M = T * n1; g.N = r3 * sc.ld_b; g.K = r1; g.nb1 = np; g.nb2 = 1;
         g.b_z1 = 1;
         g.C = Z; g.c_m = (long)r3 * sc.ld_b; g.c_n = 1; g.c_b1 = (long)sc.z;
-        g.c_lo = (long)np * sc.z; g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
-        TX_TRY(tc_rows_launch(A, B, g, op->tf32, op->split, "tc_zprod", s));
+        g.c_type = out_type; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_rows_launch(A, B, g, op->tf32, false, "tc_zprod", s));
     }
     // 5. modes 2 and 3 for every term, phi accumulated in TMEM, Hadamard / energy epilogue
-    // (symmetric pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers)
-    TX_TRY(tc_consume(c, b.recs, b.p0, np, Z, SA, cs.occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, b.epart, s,
-                      subset));
-    (void)r1;
-    return TX_OK;
+    return tc_consume(c, recs, b.p0, np, Z, SA, SB, MUL0, MUL1, OUT0, OUT1, cnt, flags, b.epart, s, subset);
+}
+
+// float32 scratch of the adjoint (elements per pair): R [T][n1][r3 r2], H [r3 r2][r1], Z [n1][r3 r2]
+struct AdjF32 {
+    size_t r, h, z;
+};
+static AdjF32 adj_f32(const tx_ctx* c) {
+    const size_t n1 = c->n[0], r1 = c->r[0], rr = (size_t)c->r[1] * c->r[2];
+    return AdjF32{(size_t)c->T * n1 * rr, rr * r1, n1 * rr};
+}
+
+// The adjoint of one pair batch (derived; the paper has no gradient): with L = sum_t mu_t
+// (x)_d A_td U_d^T, zeta_p = L^T y_p = (x)_d U_d [sum_t mu_t y_p x1 A_t1^T x2 A_t2^T x3 A_t3^T] for the
+// pair products y_p = SA[ia] * SB[ib] (* w), then fo.OUT0[o0] -= fo.MUL0[m0] * zeta and
+// fo.OUT1[o1] -= fo.MUL1[m1] * zeta.  Modes 3 and 2 of every term (2 n^3 r + 2 n^2 r^2 flops per
+// term, the adjoint's dominant work) run on the tensor cores; the sum over terms and x of mode 1
+// and the single-term expansion with U run in float32 on the CUDA cores (as the split forms'
+// projection does, so that the split forms keep float32 accuracy there).
+static int tc_adjoint(tx_ctx* c, const BatchBuffers& b, const PairRec* recs, const float* SA, int nA, const float* SB,
+                      int nB, int pflags, const FieldArgs& fo, cudaStream_t s) {
+    const TcOperands* op = c->tc;
+    const TcScratch sc = tc_scratch(c);
+    const int np = b.np;
+    const int eb = op->esize, mult = op->split ? 2 : 1;
+    const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T;
+    const long rr = (long)r2 * r3;
+    const AdjF32 f = adj_f32(c);
+    char* S1 = b.scratch;
+    float* R = (float*)(((uintptr_t)(S1 + (size_t)np * sc.s1 * eb * mult) + 255) & ~(uintptr_t)255);
+    float* H = R + (size_t)np * f.r;
+    float* Z = H + (size_t)np * f.h;
+    const int out_type = op->tf32 ? (op->split ? TC_OUT_F32_SPLIT : TC_OUT_F32) : (op->split ? TC_OUT_BF16_SPLIT : TC_OUT_BF16);
+    (void)out_type;
+    for (int t = 0; t < T; ++t) {
+        // S1[p][g][x][y] = sum_z y_p[x][y][z] (mu_t A_t3)[z][g]
+        const char* a3t = (const char*)op->st.A3T + (size_t)t * r3 * ldk(n3, eb) * eb;
+        TX_TRY(tc_project_mode3(c, recs, b.p0, np, SA, nA, SB, nB, pflags, S1, s, a3t));
+        // R[p][t][x][g][b] = sum_y S1[p][(g,x)][y] A_t2[y][b]   (float32)
+        const char* a2t = (const char*)op->st.A2T + (size_t)t * r2 * ldk(n2, eb) * eb;
+        TcOperand A{S1, op->split ? S1 + (size_t)np * sc.s1 * eb : nullptr, (uint64_t)n2, (uint64_t)r3 * n1, (uint64_t)np,
+                    (uint64_t)sc.ld_y, sc.s1};
+        TcOperand B{a2t, op->split ? a2t + op->st.off_lo : nullptr, (uint64_t)ldk(n2, eb), (uint64_t)r2, 1,
+                    (uint64_t)ldk(n2, eb), 0};
+        TcGemmArgs g{};
+        g.M = r3 * n1; g.N = r2; g.K = n2; g.nb1 = np; g.nb2 = 1;
+        g.a_z1 = 1;
+        g.C = R + (size_t)t * n1 * rr; g.rdiv = n1; g.c_mh = r2; g.c_m = rr; g.c_n = 1; g.c_b1 = (long)f.r;
+        g.c_type = TC_OUT_F32; g.alpha = 1.f; g.err = c->d_err;
+        TX_TRY(tc_gemm_launch(A, B, g, op->tf32, op->split, "tc_adj2", s));
+    }
+    TX_TRY(simt_adjoint_mode1(c, R, H, np, s));                  // H = sum_{t,x} R A_t1
+    TX_TRY(simt_expand_mode1(c, H, c->f_U[0], 1, Z, np, s));     // Z = U1 H
+    return simt_expand_consume(c, recs, b.p0, np, fo, Z, 1, c->f_U[1], c->f_U[2], EPI_OUT, b.epart, s);
+}
+
+size_t tc_adjoint_bytes_per_pair(const tx_ctx* c) {
+    const TcScratch sc = tc_scratch(c);
+    const TcOperands* op = c->tc;
+    const AdjF32 f = adj_f32(c);
+    return sc.s1 * op->esize * (op->split ? 2 : 1) + (f.r + f.h + f.z) * sizeof(float) + 1024;
+}
+
+int tc_run_batch(tx_ctx* c, const CallSpec& cs, const BatchBuffers& b, cudaStream_t s) {
+    const bool subset = cs.mode == PAIRS_SUBSET;
+    switch (cs.kind) {
+        case CALL_APPLY:
+        case CALL_ENERGY: {
+            const float* SA = subset ? cs.occ : cs.tgt;
+            const int nA = subset ? cs.n_occ : cs.n_tgt;
+            int flags = (cs.kind == CALL_APPLY) ? EPI_OUT : 0;
+            if (cs.kind == CALL_ENERGY || cs.e_dev) flags |= EPI_ENERGY;
+            // OUT rows: the call's targets (apply only; the energy call writes no W); symmetric
+            // pairs: rec.ia == rec.m1 and rec.ib == rec.m0, so the energy factors are the multipliers
+            const int nout = cs.out0 ? cs.n_tgt : 0;
+            const OrbCounts cnt{nA, cs.n_occ, cs.n_occ, cs.n_occ, nout, nout};
+            return tc_forward(c, b, b.recs, SA, nA, cs.occ, cs.n_occ, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, subset,
+                              s);
+        }
+        case CALL_GRAD: {
+            // dE/dpsi_k = w * W_k - sum_j psi_j * L^T(w * rho_kj): the forward pipeline with the
+            // weights folded into the epilogue, then the adjoint of the weighted pair densities
+            const int n = cs.n_occ;
+            const OrbCounts cnt{n, n, n, n, n, n};
+            const int flags = EPI_OUT | EPI_MULW | (cs.e_dev ? EPI_ENERGY : 0);
+            TX_TRY(tc_forward(c, b, b.recs, cs.occ, n, cs.occ, n, cs.occ, cs.occ, cs.out0, cs.out0, cnt, flags, true, s));
+            FieldArgs fo{};
+            fo.MUL0 = cs.occ;
+            fo.MUL1 = cs.occ;
+            fo.OUT0 = cs.out0;
+            fo.OUT1 = cs.out0;
+            return tc_adjoint(c, b, b.recs, cs.occ, n, cs.occ, n, PROD_MULW, fo, s);
+        }
+        case CALL_VJP: {
+            if (cs.out0) {
+                // grad_occ_j -= cot_k * phi_kj
+                const OrbCounts cnt{cs.n_tgt, cs.n_occ, cs.n_tgt, 0, cs.n_occ, 0};
+                TX_TRY(tc_forward(c, b, b.recs, cs.tgt, cs.n_tgt, cs.occ, cs.n_occ, cs.cot, nullptr, cs.out0, nullptr, cnt,
+                                  EPI_OUT, false, s));
+            }
+            // zeta_kj = L^T(cot_k psi_j): grad_tgt_k -= psi_j zeta, grad_occ_j -= psi_tgt_k zeta
+            FieldArgs fo{};
+            fo.MUL0 = cs.occ;
+            fo.OUT0 = cs.out1;
+            fo.MUL1 = cs.tgt;
+            fo.OUT1 = cs.out0;
+            return tc_adjoint(c, b, b.recs2, cs.cot, cs.n_tgt, cs.occ, cs.n_occ, 0, fo, s);
+        }
+    }
+    return fail(TX_ERR_INVALID_ARG, "unknown call kind");
 }
 
 }  // namespace tx

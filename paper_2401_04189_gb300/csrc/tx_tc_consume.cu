@@ -74,6 +74,8 @@ struct ConsumeArgs {
     // persistent single-pass kernel: work items (pair, slab), slabs per pair, epilogue region
     int nitems, nslab;
     int nyi;                   // persistent kernel: work items per slab (1, or one per y tile of 128 rows)
+    int nys;                   // bf16 persistent kernel: Y operand tiles in shared memory
+    uint32_t ys_off, ys_bytes, ys_tile;   // ... their offset, stride per buffer, stride per tile
     uint32_t epi_off;
 };
 
@@ -1427,6 +1429,413 @@ __global__ void __launch_bounds__(32, 1)
     for (uint32_t i = threadIdx.x; i < (g.ya_bytes + g.b3_bytes) / 16; i += 32) dst[i] = src[i];
 }
 
+
+// bf16 form of the persistent kernel: stage 3 also runs as kind::f16.  Stage 2 leaves Y_t in
+// TMEM in float32 (y on the lanes); four converter warps (one per TMEM lane quadrant) round it to
+// bf16 and write it as the K-major stage-3 A operand in shared memory (128-byte swizzle, one
+// 128-row tile per plane and y tile), so stage 3 multiplies bf16 by bf16 at the full tensor rate
+// instead of running as TF32 from TMEM.  phi is double-buffered in TMEM: the epilogue of item k
+// reads it directly from TMEM while item k + 1 accumulates into the other buffer.
+// Warp roles: 0-7 converters (two groups of four, one TMEM lane quadrant per warp, taking
+// alternate terms so that one group's TMEM load round trip overlaps the other's stores), 8
+// stage-2 producer, 9 stage-2 MMAs, 10 stage-3 producer and Z prefetches, 11 stage-3 MMAs, 12-15
+// epilogue.
+constexpr int kThreadsTb = 512;
+constexpr int kMaxYs = 3;
+constexpr uint32_t kTbEpiBytes = 0;                  // the epilogue reads the orbitals directly
+constexpr uint32_t kYsAtom = 128u * 128u;            // one 128-row x 128-byte operand atom
+
+template <int KS2, int KS3>
+__global__ void __launch_bounds__(kThreadsTb, 1)
+    k_consume_tb(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ EpiMaps em, ConsumeArgs a) {
+    constexpr int AK2 = 64;                  // stage-2 elements per 128-byte atom
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
+    __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], ysfull[kMaxYs], ysfree[kMaxYs];
+    __shared__ uint64_t phidone[2], phifree[2], s3fin[2], ebar[4];
+    __shared__ uint32_t tmem_base;
+    __shared__ double red[2][4];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NL = a.nload, NL3 = a.nload3, NYB = a.nyb, NYS = a.nys, BX = a.bx, NT = a.nt;
+    const int nmine = (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto item_of = [&](int k, int& pl, int& slab, int& iy) {
+        const int it = (int)blockIdx.x + k * (int)gridDim.x;
+        const int ps = it / a.nyi;
+        iy = it - ps * a.nyi;
+        pl = ps / a.nslab;
+        slab = ps - pl * a.nslab;
+    };
+    auto YAs = [&](int s) { return smem + s * a.load_bytes; };
+    auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
+    auto B3s = [&](int s) { return smem + a.a3_off + s * a.load3_bytes; };
+    auto YSs = [&](int b) { return smem + a.ys_off + b * a.ys_bytes; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMaxLoad; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+            mbar_init(&full3[s], 1);
+            mbar_init(&empty3[s], 1);
+        }
+        for (int b = 0; b < kMaxYBuf; ++b) {
+            mbar_init(&s2bar[b], 1);
+            mbar_init(&ybar[b], 4);
+        }
+        for (int b = 0; b < kMaxYs; ++b) {
+            mbar_init(&ysfull[b], 4);
+            mbar_init(&ysfree[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&phidone[b], 1);
+            mbar_init(&phifree[b], 4);
+            mbar_init(&s3fin[b], 1);
+        }
+        for (int w = 0; w < 4; ++w) mbar_init(&ebar[w], 1);
+        fence_barrier_init();
+    }
+    // Z tile rows that no copy writes feed Y columns that are never converted: keep them finite
+    for (int s = 0; s < NL; ++s) {
+        uint4* z = (uint4*)Zs(s);
+        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreadsTb) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    fence_async_smem();
+    if (warp == 8) {
+        tmem_alloc(&tmem_base, a.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t phi_cols = (uint32_t)(a.nT3 * a.n3p);
+    const uint32_t tPhi0 = tmem + (uint32_t)NYB * a.y_cols;
+    const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
+    const int na2 = (a.ks2 + 3) / 4;
+
+    if (warp == 8) {
+        // ------------------------- stage-2 producer: A_t2 and Z -------------------------
+        int issued = 0, s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k) {
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
+            const int x0 = slab * BX;
+            for (int t = 0; t < NT; ++t) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[s], ph ^ 1, a.err, 61));
+                if (!ok) break;
+                ++issued;
+                mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
+                const int zdep = pl * NT + t;
+                bulk_load_w(YAs(s), a.img + (size_t)t * a.img_stride, a.ya_bytes, &full_bar[s]);
+                if (a.zone) {
+                    tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, x0 * a.r3, zdep);
+                    for (int kk = 1; kk < na2; ++kk)
+                        tma_load_3d_w(Zs(s) + kk * z_atom, &mZ, &full_bar[s], kk * AK2, x0 * a.r3, zdep);
+                } else {
+                    for (int kk = 0; kk < na2; ++kk)
+                        for (int p = 0; p < BX; ++p)
+                            tma_load_3d_w(Zs(s) + kk * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s],
+                                          kk * AK2, (x0 + p) * a.r3, zdep);
+                }
+                if (++s == NL) { s = 0; ph ^= 1; }
+            }
+        }
+        if (!ok)
+            for (int g = (issued > NL ? issued - NL : 0); g < issued; ++g)
+                mbar_drain(&full_bar[g % NL], (g / NL) & 1, a.err);
+    } else if (warp == 10) {
+        // ---------------- stage-3 producer: mu_t A_t3 (bf16), and the Z L2 prefetches ----------------
+        const size_t zterm = (size_t)a.n1 * a.z_plane;
+        auto prefetch = [&](int g) {
+            const int k = g / NT, t = g - k * NT;
+            if (k >= nmine) return;
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
+            const int x0 = slab * BX;
+            const int np_ = min(BX, a.n1 - x0);
+            bulk_prefetch_l2_w(a.zsrc + ((size_t)pl * NT * a.n1 + x0) * a.z_plane + (size_t)t * zterm,
+                               (uint32_t)np_ * a.z_plane);
+        };
+        for (int g = 1; g <= NL + 2; ++g) prefetch(g);
+        int issued = 0, s = 0, g = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t, ++g) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&empty3[s], ph ^ 1, a.err, 62));
+                if (!ok) break;
+                ++issued;
+                mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
+                bulk_load_w(B3s(s), a.img + (size_t)t * a.img_stride + a.ya_bytes, a.b3_bytes, &full3[s]);
+                if (g > 0) prefetch(g + NL + 2);
+                if (++s == NL3) { s = 0; ph ^= 1; }
+            }
+        if (!ok)
+            for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q)
+                mbar_drain(&full3[q % NL3], (q / NL3) & 1, a.err);
+    } else if (warp == 9) {
+        // ------------------------------ stage-2 MMA issuer ------------------------------
+        const uint64_t d0 = sdesc_sw128(0);
+        const int n0 = pad16c(min(a.npc, BX) * a.gs);
+        const uint32_t id0 = idesc_bf16(128, n0);
+        const bool more2 = a.nY > 1 || a.npc < BX;
+        int s = 0, yb = 0, g = 0;
+        uint32_t ph = 0, yph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k) {
+            int pl_, slab_, iy;
+            item_of(k, pl_, slab_, iy);
+            for (int t = 0; t < NT; ++t, ++g) {
+                bool w = mbar_wait(&full_bar[s], ph, a.err, 63);
+                // Y buffer yb was last converted for term g - nyb
+                if (w && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 64);
+                ok = __all_sync(0xffffffffu, w);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4) + (uint32_t)iy * 1024u, zb = d0 + (smem_u32(Zs(s)) >> 4);
+                const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
+                s2_mmas<false, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
+                if (more2)
+                    for (int i = 0; i < a.nY; ++i)
+                        for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
+                            const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                            s2_mmas<false, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs), ya + (uint32_t)i * 1024u,
+                                                zb + (uint32_t)(p0 * a.gs) * 8u, ya_atom >> 4, z_atom >> 4,
+                                                idesc_bf16(128, N));
+                        }
+                mma_commit_w(&s2bar[yb]);
+                mma_commit_w(&empty_bar[s]);
+                if (++s == NL) { s = 0; ph ^= 1; }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
+            }
+        }
+        mma_commit_w(&s3fin[0]);
+        mbar_drain(&s3fin[0], 0, a.err);
+    } else if (warp == 11) {
+        // ------------- stage-3 MMA issuer: bf16 Y tiles (shared memory) x mu_t A_t3 -------------
+        const uint64_t d0 = sdesc_sw128(0);
+        const uint32_t id3 = idesc_bf16(128, a.n3p);
+        int s3 = 0, ys = 0;
+        uint32_t ph3 = 0, yph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k) {
+            const int fb = k & 1;
+            const uint32_t tPhi = tPhi0 + (uint32_t)fb * phi_cols;
+            for (int t = 0; t < NT; ++t) {
+                bool w = mbar_wait(&ysfull[ys], yph, a.err, 65);
+                if (w) w = mbar_wait(&full3[s3], ph3, a.err, 66);
+                // phi buffer fb was last read by the epilogue of item k - 2
+                if (w && t == 0 && k >= 2) w = mbar_wait(&phifree[fb], (uint32_t)(((k - 2) >> 1) & 1), a.err, 67);
+                ok = __all_sync(0xffffffffu, w);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t b3 = d0 + (smem_u32(B3s(s3)) >> 4);
+                const uint64_t ya = d0 + (smem_u32(YSs(ys)) >> 4);
+                for (int jt = 0; jt < a.nT3; ++jt) {
+                    const uint32_t d = tPhi + (uint32_t)(jt * a.n3p);
+                    const uint64_t at = ya + (uint32_t)jt * (a.ys_tile >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < (KS3 > 0 ? KS3 : 16); ++kk) {
+                        if (KS3 == 0 && kk >= a.ks3) break;
+                        mma_ss_w<false>(d, at + (uint32_t)(kk >> 2) * (kYsAtom >> 4) + (uint32_t)(kk & 3) * 2u,
+                                        b3 + (uint32_t)(kk >> 2) * (b3_atom >> 4) + (uint32_t)(kk & 3) * 2u, id3,
+                                        (t > 0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit_w(&ysfree[ys]);
+                mma_commit_w(&empty3[s3]);
+                if (t == NT - 1) mma_commit_w(&phidone[fb]);
+                if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
+                if (++ys == NYS) { ys = 0; yph ^= 1; }
+            }
+        }
+        mma_commit_w(&s3fin[1]);
+        mbar_drain(&s3fin[1], 0, a.err);
+    } else if (warp < 8) {
+        // ---------------- converters: Y (float32, TMEM) -> bf16 stage-3 A operand ----------------
+        const int q = warp & 3, grp = warp >> 2;
+        const int kpad = 16 * a.ks3;             // K of the operand tile (zero past gs)
+        int yb = 0, ys = 0, g = 0;
+        uint32_t yph = 0, sph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t, ++g) {
+                if ((g & 1) != grp) {            // the other group's term: advance the rings only
+                    if (++yb == NYB) { yb = 0; yph ^= 1; }
+                    if (++ys == NYS) { ys = 0; sph ^= 1; }
+                    continue;
+                }
+                bool w = mbar_wait(&s2bar[yb], yph, a.err, 68);
+                if (w && g >= NYS) w = mbar_wait(&ysfree[ys], sph ^ 1, a.err, 69);
+                ok = __all_sync(0xffffffffu, w);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t tY = tmem + (uint32_t)yb * a.y_cols + ((uint32_t)(q * 32) << 16);
+                uint8_t* tileb = YSs(ys);
+                const uint32_t row = (uint32_t)(q * 32 + lane);
+                for (int jt = 0; jt < a.nT3; ++jt) {
+                    const int p = jt / a.nY, i = jt - p * a.nY;
+                    const uint32_t col = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
+                    uint8_t* tile = tileb + jt * a.ys_tile;
+                    // the columns of one 64-wide atom are loaded together and waited for once:
+                    // a TMEM load round trip costs far more than the conversion itself
+                    for (int a0 = 0; a0 < kpad; a0 += 64) {
+                        uint32_t r[4][16];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (a0 + 16 * c < kpad && a0 + 16 * c < a.gs) tmem_ld16(col + a0 + 16 * c, r[c]);
+                        tmem_ld_wait();
+                        uint8_t* at = tile + (a0 >> 6) * kYsAtom;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int g0 = a0 + 16 * c;
+                            if (g0 >= kpad) break;
+                            uint32_t w8[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int c0 = g0 + 2 * e;
+                                const float lo = c0 < a.gs ? __uint_as_float(r[c][2 * e]) : 0.f;
+                                const float hi = c0 + 1 < a.gs ? __uint_as_float(r[c][2 * e + 1]) : 0.f;
+                                w8[e] = pack_bf16(lo, hi);
+                            }
+                            // bytes (g0 % 64) * 2 .. + 32 of this row of the atom
+                            const uint32_t b0 = (uint32_t)((g0 & 63) * 2);
+                            *(uint4*)(at + sw128_offset(row, b0)) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+                            *(uint4*)(at + sw128_offset(row, b0 + 16)) = make_uint4(w8[4], w8[5], w8[6], w8[7]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&ybar[yb]);
+                    mbar_arrive(&ysfull[ys]);
+                }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
+                if (++ys == NYS) { ys = 0; sph ^= 1; }
+            }
+    } else {
+        // ---------------- epilogue warps 12-15: phi straight from TMEM ----------------
+        // Each lane owns one grid row (x, y) of a tile and walks its z in chunks of 16: the
+        // orbital values come with direct 16-byte loads (one 64-byte row segment per lane and
+        // orbital, all issued before any is used) and W is updated with 16-byte vector atomics,
+        // so no chunk waits on a shared-memory round trip.
+        const int q = warp - 12;
+        const long N3 = (long)a.n1 * a.n2 * a.n3;
+        for (int k = 0; k < nmine; ++k) {
+            const int fb = k & 1;
+            // on an error every later wait returns at once; the four warps still meet at the
+            // named barrier below once per item
+            const bool live = mbar_wait_idle(&phidone[fb], (uint32_t)((k >> 1) & 1), a.err, 70);
+            tc_fence_after();
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
+            const int x0 = slab * BX;
+            const PairRec rec = a.recs[a.p0 + pl];
+            const uint32_t tPhi = tPhi0 + (uint32_t)fb * phi_cols + ((uint32_t)(q * 32) << 16);
+            double e = 0.0;
+            const bool en = (a.flags & EPI_ENERGY) != 0;
+            const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0;
+            const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
+            const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
+            const float* mul0 = need0 ? a.MUL0 + (long)rec.m0 * N3 : nullptr;
+            const float* mul1 = need1 ? a.MUL1 + (long)rec.m1 * N3 : nullptr;
+            float* out0 = o0 ? a.OUT0 + (long)rec.o0 * N3 : nullptr;
+            float* out1 = o1 ? a.OUT1 + (long)rec.o1 * N3 : nullptr;
+            for (int jt = 0; jt < a.nT3 && live; ++jt) {
+                const int p = jt / a.nY, x = x0 + p, y = (iy + jt - p * a.nY) * 128 + q * 32 + lane;
+                // the whole warp takes part in the TMEM loads; rows past the grid skip the rest
+                const bool rowin = x < a.n1 && y < a.n2 && (need0 || need1);
+                const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
+                const long rowoff = rowin ? ((long)x * a.n2 + y) * a.n3 : 0;
+                for (int zc = 0; zc < a.n3; zc += 16) {
+                    uint32_t phr[16];
+                    tmem_ld16(tPhi + (uint32_t)(jt * a.n3p + zc), phr);
+                    float4 m0v[4], m1v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int z = zc + 4 * c;
+                        const bool zin = rowin && z < a.n3;
+                        m0v[c] = (need0 && zin) ? __ldg((const float4*)(mul0 + rowoff + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        m1v[c] = (need1 && zin) ? __ldg((const float4*)(mul1 + rowoff + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    tmem_ld_wait();
+                    if (!rowin) continue;
+                    float eb = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int z = zc + 4 * c;
+                        if (z >= a.n3) break;                    // n3 % 4 == 0
+                        const float4 phi = make_float4(__uint_as_float(phr[4 * c]), __uint_as_float(phr[4 * c + 1]),
+                                                       __uint_as_float(phr[4 * c + 2]), __uint_as_float(phr[4 * c + 3]));
+                        const float4 w3 = *(const float4*)(a.w3 + z);
+                        const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+                        float4 f = phi;
+                        if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+                        const float4 m0 = m0v[c], m1 = m1v[c];
+                        if (o0) atomicAdd((float4*)(out0 + rowoff + z), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+                        if (o1) atomicAdd((float4*)(out1 + rowoff + z), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+                        if (en && a.emul)
+                            eb += wv.x * m1.x * m0.x * phi.x + wv.y * m1.y * m0.y * phi.y + wv.z * m1.z * m0.z * phi.z +
+                                  wv.w * m1.w * m0.w * phi.w;
+                    }
+                    e += (double)eb;
+                }
+            }
+            // this item's phi has been read: the stage-3 warp may reuse the buffer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&phifree[fb]);
+            if (a.flags & EPI_ENERGY) {
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+                if (lane == 0) red[k & 1][q] = e * rec.ew;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if ((a.flags & EPI_ENERGY) && q == 0 && lane == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < 4; ++w) sum += red[k & 1][w];
+                a.epart[((long)pl * a.nslab + slab) * a.nyi + iy] = sum;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// Image of the bf16 persistent kernel's per-term operator tiles: [A_t2 tile][mu_t A_t3 (bf16)],
+// both 128-byte swizzled K-major atoms laid out as the tile loads would write them.
+template <int DUMMY>
+__global__ void __launch_bounds__(32, 1)
+    k_operand_image_b16(const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA3, ImageArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int t = blockIdx.x;
+    const int na2 = (g.ks2 + 3) / 4, na3 = (g.ks3 + 3) / 4;
+    const uint32_t ya_atom = g.ya_rows * 128u, b3_atom = (uint32_t)g.n3p * 128u;
+    uint8_t* b3 = smem + g.ya_bytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+        mbar_arrive_expect_tx(&bar, g.ya_bytes + g.b3_bytes);
+        for (int k = 0; k < na2; ++k) tma_load_3d(smem + k * ya_atom, &mA2, &bar, k * 64, 0, t);
+        for (int k = 0; k < na3; ++k) tma_load_3d(b3 + k * b3_atom, &mA3, &bar, k * 64, 0, t);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&bar, 0, g.err, 72);
+    if (!__all_sync(0xffffffffu, ok)) {
+        mbar_drain(&bar, 0, g.err);
+        return;
+    }
+    const uint4* src = (const uint4*)smem;
+    uint4* dst = (uint4*)(g.img + (size_t)t * (g.ya_bytes + g.b3_bytes));
+    for (uint32_t i = threadIdx.x; i < (g.ya_bytes + g.b3_bytes) / 16; i += 32) dst[i] = src[i];
+}
+
 }  // namespace tcc
 
 // ======================================================================================
@@ -1434,6 +1843,9 @@ __global__ void __launch_bounds__(32, 1)
 // ======================================================================================
 
 struct ConsumePlan {
+    bool tb;                 // bf16 persistent kernel (stage 3 in bf16 from shared memory)
+    int nys;                 // ... its Y operand tiles in shared memory
+    uint32_t ys_tile, ys_bytes;
     bool ts;                 // single-pass kernel (stage 3 from TMEM) instead of the converter kernel
     bool ysplit;             // single-pass, persistent only: one work item per 128-row y tile
     int nyi;                 // work items per slab (nY with ysplit, else 1)
@@ -1524,6 +1936,81 @@ static double ts_cost(const ConsumePlan& p) {
 
 static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p);
 
+// bf16 persistent plan (k_consume_tb): bx planes, nload stage-2 stages.  phi (double-buffered),
+// at least two float32 Y buffers in TMEM; the stage-3 ring, the bf16 Y tiles and the epilogue
+// boxes in shared memory.  Planes of more than 128 rows take one work item per y tile.
+static bool plan_tb(const tx_ctx* c, int bx, int nload, ConsumePlan* p) {
+    const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
+    if (c->consume_form == 1 || bx < 1 || bx > n1 || bx > 4 || nload < 2 || nload > 4) return false;
+    *p = ConsumePlan{};
+    p->ts = true;
+    p->tb = true;
+    p->bx = bx;
+    p->n2p = pad16(n2);
+    p->n3p = pad16(n3);
+    p->gs = pad8(r3);
+    if (p->n2p > 256 || p->n3p > 256 || p->gs > 256) return false;
+    const int nyf = (n2 + 127) / 128;
+    p->ysplit = nyf > 1;
+    p->nyi = p->ysplit ? nyf : 1;
+    p->nY = p->ysplit ? 1 : nyf;
+    if (p->ysplit && bx > 2) return false;
+    p->npc = std::min(bx, 256 / p->gs);
+    p->ks2 = (r2 + 15) / 16;
+    p->ks3 = (r3 + 15) / 16;
+    p->ycol_tile = 0;
+    for (int p0 = 0; p0 < bx; p0 += p->npc)
+        p->ycol_tile = std::max(p->ycol_tile, p0 * p->gs + pad16(std::min(p->npc, bx - p0) * p->gs));
+    p->y_cols = (uint32_t)(p->nY * p->ycol_tile);
+    p->nT3 = bx * p->nY;
+    const uint32_t phi = 2u * (uint32_t)(p->nT3 * p->n3p);
+    p->nyb = std::min(3, tcc::kMaxYBuf);
+    while (p->nyb >= 2 && p->nyb * p->y_cols + phi > 512) --p->nyb;
+    if (p->nyb < 2) return false;
+    const uint32_t cols = p->nyb * p->y_cols + phi;
+    p->tmem_cols = 32;
+    while (p->tmem_cols < cols) p->tmem_cols <<= 1;
+    const int na2 = (p->ks2 + 3) / 4, na3 = (p->ks3 + 3) / 4;
+    p->ya_rows = (uint32_t)p->n2p;
+    p->z_rows = (uint32_t)p->ycol_tile;
+    p->ya = (uint32_t)na2 * p->ya_rows * 128u;
+    p->zb = (uint32_t)na2 * p->z_rows * 128u;
+    p->b3 = (uint32_t)na3 * p->n3p * 128u;
+    p->load = (p->ya + p->zb + 1023) & ~1023u;
+    p->load3 = (p->b3 + 1023) & ~1023u;
+    p->ys_tile = (uint32_t)na3 * tcc::kYsAtom;
+    p->ys_bytes = (uint32_t)p->nT3 * p->ys_tile;
+    p->nload = nload;
+    p->a3_off = p->load * (uint32_t)nload;
+    auto total = [&](int nl3, int nys) {
+        return (size_t)p->a3_off + (size_t)nl3 * p->load3 + (size_t)nys * p->ys_bytes + tcc::kTbEpiBytes + 1024;
+    };
+    // the deepest stage-3 ring with two Y tiles, then a third Y tile if it still fits
+    p->nys = 2;
+    for (p->nload3 = 4; p->nload3 >= 2; --p->nload3)
+        if (total(p->nload3, 2) <= 226 * 1024) break;
+    if (p->nload3 < 2) return false;
+    if (total(p->nload3, 3) <= 226 * 1024) p->nys = 3;
+    p->smem = total(p->nload3, p->nys);
+    return true;
+}
+
+// tensor-pipe cycles per plane and term of a bf16 persistent plan (one MMA costs max(50, N / 2))
+static double tb_cost(const ConsumePlan& p) {
+    double s2 = 0;
+    for (int p0 = 0; p0 < p.bx; p0 += p.npc) s2 += std::max(50.0, pad16(std::min(p.npc, p.bx - p0) * p.gs) / 2.0);
+    const double s3 = p.bx * std::max(50.0, p.n3p / 2.0);
+    return (p.nY * p.ks2 * s2 + p.nY * p.ks3 * s3) / p.bx;
+}
+
+static bool tb_possible(const tx_ctx* c, bool tf32, bool split) {
+    if (tf32 || split || c->consume_form == 1) return false;
+    ConsumePlan p;
+    for (int bx = 1; bx <= 4; ++bx)
+        if (plan_tb(c, bx, 2, &p)) return true;
+    return false;
+}
+
 // single-pass shapes whose planes fit no TMEM plan (large n with large r) take one work item per
 // y tile in the persistent kernel (unless the one-CTA-per-item form is forced); failing that,
 // the converter kernel
@@ -1539,6 +2026,7 @@ static bool ts_ysplit(const tx_ctx* c, bool tf32) {
 static bool ts_possible(const tx_ctx* c, bool tf32) { return ts_fits(c, tf32, false) || ts_ysplit(c, tf32); }
 
 static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p) {
+    if (tb_possible(c, tf32, split)) return plan_tb(c, bx, nload, p);
     if (!split && ts_possible(c, tf32)) return plan_ts(c, tf32, bx, nload, p, ts_ysplit(c, tf32));
     return plan_cv(c, tf32, split, bx, nload, na3, p);
 }
@@ -1592,6 +2080,20 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
         if (plan_for(c, tf32, split, c->tile_bx, nl, nl > 1 ? 2 : 1, best)) return true;
     }
     double best_score = -1;
+    if (tb_possible(c, tf32, split)) {
+        // least tensor-pipe time per plane and term, then the deepest stage-2 ring
+        for (int nl = 4; nl >= 2; --nl)
+            for (int bx = 1; bx <= 4; ++bx) {
+                ConsumePlan p;
+                if (!plan_tb(c, bx, nl, &p)) continue;
+                const double score = 1.0 / tb_cost(p) * (0.9 + 0.03 * nl);
+                if (score > best_score * 1.0001) {
+                    best_score = score;
+                    *best = p;
+                }
+            }
+        return best_score > 0;
+    }
     if (!split && ts_possible(c, tf32)) {
         const bool ysplit = ts_ysplit(c, tf32);
         // least tensor-pipe time per plane and term, then the deepest load pipeline
@@ -1715,20 +2217,54 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
     const bool split = c->prec == TX_PREC_TF32X3 || c->prec == TX_PREC_BF16X3;
     ConsumePlan p;
     if (!choose_plan(c, tf32, split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
-    const TpSplit t = p.ts ? tp_split(c, p, false, false) : TpSplit{};
-    const int v[12] = {t.on ? 3 : (p.ts ? 2 : 1),
+    const TpSplit t = (p.ts && !p.tb) ? tp_split(c, p, false, false) : TpSplit{};
+    const int v[12] = {p.tb ? 4 : (t.on ? 3 : (p.ts ? 2 : 1)),
                        p.bx,
                        t.on ? t.nl1 : p.nload,
                        p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
                        p.ts ? p.nyb : 0,
                        (int)p.tmem_cols,
                        (int)(t.on ? t.smem : p.smem),
-                       t.on ? tcc::kThreadsTp : (p.ts ? tcc::kThreadsTs : tcc::kThreads),
+                       p.tb ? tcc::kThreadsTb : (t.on ? tcc::kThreadsTp : (p.ts ? tcc::kThreadsTs : tcc::kThreads)),
                        p.ks2,
                        p.ks3,
                        p.n3p,
                        (c->n[0] + p.bx - 1) / p.bx * (p.ts ? p.nyi : 1)};
     for (int i = 0; i < nout && i < 12; ++i) out[i] = v[i];
+    return TX_OK;
+}
+
+// operator image of the bf16 persistent kernel: [A_t2 tile][mu_t A_t3 tile], bf16, per term
+static int build_image_tb(tx_ctx* c, cudaStream_t s) {
+    TcOperands* op = c->tc;
+    ConsumePlan p;
+    bool found = false;
+    for (int bx = 1; bx <= 4 && !found; ++bx) found = plan_tb(c, bx, 2, &p);
+    if (!found) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no bf16 expansion plan");
+    const int n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T;
+    op->img_stride = p.ya + p.b3;
+    if (cudaMalloc(&op->img, (size_t)T * op->img_stride) != cudaSuccess) {
+        cudaGetLastError();
+        op->img = nullptr;
+        return fail(TX_ERR_OOM, "expansion operator image");
+    }
+    CUtensorMap mA2, mA3;
+    const int l2 = ldk(r2, 2), l3 = ldk(r3, 2);
+    TX_TRY(make_map(&mA2, op->st.A2, 2, l2, n2, T, l2, (uint64_t)n2 * l2, 64, (uint32_t)p.n2p));
+    TX_TRY(make_map(&mA3, op->st.A3, 2, l3, n3, T, l3, (uint64_t)n3 * l3, 64, (uint32_t)p.n3p));
+    tcc::ImageArgs g{};
+    g.ks2 = p.ks2;
+    g.ks3 = p.ks3;
+    g.n3p = p.n3p;
+    g.ya_rows = p.ya_rows;
+    g.ya_bytes = p.ya;
+    g.b3_bytes = p.b3;
+    g.img = (uint8_t*)op->img;
+    g.err = c->d_err;
+    const int smem = (int)op->img_stride + 1024;
+    cudaFuncSetAttribute(tcc::k_operand_image_b16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    tcc::k_operand_image_b16<0><<<(unsigned)T, 32, smem, s>>>(mA2, mA3, g);
+    TX_LAUNCHED();
     return TX_OK;
 }
 
@@ -1740,6 +2276,7 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
         op->img = nullptr;
     }
     ConsumePlan p;
+    if (tb_possible(c, op->tf32, op->split)) return build_image_tb(c, s);
     if (op->split || !ts_possible(c, op->tf32)) return TX_OK;
     const bool ysplit = ts_ysplit(c, op->tf32);
     for (int nl = 2; nl <= tcc::kMaxLoad; ++nl)
@@ -1843,6 +2380,35 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         TX_TRY(orb_map(&em.sb, SB, cnt.sb));
         TX_TRY(orb_map(&em.o0, OUT0, cnt.out0));
         TX_TRY(orb_map(&em.o1, OUT1, cnt.out1));
+        if (p.tb) {
+            if ((flags & EPI_ENERGY) && !a.emul)
+                return fail(TX_ERR_UNSUPPORTED_SHAPE, "bf16 expansion: energy sums need the symmetric pair table");
+            a.nload3 = p.nload3;
+            a.load3_bytes = p.load3;
+            a.nys = p.nys;
+            a.ys_tile = p.ys_tile;
+            a.ys_bytes = p.ys_bytes;
+            a.ys_off = p.a3_off + (uint32_t)p.nload3 * p.load3;
+            a.epi_off = a.ys_off + (uint32_t)p.nys * p.ys_bytes;
+            a.ks3 = p.ks3;
+            a.nslab = (int)grid.x;
+            a.nyi = p.nyi;
+            a.nitems = (int)grid.x * np * p.nyi;
+            int dev = 0, nsm = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            using KernTb = void (*)(const CUtensorMap, const tcc::EpiMaps, tcc::ConsumeArgs);
+            KernTb kern = tcc::k_consume_tb<0, 0>;
+            if (p.ks2 == 2 && p.ks3 == 2) kern = tcc::k_consume_tb<2, 2>;
+            if (p.ks2 == 3 && p.ks3 == 3) kern = tcc::k_consume_tb<3, 3>;
+            if (p.ks2 == 4 && p.ks3 == 4) kern = tcc::k_consume_tb<4, 4>;
+            const int ps = prof_begin("tc_consume", s);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+            kern<<<dim3((unsigned)std::min(a.nitems, nsm)), tcc::kThreadsTb, p.smem, s>>>(mZ, em, a);
+            prof_end(ps, s);
+            TX_LAUNCHED();
+            return TX_OK;
+        }
         if (8 * tcc::kEpiWarpBytes + 1024 > p.smem) return fail(TX_ERR_UNSUPPORTED_SHAPE, "expansion epilogue buffers");
         const TpSplit tps = tp_split(c, p, (flags & EPI_ENERGY) != 0, a.emul != 0);
         const bool tp = tps.on;

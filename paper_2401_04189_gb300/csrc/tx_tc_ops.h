@@ -23,6 +23,8 @@ struct TcStatic {
     void* A2;    // [T][n2][ld(r2)]  rows y, K = beta         (expansion, mode 2)
     void* A3;    // [T][n3][ld(r3)]  rows z, K = gamma, mu_t folded in (expansion, mode 3)
     void* A3f;   // the same in float32 rounded to TF32 (single-pass precisions; == A3 for tf32)
+    void* A3T;   // [T][r3][ld(n3)]  rows gamma, K = z, mu_t folded in (adjoint, mode 3)
+    void* A2T;   // [T][r2][ld(n2)]  rows beta,  K = y        (adjoint, mode 2)
     size_t off_lo;   // byte offset from each hi array to its lo copy (3-pass precisions)
 };
 
@@ -46,8 +48,10 @@ struct TcScratch {
 };
 TcScratch tc_scratch(const tx_ctx* c);
 
+// S1 = (SA * SB (* w)) x3 B^T with B the operand U3^T (forward projection, Bhi NULL) or a term's
+// mu_t A_t3^T (the adjoint's first mode)
 int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
-                     int nB, int flags, void* S1, cudaStream_t s);
+                     int nB, int flags, void* S1, cudaStream_t s, const void* Bhi = nullptr);
 int tc_build_operand_image(tx_ctx* c, cudaStream_t s);
 // orbital counts of the arrays the expansion epilogue reads and writes (bounds of its tensors)
 struct OrbCounts {

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kP3Threads, 1)
 }  // namespace tcp
 
 int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const float* SA, int nA, const float* SB,
-                     int nB, int flags, void* S1, cudaStream_t s) {
+                     int nB, int flags, void* S1, cudaStream_t s, const void* Bhi) {
     const TcOperands* op = c->tc;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r3 = c->r[2];
     const TcScratch sc = tc_scratch(c);
@@ -467,9 +467,10 @@ int tc_project_mode3(const tx_ctx* c, const PairRec* recs, int p0, int np, const
     TX_TRY(make_map_f32_plain(&mA, SA, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nA, (uint32_t)ZB, 128));
     TX_TRY(make_map_f32_plain(&mB, SB, (uint64_t)n3, (uint64_t)nrows, (uint64_t)nB, (uint32_t)ZB, 128));
     const int eb = op->esize;
-    TX_TRY(make_map(&mU, op->st.U3T, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB, (uint32_t)a.N3p));
+    const void* Bop = Bhi ? Bhi : op->st.U3T;
+    TX_TRY(make_map(&mU, Bop, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB, (uint32_t)a.N3p));
     if (op->split)
-        TX_TRY(make_map(&mUlo, (const char*)op->st.U3T + op->st.off_lo, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB,
+        TX_TRY(make_map(&mUlo, (const char*)Bop + op->st.off_lo, eb, ldk(n3, eb), r3, 1, ldk(n3, eb), 0, (uint32_t)ZB,
                         (uint32_t)a.N3p));
     else
         mUlo = mU;

@@ -103,3 +103,15 @@ def test_calls_on_null_context_are_rejected(L):
     assert L.tx_set_precision(None, 0, None) == -8
     L.tx_destroy(None)                     # no-op
     assert L.tx_workspace_bytes(None) == 0
+
+
+def test_new_entry_points_reject_a_null_context(L):
+    """The ACE, energy-share, wait-limit and wait self-test entry points validate their context on
+    the host before anything else (no device is touched)."""
+    P_ = ctypes.c_void_p
+    assert L.tx_ace_projectors(None, P_(0), 1, P_(0), P_(0), P_(0), P_(0)) == -8
+    assert L.tx_ace_apply(None, P_(0), 1, P_(0), 1, P_(0), P_(0)) == -8
+    assert L.tx_exchange_energy_from_w(None, P_(0), P_(0), 1, P_(0), P_(0)) == -8
+    assert L.tx_set_wait_limit(None, 0) == -8
+    assert L.tx_selftest_wait(None, 1, P_(0)) == -8
+    assert L.tx_status_string(-11).decode() == "TX_ERR_NOT_DEFINITE"

@@ -21,18 +21,17 @@ def pad16(v):
     return (v + 15) // 16 * 16
 
 
-def test_pt_shaped_bf16_plan_matches_the_profiled_launch():
-    """96^3, rank 40, 40 terms, bf16: the persistent kernel with 384 threads and 213 KiB of
-    dynamic shared memory, as ncu recorded for the bench kernel (152 CTAs x 384 threads,
-    213 KiB); 2 planes per item, so 48 items per pair (1,728 items for 36 pairs)."""
+def test_pt_shaped_bf16_plan():
+    """96^3, rank 40, 40 terms, bf16: the bf16 persistent kernel (stage 3 in bf16 as well) with
+    512 threads, one plane per item (96 items per pair): phi double-buffered (2 x 96 TMEM columns)
+    and three float32 Y buffers of 48 columns; the one-CTA-per-item form takes the TF32 stage 3."""
     d = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16")
-    assert d["kernel"] == "persistent"
-    assert (d["threads"], d["smem_bytes"]) == (384, 213 * 1024)
-    assert (d["planes"], d["items_per_pair"]) == (2, 48)
-    assert (d["ybuffers"], d["tmem_cols"]) == (4, 512)       # 4 x 80 Y columns + 2 x 96 phi columns
-    assert (d["ksteps2"], d["ksteps3"]) == (3, 5)            # bf16 K = 16 per step (40 -> 48); tf32 K = 8
+    assert d["kernel"] == "persistent_bf16" and d["threads"] == 512
+    assert (d["planes"], d["items_per_pair"]) == (1, 96)
+    assert (d["ybuffers"], d["tmem_cols"]) == (3, 512)       # 3 x 48 Y columns + 2 x 96 phi columns
+    assert (d["ksteps2"], d["ksteps3"]) == (3, 3)            # bf16 K = 16 per step (40 -> 48) in both stages
     one = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16", form=1)
-    assert one["kernel"] == "per_item" and one["threads"] == 352
+    assert one["kernel"] == "per_item" and one["threads"] == 352 and one["ksteps3"] == 5   # TF32: K = 8
 
 
 def test_split_precisions_use_the_converter_kernel():
@@ -47,12 +46,13 @@ def test_split_precisions_use_the_converter_kernel():
 
 
 def test_tio2_shaped_bf16_plan_takes_one_y_tile_per_item():
-    """160^3, rank 64, 45 terms, bf16: a whole plane (two y tiles) would need 576 TMEM columns, so
-    the persistent kernel takes one item per (pair, plane, y tile): phi 160 + four Y buffers of
-    64 columns; the one-CTA-per-item form (form 1) falls back to the converter kernel."""
+    """160^3, rank 64, 45 terms, bf16: a whole plane (two y tiles) does not fit TMEM, so the bf16
+    persistent kernel takes one item per (pair, plane, y tile): phi 2 x 160 columns (double
+    buffer) + three float32 Y buffers of 64; the one-CTA-per-item form (form 1) falls back to the
+    converter kernel."""
     d = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16")
-    assert d["kernel"] == "persistent" and d["planes"] == 1 and d["items_per_pair"] == 320
-    assert d["ybuffers"] == 4 and d["tmem_cols"] == 512
+    assert d["kernel"] == "persistent_bf16" and d["planes"] == 1 and d["items_per_pair"] == 320
+    assert d["ybuffers"] == 3 and d["tmem_cols"] == 512
     assert d["stages2"] >= 2 and d["stages3"] >= 2
     assert P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=1)["kernel"] == "converter"
 
@@ -83,7 +83,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
         yi = d["items_per_pair"] // slabs       # work items per slab: 1, or one per 128-row y tile
         assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
         if yi > 1:
-            assert d["kernel"] == "persistent" and form == 0, key
+            assert d["kernel"] in ("persistent", "persistent_bf16") and form == 0, key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -92,6 +92,11 @@ def test_every_plan_respects_the_hardware_limits(prec):
             assert d["ksteps3"] == -(-rr[2] // mk), key
             continue
         if d["kernel"] == "converter":          # single-pass shapes no TMEM plan holds
+            continue
+        if d["kernel"] == "persistent_bf16":
+            assert prec == "bf16" and form == 0 and d["threads"] == 512, key
+            assert d["ksteps3"] == -(-rr[2] // 16) and d["ybuffers"] >= 2 and d["stages3"] >= 2, key
+            assert d["planes"] <= (2 if yi > 1 else 4) and d["stages2"] <= 4, key
             continue
         assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
