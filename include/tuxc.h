@@ -215,17 +215,21 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
 
 /* Single-pass precisions (BF16, TF32): form of the expansion kernel (the final contraction of
  * Eq. final, fused with the Hadamard product and the sum over j).  0 (default): automatic --
- * the persistent form, in which one CTA per SM walks the (pair, x slab) work items and the
- * epilogue of one item overlaps the MMAs of the next, wherever its limits hold (at most two x
- * planes per CTA, n3 <= 96 after padding to 16, energy factors equal to the multipliers); one
- * CTA per work item elsewhere.  1: always one CTA per work item.  Both give the same result
- * up to float32 summation order.  TX_ERR_INVALID_ARG outside 0..1. */
+ * the persistent form, in which one CTA per SM walks the (pair, x slab) work items (one item per
+ * 128-row y tile where a plane has more rows) and the epilogue of one item overlaps the MMAs of
+ * the next, wherever its limits hold (at most two x planes per CTA, energy factors equal to the
+ * multipliers); one CTA per work item elsewhere.  Stage 3 reads the stage-2 output Y from TMEM
+ * as a TF32 operand.  1: always one CTA per work item.  2 (bf16 only): a persistent form in which
+ * converter warps round Y to bf16 into shared memory so that stage 3 also runs as bf16 (measured
+ * slower than form 0 on the Pt- and TiO2-shaped blocks: the extra hop lengthens the per-term
+ * chain of barriers).  All forms give the same result up to float32 summation order (form 2 up to
+ * the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..2. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
 /* Host-only description of the expansion kernel (the final contraction of Eq. final with the
  * Hadamard product and the sum over j, the dominant kernel) that tx_exchange_apply and
  * tx_exchange_apply_energy launch for a context of this shape, precision and expansion form
- * (0 or 1, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
+ * (0, 1 or 2, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
  * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 12)
  * values to out:
  *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
@@ -234,9 +238,10 @@ int tx_set_expansion_form(tx_ctx* ctx, int form);
  *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
- *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs)
+ *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs, times y
+ *   tiles where an item covers one y tile)
  * For the float32 precision every value is 0.  Returns TX_OK; TX_ERR_INVALID_ARG for NULL
- * arrays, nout < 1, T < 1 or a form outside 0..1; TX_ERR_SHAPE for sizes outside
+ * arrays, nout < 1, T < 1 or a form outside 0..2; TX_ERR_SHAPE for sizes outside
  * 2 <= n_d <= 4096, 1 <= r_d <= n_d; TX_ERR_UNSUPPORTED_PRECISION; TX_ERR_UNSUPPORTED_SHAPE
  * where tx_set_precision would refuse the shape. */
 int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out, int nout);

@@ -456,7 +456,8 @@ def tx_set_accumulation_chunk(ctx, terms):
 
 
 def tx_set_expansion_form(ctx, form):
-    """Single-pass precisions: 0 = automatic (persistent expansion kernel where it applies, default), 1 = one CTA per item."""
+    """Single-pass precisions: 0 = automatic (persistent expansion kernel where it applies, default),
+    1 = one CTA per item, 2 = persistent with stage 3 in bf16 (bf16 only)."""
     _check(lib().tx_set_expansion_form(ctx.handle, int(form)), "tx_set_expansion_form")
 
 

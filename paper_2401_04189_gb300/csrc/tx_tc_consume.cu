@@ -1065,7 +1065,7 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
 // stage-3 producer and Z prefetches, 11 stage-3 MMAs of every plane.  Used when every epilogue
 // warp holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
 constexpr int kTpMaxZ = 96;                           // phi registers per epilogue lane
-constexpr uint32_t kTpEpiBytes = 8 * 2 * kEpiBox;     // two 32 x 32 boxes per epilogue warp
+constexpr uint32_t kTpEpiBytes = 0;                   // the epilogue reads the orbitals directly
 
 template <bool S2TF32, int KS2, int KS3>
 __global__ void __launch_bounds__(kThreadsTp, 1)
@@ -1276,9 +1276,6 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         const int jt = csplit ? 0 : h;
         const int cbase = csplit ? h : 0, cstep = csplit ? 2 : 1;
         auto chunk_of = [&](int j) { return cbase + cstep * j; };   // global 32-column chunk
-        uint8_t* b0 = smem + a.epi_off + warp * 2 * kEpiBox;
-        uint8_t* b1 = b0 + kEpiBox;
-        uint32_t eph = 0;
         for (int k = 0; k < nmine; ++k) {
             // on an error every later wait returns at once; the warps still meet at the named
             // barrier below once per item, so none of them is left waiting there
@@ -1312,57 +1309,51 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
             const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
             if (has && x < a.n1 && y0 < a.n2 && (need0 || need1)) {
+                // each lane walks its own grid row: the orbital values come with direct 16-byte
+                // loads (a 64-byte row segment per chunk and orbital, all issued before use) and W
+                // is updated with 16-byte vector atomics, so no chunk waits on a shared-memory
+                // round trip and the pipeline keeps the shared memory for deeper operand rings
+                const long N3 = (long)a.n1 * a.n2 * a.n3;
                 const int y = y0 + lane;
                 const bool rowin = y < a.n2;
                 const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
-                const int nbx = (need0 ? 1 : 0) + (need1 ? 1 : 0);
-                uint8_t* s0 = b0;
-                uint8_t* s1 = need0 ? b1 : b0;
+                const long rowoff = rowin ? ((long)x * a.n2 + y) * a.n3 : 0;
+                const float* mul0 = need0 ? a.MUL0 + (long)rec.m0 * N3 + rowoff : nullptr;
+                const float* mul1 = need1 ? a.MUL1 + (long)rec.m1 * N3 + rowoff : nullptr;
+                float* out0 = o0 ? a.OUT0 + (long)rec.o0 * N3 + rowoff : nullptr;
+                float* out1 = o1 ? a.OUT1 + (long)rec.o1 * N3 + rowoff : nullptr;
 #pragma unroll
-                for (int ch = 0; ch < kTpMaxZ / 32; ++ch) {
-                    const int zc = 32 * chunk_of(ch);
+                for (int h16 = 0; h16 < kTpMaxZ / 16; ++h16) {
+                    const int zc = 32 * chunk_of(h16 >> 1) + 16 * (h16 & 1);
                     if (zc >= a.n3) break;
-                    if (lane == 0) {
-                        mbar_arrive_expect_tx(&ebar[warp], (uint32_t)nbx * kEpiBox);
-                        if (need0) tma_load_3d(s0, &em.m0, &ebar[warp], zc, y0, rec.m0 * a.n1 + x);
-                        if (need1) tma_load_3d(s1, &em.m1, &ebar[warp], zc, y0, rec.m1 * a.n1 + x);
+                    if (!rowin) continue;
+                    float4 m0v[4], m1v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int z = zc + 4 * c;
+                        m0v[c] = (need0 && z < a.n3) ? __ldg((const float4*)(mul0 + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        m1v[c] = (need1 && z < a.n3) ? __ldg((const float4*)(mul1 + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    const bool w = mbar_wait(&ebar[warp], eph, a.err, 49);
-                    eph ^= 1;
-                    if (!__all_sync(0xffffffffu, w)) break;
                     float eb = 0.f;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
+                    for (int c = 0; c < 4; ++c) {
                         const int z = zc + 4 * c;
-                        const uint32_t off = (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4);
-                        float4 phi = make_float4(__uint_as_float(phr[32 * ch + 4 * c]), __uint_as_float(phr[32 * ch + 4 * c + 1]),
-                                                 __uint_as_float(phr[32 * ch + 4 * c + 2]), __uint_as_float(phr[32 * ch + 4 * c + 3]));
-                        if (z >= a.n3p) phi = make_float4(0.f, 0.f, 0.f, 0.f);     // registers past the tile
-                        const float4 w3 = (rowin && z < a.n3) ? *(const float4*)(a.w3 + z) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (z >= a.n3) break;                    // n3 % 4 == 0
+                        const int r0 = 16 * h16 + 4 * c;
+                        const float4 phi = make_float4(__uint_as_float(phr[r0]), __uint_as_float(phr[r0 + 1]),
+                                                       __uint_as_float(phr[r0 + 2]), __uint_as_float(phr[r0 + 3]));
+                        const float4 w3 = *(const float4*)(a.w3 + z);
                         const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
                         float4 f = phi;
                         if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
-                        const float4 m0 = need0 ? *(const float4*)(s0 + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 m1 = need1 ? *(const float4*)(s1 + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (o0) *(float4*)(s0 + off) = make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w);
-                        if (o1) *(float4*)(s1 + off) = make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w);
-                        if (en && a.emul && rowin && z < a.n3)
+                        const float4 m0 = m0v[c], m1 = m1v[c];
+                        if (o0) atomicAdd((float4*)(out0 + z), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+                        if (o1) atomicAdd((float4*)(out1 + z), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+                        if (en && a.emul)
                             eb += wv.x * m1.x * m0.x * phi.x + wv.y * m1.y * m0.y * phi.y + wv.z * m1.z * m0.z * phi.z +
                                   wv.w * m1.w * m0.w * phi.w;
                     }
                     e += (double)eb;
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (o0 || o1) {
-                            if (o0) tma_reduce_add_3d(&em.o0, s0, zc, y0, rec.o0 * a.n1 + x);
-                            if (o1) tma_reduce_add_3d(&em.o1, s1, zc, y0, rec.o1 * a.n1 + x);
-                            bulk_commit();
-                        }
-                        // the next chunk reloads these buffers
-                        bulk_wait_read0();
-                    }
-                    __syncwarp();
                 }
             }
             if (a.flags & EPI_ENERGY) {
@@ -1377,8 +1368,6 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 a.epart[((long)pl * a.nslab + slab) * a.nyi + iy] = sum;
             }
         }
-        if (lane == 0) bulk_wait_all();
-        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -1941,7 +1930,7 @@ static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, i
 // boxes in shared memory.  Planes of more than 128 rows take one work item per y tile.
 static bool plan_tb(const tx_ctx* c, int bx, int nload, ConsumePlan* p) {
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
-    if (c->consume_form == 1 || bx < 1 || bx > n1 || bx > 4 || nload < 2 || nload > 4) return false;
+    if (c->consume_form != 2 || bx < 1 || bx > n1 || bx > 4 || nload < 2 || nload > 4) return false;
     *p = ConsumePlan{};
     p->ts = true;
     p->tb = true;
@@ -2004,7 +1993,7 @@ static double tb_cost(const ConsumePlan& p) {
 }
 
 static bool tb_possible(const tx_ctx* c, bool tf32, bool split) {
-    if (tf32 || split || c->consume_form == 1) return false;
+    if (tf32 || split || c->consume_form != 2) return false;
     ConsumePlan p;
     for (int bx = 1; bx <= 4; ++bx)
         if (plan_tb(c, bx, 2, &p)) return true;
@@ -2193,20 +2182,28 @@ static TpSplit tp_split(const tx_ctx* c, const ConsumePlan& p, bool energy, bool
     t.on = p.ts && (c->consume_form != 1 || p.ysplit) && p.nT3 <= 2 && p.bx <= 2 && lane_cols <= tcc::kTpMaxZ &&
            p.nyb >= 2 && (!energy || emul);
     if (!t.on) return t;
-    // a stage-2 ring of at most four stages, shallower where the stage-3 ring needs the room
-    int nl3 = 1;
-    for (t.nl1 = std::min(p.nload, 4); t.nl1 >= 2; --t.nl1) {
-        t.a3_off = p.load * (uint32_t)t.nl1;
-        for (nl3 = tcc::kMaxLoad; nl3 >= 2; --nl3)
-            if ((size_t)t.a3_off + (size_t)nl3 * p.load3 + tcc::kTpEpiBytes + 1024 <= 226 * 1024) break;
-        if (nl3 >= 2) break;
-    }
-    if (t.nl1 < 2 || nl3 < 2) {
+    // the two rings as deep as shared memory allows, the shallower of the two first (a ring
+    // turns over only when the MMAs queued ahead of its stage have run and the next tile has
+    // arrived, so a shallow ring bounds the term rate); at most four stage-2 stages
+    auto fits = [&](int n1, int n3) {
+        return (size_t)p.load * n1 + (size_t)n3 * p.load3 + tcc::kTpEpiBytes + 1024 <= 226 * 1024;
+    };
+    int b1 = 0, b3 = 0;
+    for (int n1 = 2; n1 <= std::min(p.nload, 4); ++n1)
+        for (int n3 = 2; n3 <= tcc::kMaxLoad; ++n3)
+            if (fits(n1, n3) && (std::min(n1, n3) > std::min(b1, b3) ||
+                                 (std::min(n1, n3) == std::min(b1, b3) && n1 + n3 > b1 + b3))) {
+                b1 = n1;
+                b3 = n3;
+            }
+    if (b1 < 2 || b3 < 2) {
         t.on = false;
         return t;
     }
-    t.nl3 = nl3;
-    t.epi_off = t.a3_off + (uint32_t)nl3 * p.load3;
+    t.nl1 = b1;
+    t.a3_off = p.load * (uint32_t)t.nl1;
+    t.nl3 = b3;
+    t.epi_off = t.a3_off + (uint32_t)t.nl3 * p.load3;
     t.smem = (size_t)t.epi_off + tcc::kTpEpiBytes + 1024;
     return t;
 }

@@ -252,9 +252,8 @@ def test_accumulation_chunk_bounds_the_accumulator_error(prec):
 @pytest.mark.parametrize("system", ["small", "ragged", "pt8"])
 def test_expansion_forms_agree(prec, system):
     """The persistent expansion kernel (default where it applies) and the one-CTA-per-item
-    kernel give the same apply and energy (to float32 summation order for TF32; for bf16 the
-    persistent form also rounds the stage-3 operand Y to bf16 where the per-item form keeps TF32,
-    so the two agree to the bf16 tolerance), and both match the oracle."""
+    kernel give the same apply and energy (to float32 summation order), and match the oracle;
+    for bf16 the third form (stage 3 in bf16 as well) agrees with them to the bf16 tolerance."""
     P = _P()
     if system == "small":
         s = W.config_small()
@@ -264,16 +263,18 @@ def test_expansion_forms_agree(prec, system):
         s = W.config_pt(n_orb=8)
     S = O.Setup.from_system(s)
     outs, energies = [], []
-    for form in (0, 1):
+    for form in ((0, 1, 2) if prec == "bf16" else (0, 1)):
         ctx = P.Context.from_system(s, precision=prec)
         P.tx_set_expansion_form(ctx, form)
         occ = to_gpu(s.psi)
         outs.append(P.tx_exchange_apply(ctx, occ).cpu().numpy())
         energies.append(float(P.tx_exchange_energy(ctx, occ).item()))
         ctx.check_device_error()
-    agree = 1e-5 if prec == "tf32" else W_TOL[prec]
-    assert rel(outs[0], outs[1]) < agree
-    assert abs(energies[0] - energies[1]) <= agree * abs(energies[1])
+    assert rel(outs[0], outs[1]) < 1e-5
+    assert abs(energies[0] - energies[1]) <= 1e-5 * abs(energies[1])
+    if prec == "bf16":         # form 2 also rounds the stage-3 operand Y to bf16
+        assert rel(outs[2], outs[0]) < W_TOL[prec]
+        assert abs(energies[2] - energies[0]) <= E_TOL[prec] * abs(energies[0])
     if system != "pt8":
         ref = O.exchange_apply(s.psi, S)
         assert_close(outs[0], ref, prec, f"forms-{system}")
@@ -283,18 +284,17 @@ def test_expansion_forms_agree(prec, system):
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
         assert_close(outs[0][3:4], ref, prec, "forms-pt8")
     with pytest.raises(P.TuckerExchangeError):
-        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 2)
+        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 3)
 
 
-@pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent_bf16"), (64, "tf32", "converter"),
-                                              (48, "bf16", "persistent_bf16"), (48, "tf32", "per_item")])
+@pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent"), (64, "tf32", "persistent"),
+                                              (48, "bf16", "per_item"), (48, "tf32", "per_item")])
 def test_large_grid_two_y_tiles(prec, rank, kernel):
     """n = 160: two 128-row y tiles per plane.  At rank 64 (the TiO2-shaped workload) a whole
     plane's stage-2 output buffers (2 x 128 TMEM columns) and phi (2 x 160) exceed TMEM's 512
-    columns: bf16 runs the persistent kernel with one work item per y tile (phi 160 columns,
-    four 64-column Y buffers), TF32 (whose load stages are twice as large) the converter kernel;
-    at rank 48 the one-CTA-per-item kernel with stage 3 read from TMEM.  Apply and energy against
-    the oracle."""
+    columns: bf16 and TF32 run the persistent kernel with one work item per y tile (phi 160
+    columns, four 64-column Y buffers); at rank 48 the one-CTA-per-item kernel.  Apply and energy
+    against the oracle."""
     P = _P()
     assert P.tx_describe_expansion_plan((160, 160, 160), (rank,) * 3, 6, prec)["kernel"] == kernel
     s = W.config_small(n=160, n_orb=2, rank=rank, T=6, L=16.0)

@@ -22,16 +22,21 @@ def pad16(v):
 
 
 def test_pt_shaped_bf16_plan():
-    """96^3, rank 40, 40 terms, bf16: the bf16 persistent kernel (stage 3 in bf16 as well) with
-    512 threads, one plane per item (96 items per pair): phi double-buffered (2 x 96 TMEM columns)
-    and three float32 Y buffers of 48 columns; the one-CTA-per-item form takes the TF32 stage 3."""
+    """96^3, rank 40, 40 terms, bf16: the persistent kernel (384 threads) with 2 planes per item,
+    so 48 items per pair; four Y buffers of 80 TMEM columns and phi 2 x 96.  Form 1 gives the
+    one-CTA-per-item kernel, form 2 the persistent kernel with stage 3 in bf16 (512 threads, one
+    plane per item, phi double-buffered, three Y buffers of 48 columns)."""
     d = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16")
-    assert d["kernel"] == "persistent_bf16" and d["threads"] == 512
-    assert (d["planes"], d["items_per_pair"]) == (1, 96)
-    assert (d["ybuffers"], d["tmem_cols"]) == (3, 512)       # 3 x 48 Y columns + 2 x 96 phi columns
-    assert (d["ksteps2"], d["ksteps3"]) == (3, 3)            # bf16 K = 16 per step (40 -> 48) in both stages
+    assert d["kernel"] == "persistent" and d["threads"] == 384
+    assert (d["planes"], d["items_per_pair"]) == (2, 48)
+    assert (d["ybuffers"], d["tmem_cols"]) == (4, 512)       # 4 x 80 Y columns + 2 x 96 phi columns
+    assert (d["ksteps2"], d["ksteps3"]) == (3, 5)            # bf16 K = 16 per step (40 -> 48); tf32 K = 8
+    assert d["stages2"] >= 3 and d["stages3"] >= 3            # the epilogue needs no staging buffers
     one = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16", form=1)
-    assert one["kernel"] == "per_item" and one["threads"] == 352 and one["ksteps3"] == 5   # TF32: K = 8
+    assert one["kernel"] == "per_item" and one["threads"] == 352
+    b = P.tx_describe_expansion_plan((96, 96, 96), (40, 40, 40), 40, "bf16", form=2)
+    assert b["kernel"] == "persistent_bf16" and b["threads"] == 512
+    assert (b["planes"], b["items_per_pair"], b["ybuffers"]) == (1, 96, 3) and b["ksteps3"] == 3
 
 
 def test_split_precisions_use_the_converter_kernel():
@@ -46,15 +51,16 @@ def test_split_precisions_use_the_converter_kernel():
 
 
 def test_tio2_shaped_bf16_plan_takes_one_y_tile_per_item():
-    """160^3, rank 64, 45 terms, bf16: a whole plane (two y tiles) does not fit TMEM, so the bf16
-    persistent kernel takes one item per (pair, plane, y tile): phi 2 x 160 columns (double
-    buffer) + three float32 Y buffers of 64; the one-CTA-per-item form (form 1) falls back to the
-    converter kernel."""
+    """160^3, rank 64, 45 terms, bf16: a whole plane (two y tiles) would need 576 TMEM columns, so
+    the persistent kernel takes one item per (pair, plane, y tile): phi 160 + four Y buffers of
+    64 columns; the one-CTA-per-item form (form 1) falls back to the converter kernel."""
     d = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16")
-    assert d["kernel"] == "persistent_bf16" and d["planes"] == 1 and d["items_per_pair"] == 320
-    assert d["ybuffers"] == 3 and d["tmem_cols"] == 512
+    assert d["kernel"] == "persistent" and d["planes"] == 1 and d["items_per_pair"] == 320
+    assert d["ybuffers"] == 4 and d["tmem_cols"] == 512
     assert d["stages2"] >= 2 and d["stages3"] >= 2
     assert P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=1)["kernel"] == "converter"
+    b = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=2)
+    assert b["kernel"] == "persistent_bf16" and b["items_per_pair"] == 320
 
 
 SIZES = [(16, 16, 16), (20, 27, 36), (32, 32, 32), (48, 64, 80), (64, 64, 64), (96, 96, 96), (112, 112, 112),
@@ -68,7 +74,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
     split = prec.endswith("x3")
     mk = 8 if tf32 else 16
     planned = 0
-    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1)):
+    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2)):
         rr = tuple(min(r, v) for v in n)
         try:
             d = P.tx_describe_expansion_plan(n, rr, T, prec, form)
@@ -83,7 +89,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
         yi = d["items_per_pair"] // slabs       # work items per slab: 1, or one per 128-row y tile
         assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
         if yi > 1:
-            assert d["kernel"] in ("persistent", "persistent_bf16") and form == 0, key
+            assert d["kernel"] in ("persistent", "persistent_bf16") and form in (0, 2), key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -94,14 +100,14 @@ def test_every_plan_respects_the_hardware_limits(prec):
         if d["kernel"] == "converter":          # single-pass shapes no TMEM plan holds
             continue
         if d["kernel"] == "persistent_bf16":
-            assert prec == "bf16" and form == 0 and d["threads"] == 512, key
+            assert prec == "bf16" and form == 2 and d["threads"] == 512, key
             assert d["ksteps3"] == -(-rr[2] // 16) and d["ybuffers"] >= 2 and d["stages3"] >= 2, key
             assert d["planes"] <= (2 if yi > 1 else 4) and d["stages2"] <= 4, key
             continue
         assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
         if d["kernel"] == "persistent":
-            assert form == 0 and d["threads"] == 384, key
+            assert form in (0, 2) and d["threads"] == 384, key
             assert d["planes"] <= 2 and d["stages2"] <= 4, key
             tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
             assert tiles <= 2, key                                  # at most one phi tile per epilogue warp
@@ -121,7 +127,7 @@ def test_shapes_the_tensor_cores_cannot_take_are_refused():
         P.tx_describe_expansion_plan((12, 13, 300), (3, 4, 5), 3, "fp32")    # float32 kernels: n3 <= 256
     assert ei.value.status == -9
     for bad, status in [(((1, 8, 8), (1, 1, 1), 3, "bf16", 0), -2), (((8, 8, 8), (9, 1, 1), 3, "bf16", 0), -2),
-                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 2), -1)]:
+                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 3), -1)]:
         with pytest.raises(P.TuckerExchangeError) as ei:
             P.tx_describe_expansion_plan(*bad)
         assert ei.value.status == status, bad
