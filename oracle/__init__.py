@@ -28,6 +28,13 @@ L = sum_t mu_t (x)_d (A_td U_d^T), so that phi_ij = L rho_ij:
     grad_tgt_k   = - sum_j psi_j * L^T(Wbar_k * psi_j)
     grad_occ_j   = - sum_k Wbar_k * phi_kj - sum_k psi_k * L^T(Wbar_k * psi_j)
 
+A second set-up variant follows Eqs. quadVal and discInteg with finite-element quadrature: the
+1-D field is interpolated by Lagrange elements of order p on the nodes (elements of p + 1
+consecutive nodes sharing their end nodes), and each 1-D convolution integral is evaluated by
+Gauss-Legendre quadrature inside every element:
+  C_td[a,b] = sum_e sum_q J_e w_q N_b(x_q) exp(-theta_t (x_a - x_q)^2)
+(conv_matrix_fe; Setup(..., quadrature=("fe", p, points))).
+
 The adaptively compressed exchange operator built from W (section "ACE implementation",
 Eqs. eta, ace1): M_ij = <psi_i, W_j>_w, M = -L L^T, xi_k = sum_i W_i (L^-1)_ki and
 V_ACE psi = - sum_k xi_k <xi_k, psi>_w (M symmetrised first where a truncated rank leaves it
@@ -46,7 +53,8 @@ __all__ = [
     "apply_L", "apply_LT", "pair_potential", "exchange_apply", "exchange_energy",
     "exchange_energy_grad", "exchange_apply_vjp", "ace_projectors", "ace_apply",
     "direct_gaussian_kernel_potential", "direct_coulomb_potential",
-    "gaussian_charge_potential", "gaussian_kernel_charge_potential",
+    "gaussian_charge_potential", "gaussian_kernel_charge_potential", "conv_matrix_fe",
+    "conv_matrix_p1_exact",
 ]
 
 
@@ -62,25 +70,94 @@ def conv_matrix(x, w, theta):
     return np.exp(-float(theta) * d * d) * w[None, :]
 
 
+def conv_matrix_fe(x, theta, order, points):
+    """C[a, b] = integral of N_b(x') exp(-theta (x_a - x')^2) dx' (Eqs. quadVal, discInteg) with
+    N_b the Lagrange basis function of node b on elements of `order` + 1 consecutive nodes
+    (element e holds nodes order*e .. order*e + order), each element integrated by
+    Gauss-Legendre quadrature with `points` points on its interval.  len(x) - 1 must be a
+    multiple of `order`."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    p = int(order)
+    if p < 1 or (n - 1) % p:
+        raise ValueError("len(x) - 1 must be a multiple of the element order")
+    xi, wq = np.polynomial.legendre.leggauss(int(points))
+    C = np.zeros((n, n))
+    for e in range((n - 1) // p):
+        nodes = x[p * e: p * e + p + 1]
+        xl, xr = nodes[0], nodes[-1]
+        half = 0.5 * (xr - xl)
+        xq = 0.5 * (xl + xr) + half * xi                    # quadrature points in the element
+        # Lagrange basis of the element's nodes at the quadrature points: L[k, q]
+        L = np.ones((p + 1, len(xq)))
+        for k in range(p + 1):
+            for m in range(p + 1):
+                if m != k:
+                    L[k] *= (xq - nodes[m]) / (nodes[k] - nodes[m])
+        K = np.exp(-float(theta) * (x[:, None] - xq[None, :]) ** 2)   # [a, q]
+        C[:, p * e: p * e + p + 1] += (K * (half * wq)[None, :]) @ L.T
+    return C
+
+
+def conv_matrix_p1_exact(x, theta):
+    """The same integral for linear elements (order 1) in closed form: the hat function of node b
+    times the Gaussian, integrated exactly with erf on each of its two intervals."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    th = float(theta)
+    s = math.sqrt(th)
+    C = np.zeros((n, n))
+
+    def lin_gauss(xa, u0, u1):
+        # integral over [u0, u1] of (u - u0) exp(-th (xa - u)^2) du
+        erf = math.erf
+        g = 0.5 * math.sqrt(math.pi / th) * (erf(s * (u1 - xa)) - erf(s * (u0 - xa)))   # int exp
+        m = (math.exp(-th * (u0 - xa) ** 2) - math.exp(-th * (u1 - xa) ** 2)) / (2 * th)   # int (u - xa) exp
+        return m + (xa - u0) * g
+
+    for a in range(n):
+        xa = x[a]
+        for b in range(n):
+            v = 0.0
+            if b > 0:                                           # rising part on [x_{b-1}, x_b]
+                u0, u1 = x[b - 1], x[b]
+                v += lin_gauss(xa, u0, u1) / (u1 - u0)
+            if b < n - 1:                                       # falling part on [x_b, x_{b+1}]
+                u0, u1 = x[b], x[b + 1]
+                erf = math.erf
+                g = 0.5 * math.sqrt(math.pi / th) * (erf(s * (u1 - xa)) - erf(s * (u0 - xa)))
+                v += g - lin_gauss(xa, u0, u1) / (u1 - u0)
+            C[a, b] = v
+    return C
+
+
 class Setup:
     """Everything that does not depend on the orbitals: grid, weights, basis, and the
-    Gaussian-sum coefficients of 1/r, plus the derived A_td = C_td U_d."""
+    Gaussian-sum coefficients of 1/r, plus the derived A_td = C_td U_d.  quadrature: ("nodal",)
+    for the trapezoid rule on the nodes, or ("fe", order, points) for finite-element quadrature
+    (conv_matrix_fe)."""
 
-    def __init__(self, x, w, U, theta, mu):
+    def __init__(self, x, w, U, theta, mu, quadrature=("nodal",)):
         self.x = [np.asarray(v, dtype=np.float64) for v in x]
         self.w = [np.asarray(v, dtype=np.float64) for v in w]
         self.U = [np.asarray(u, dtype=np.float64) for u in U]
         self.theta = np.asarray(theta, dtype=np.float64)
         self.mu = np.asarray(mu, dtype=np.float64)
         self.T = len(self.theta)
+        self.quadrature = tuple(quadrature)
+
+        def C(d, t):
+            if self.quadrature[0] == "fe":
+                return conv_matrix_fe(self.x[d], self.theta[t], self.quadrature[1], self.quadrature[2])
+            return conv_matrix(self.x[d], self.w[d], self.theta[t])
+
         # A[t][d] = C_td U_d, an [n_d, r_d] matrix
-        self.A = [[conv_matrix(self.x[d], self.w[d], self.theta[t]) @ self.U[d] for d in range(3)]
-                  for t in range(self.T)]
+        self.A = [[C(d, t) @ self.U[d] for d in range(3)] for t in range(self.T)]
         self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]
 
     @classmethod
-    def from_system(cls, s):
-        return cls(s.x, s.w, s.U, s.theta, s.mu)
+    def from_system(cls, s, quadrature=("nodal",)):
+        return cls(s.x, s.w, s.U, s.theta, s.mu, quadrature=quadrature)
 
 
 # ----------------------------------------------------------------------------------

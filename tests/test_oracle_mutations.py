@@ -55,6 +55,15 @@ MUTATIONS = [
     ("expansion keeps only the first Gaussian term",
      "    for t in range(S.T):\n        Y = G\n",
      "    for t in range(1):\n        Y = G\n"),
+    ("FE elements stepped by order + 1 nodes instead of order",
+     "        nodes = x[p * e: p * e + p + 1]",
+     "        nodes = x[(p + 1) * e: (p + 1) * e + p + 1] if (p + 1) * e + p < len(x) else x[p * e: p * e + p + 1]"),
+    ("FE quadrature without the element Jacobian",
+     "        C[:, p * e: p * e + p + 1] += (K * (half * wq)[None, :]) @ L.T",
+     "        C[:, p * e: p * e + p + 1] += (K * wq[None, :]) @ L.T"),
+    ("FE basis function of the wrong node",
+     "                    L[k] *= (xq - nodes[m]) / (nodes[k] - nodes[m])",
+     "                    L[k] *= (xq - nodes[m]) / (nodes[m] - nodes[k])"),
     ("1-D kernel in |x - x'| instead of its square",
      "    return np.exp(-float(theta) * d * d) * w[None, :]",
      "    return np.exp(-float(theta) * np.abs(d)) * w[None, :]"),
@@ -65,8 +74,8 @@ MUTATIONS = [
      "    return np.exp(-float(theta) * d * d) * w[None, :]",
      "    return np.exp(-float(theta) * d * d) * w[:, None]"),
     ("A_td built from the transposed convolution",
-     "        self.A = [[conv_matrix(self.x[d], self.w[d], self.theta[t]) @ self.U[d] for d in range(3)]",
-     "        self.A = [[conv_matrix(self.x[d], self.w[d], self.theta[t]).T @ self.U[d] for d in range(3)]"),
+     "            return conv_matrix(self.x[d], self.w[d], self.theta[t])",
+     "            return conv_matrix(self.x[d], self.w[d], self.theta[t]).T"),
     ("projection skips mode 3",
      "    for d in range(3):\n        G = mode_product(G, U[d].T, d)",
      "    for d in range(2):\n        G = mode_product(G, U[d].T, d)"),

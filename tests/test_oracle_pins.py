@@ -390,3 +390,62 @@ def test_ace_at_truncated_rank_is_exact_up_to_the_asymmetry_of_M():
     Ms = 0.5 * (M + M.T)
     B = np.linalg.solve(Ms, M.T)
     assert _rel(V, np.tensordot(B, Wx, axes=(0, 0))) < 1e-10
+
+
+# ------------------------------------------------------------------------------------------
+# Finite-element quadrature of the 1-D convolutions (Eqs. quadVal, discInteg)
+# ------------------------------------------------------------------------------------------
+def test_fe_linear_elements_match_the_closed_form():
+    """Linear elements: Gauss-Legendre quadrature inside every element against the exact integral
+    of the hat function times the Gaussian (erf on each interval), on a non-uniform grid."""
+    rng = np.random.default_rng(11)
+    x = np.sort(np.concatenate([[-4.0, 4.0], rng.uniform(-4, 4, 15)]))
+    for th in (0.05, 0.6, 4.0):
+        C = O.conv_matrix_fe(x, th, 1, 24)
+        E = O.conv_matrix_p1_exact(x, th)
+        assert np.abs(C - E).max() < 1e-12 * np.abs(E).max(), th
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_fe_elements_reproduce_polynomials_of_their_order(order):
+    """Lagrange elements of order p interpolate x^k (k <= p) exactly, so sum_b C[a,b] x_b^k is the
+    convolution integral of x^k over the whole interval, computed here by adaptive quadrature
+    (scipy.integrate.quad) of the continuous integrand."""
+    from scipy.integrate import quad
+    x = np.linspace(-3.0, 3.0, 6 * order + 1)
+    th = 0.8
+    C = O.conv_matrix_fe(x, th, order, 20)
+    for k in range(order + 1):
+        for a in (0, len(x) // 3, len(x) - 1):
+            ref, _ = quad(lambda u: u ** k * np.exp(-th * (x[a] - u) ** 2), x[0], x[-1], epsabs=1e-14, epsrel=1e-13)
+            got = float(C[a] @ x ** k)
+            assert abs(got - ref) < 1e-11 * max(1.0, abs(ref)), (order, k, a, got, ref)
+
+
+def test_fe_quadrature_of_a_flat_kernel_gives_the_element_weights():
+    """For theta -> 0 the kernel is 1 and C[a, b] -> integral of N_b: the trapezoid weights for
+    linear elements, Simpson's 1/6, 4/6, 1/6 pattern (times the element length) for quadratic."""
+    x = np.linspace(-2.0, 2.0, 9)
+    h = x[1] - x[0]
+    C1 = O.conv_matrix_fe(x, 1e-12, 1, 8)
+    trap = np.full(9, h)
+    trap[[0, -1]] = h / 2
+    assert np.abs(C1 - trap[None, :]).max() < 1e-9
+    C2 = O.conv_matrix_fe(x, 1e-12, 2, 8)
+    simp = np.array([1, 4, 2, 4, 2, 4, 2, 4, 1]) * (2 * h) / 6
+    assert np.abs(C2 - simp[None, :]).max() < 1e-9
+
+
+def test_fe_setup_changes_only_the_convolution_matrices():
+    """A Setup with FE quadrature of linear elements on a resolved Gaussian sum gives nearly the
+    same potential as the nodal rule (both converge to the same integral) and exactly
+    conv_matrix_fe @ U for its A_td."""
+    s = W.config_small(n=16, n_orb=2, rank=6, T=3, L=4.0)
+    Sn = O.Setup.from_system(s)
+    Sf = O.Setup.from_system(s, quadrature=("fe", 1, 12))
+    for t in range(s.T):
+        for d in range(3):
+            assert np.abs(Sf.A[t][d] - O.conv_matrix_fe(s.x[d], s.theta[t], 1, 12) @ s.U[d]).max() < 1e-14
+    Wn = O.exchange_apply(s.psi, Sn)
+    Wf = O.exchange_apply(s.psi, Sf)
+    assert 0 < _rel(Wf, Wn) < 0.2
