@@ -35,6 +35,14 @@ Gauss-Legendre quadrature inside every element:
   C_td[a,b] = sum_e sum_q J_e w_q N_b(x_q) exp(-theta_t (x_a - x_q)^2)
 (conv_matrix_fe; Setup(..., quadrature=("fe", p, points))).
 
+A two-sided (Galerkin) variant of the convolution, which the paper does not describe: the
+one-sided operator C P (P = (x)_d U_d U_d^T) is not symmetric in the w inner product at a
+truncated rank.  Projecting the output too, with the w-adjoint P^* = D^-1 P D, gives
+P^* C P, whose form <sigma, P^* C P rho>_w = (U^T sigma)^T [sum_t mu_t (x)_d B_td] (U^T rho) is
+symmetric and positive semi-definite (B_td = U_d^T D_d K_td D_d U_d), so E_x <= 0 exactly and it
+is computable in core space (galerkin_core_matrices, apply_L_galerkin, exchange_apply_galerkin,
+exchange_energy_galerkin).
+
 The adaptively compressed exchange operator built from W (section "ACE implementation",
 Eqs. eta, ace1): M_ij = <psi_i, W_j>_w, M = -L L^T, xi_k = sum_i W_i (L^-1)_ki and
 V_ACE psi = - sum_k xi_k <xi_k, psi>_w (M symmetrised first where a truncated rank leaves it
@@ -54,7 +62,8 @@ __all__ = [
     "exchange_energy_grad", "exchange_apply_vjp", "ace_projectors", "ace_apply",
     "direct_gaussian_kernel_potential", "direct_coulomb_potential",
     "gaussian_charge_potential", "gaussian_kernel_charge_potential", "conv_matrix_fe",
-    "conv_matrix_p1_exact",
+    "conv_matrix_p1_exact", "galerkin_core_matrices", "galerkin_core_convolve", "apply_L_galerkin",
+    "exchange_apply_galerkin", "exchange_energy_galerkin",
 ]
 
 
@@ -264,6 +273,64 @@ def exchange_apply_vjp(psi_occ, psi_tgt, grad_out, S: Setup):
             g_tgt[k] -= occ[j] * zeta
             g_occ[j] -= Wb[k] * pair_potential(tgt[k], occ[j], S) + tgt[k] * zeta
     return g_occ, g_tgt
+
+
+# ----------------------------------------------------------------------------------
+# two-sided (Galerkin) projection of the convolution onto the Tucker basis
+# ----------------------------------------------------------------------------------
+def galerkin_core_matrices(S: Setup):
+    """B[t][d] = U_d^T D_d C_td U_d = U_d^T D_d A_td, an [r_d, r_d] matrix: the 1-D convolution
+    of Eq. final compressed onto the basis on both sides (D_d = diag(w_d)).  With the nodal
+    quadrature D_d C_td = D_d K_td D_d, so B[t][d] is symmetric and positive semi-definite."""
+    return [[S.U[d].T @ (S.w[d][:, None] * S.A[t][d]) for d in range(3)] for t in range(S.T)]
+
+
+def galerkin_core_convolve(G, S: Setup, B=None):
+    """H = sum_t mu_t G x1 B_t1 x2 B_t2 x3 B_t3 (the core-space convolution)."""
+    B = galerkin_core_matrices(S) if B is None else B
+    Hc = np.zeros_like(G)
+    for t in range(S.T):
+        Yc = G
+        for d in range(3):
+            Yc = mode_product(Yc, B[t][d], d)
+        Hc += S.mu[t] * Yc
+    return Hc
+
+
+def apply_L_galerkin(rho, S: Setup, B=None):
+    """phi = P^* C P rho, where P = (x)_d U_d U_d^T projects onto the basis, C is the separable
+    Gaussian-sum convolution and P^* = D^-1 P D is the adjoint of P in the w inner product:
+    phi = (sum_t mu_t G x_d B_td) x_d (D_d^-1 U_d) with G = rho x_d U_d^T."""
+    H = galerkin_core_convolve(project(rho, S.U), S, B)
+    for d in range(3):
+        H = mode_product(H, S.U[d] / S.w[d][:, None], d)
+    return H
+
+
+def exchange_apply_galerkin(psi_occ, S: Setup, psi_tgt=None):
+    """W_i = - sum_j psi_j * (P^* C P)(psi_i psi_j): the exchange action with the two-sided
+    projection (every ordered pair separately)."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    tgt = occ if psi_tgt is None else np.asarray(psi_tgt, dtype=np.float64)
+    B = galerkin_core_matrices(S)
+    W = np.zeros_like(tgt)
+    for i in range(tgt.shape[0]):
+        for j in range(occ.shape[0]):
+            W[i] -= occ[j] * apply_L_galerkin(tgt[i] * occ[j], S, B)
+    return W
+
+
+def exchange_energy_galerkin(psi_occ, S: Setup):
+    """E_x = - 1/2 sum_ij <G_ij, sum_t mu_t G_ij x_d B_td>, evaluated in core space: O(T r^4) per
+    pair instead of a reconstruction on the grid."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    B = galerkin_core_matrices(S)
+    E = 0.0
+    for i in range(occ.shape[0]):
+        for j in range(occ.shape[0]):
+            G = project(occ[i] * occ[j], S.U)
+            E -= 0.5 * float(np.sum(G * galerkin_core_convolve(G, S, B)))
+    return E
 
 
 # ----------------------------------------------------------------------------------

@@ -97,6 +97,18 @@ MUTATIONS = [
     ("ACE without symmetrising M",
      "    Ms = 0.5 * (M + M.T)",
      "    Ms = M"),
+    ("Galerkin reconstruction without the inverse weights",
+     "        H = mode_product(H, S.U[d] / S.w[d][:, None], d)",
+     "        H = mode_product(H, S.U[d], d)"),
+    ("Galerkin core matrices without the weights",
+     "    return [[S.U[d].T @ (S.w[d][:, None] * S.A[t][d]) for d in range(3)] for t in range(S.T)]",
+     "    return [[S.U[d].T @ S.A[t][d] for d in range(3)] for t in range(S.T)]"),
+    ("Galerkin core convolution drops mu_t",
+     "        Hc += S.mu[t] * Yc",
+     "        Hc += Yc"),
+    ("Galerkin energy without the factor 1/2",
+     "            E -= 0.5 * float(np.sum(G * galerkin_core_convolve(G, S, B)))",
+     "            E -= float(np.sum(G * galerkin_core_convolve(G, S, B)))"),
     ("quadrature weight of mode 2 on mode 3",
      "        self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]",
      "        self.w3 = self.w[0][:, None, None] * self.w[2][None, None, :] * self.w[2][None, None, :]"),

@@ -449,3 +449,89 @@ def test_fe_setup_changes_only_the_convolution_matrices():
     Wn = O.exchange_apply(s.psi, Sn)
     Wf = O.exchange_apply(s.psi, Sf)
     assert 0 < _rel(Wf, Wn) < 0.2
+
+
+# ---------------------------------------------------------------------------------
+# Two-sided (Galerkin) projection: P^* C P with P^* = D^-1 P D the w-adjoint of P
+# ---------------------------------------------------------------------------------
+def _explicit_pieces(S):
+    """The n^3 x n^3 matrices of the separable convolution and of the projection, built by
+    Kronecker products straight from the grid (independent of the oracle's mode products), and
+    the 3-D weight vector (C-order flattening: z fastest)."""
+    def kron3(m):
+        return np.kron(m[0], np.kron(m[1], m[2]))
+    K = sum(S.mu[t] * kron3([np.exp(-S.theta[t] * (S.x[d][:, None] - S.x[d][None, :]) ** 2) * S.w[d][None, :]
+                            for d in range(3)]) for t in range(S.T))
+    P = kron3([S.U[d] @ S.U[d].T for d in range(3)])
+    Dv = kron3([S.w[d][:, None] for d in range(3)]).ravel()
+    return K, P, Dv
+
+
+def test_galerkin_operator_equals_its_explicit_matrix():
+    rng = np.random.default_rng(21)
+    n, r = (4, 5, 6), (2, 3, 4)
+    S = _random_setup(rng, n, r, 3)
+    K, P, Dv = _explicit_pieces(S)
+    LG = (P @ (Dv[:, None] * (K @ P))) / Dv[:, None]          # D^-1 P D K P
+    rho = rng.standard_normal(n)
+    assert _rel(O.apply_L_galerkin(rho, S), (LG @ rho.ravel()).reshape(n)) < 1e-12
+    assert _rel(O.apply_L(rho, S), (K @ P @ rho.ravel()).reshape(n)) < 1e-12    # one-sided: K P
+
+
+def test_galerkin_at_full_rank_equals_the_one_sided_operator():
+    rng = np.random.default_rng(22)
+    n = (5, 6, 7)
+    S = _random_setup(rng, n, n, 3)              # square orthogonal U_d, not the identity
+    rho = rng.standard_normal(n)
+    assert _rel(O.apply_L_galerkin(rho, S), O.apply_L(rho, S)) < 1e-12
+
+
+def test_galerkin_form_is_symmetric_and_positive_semidefinite_at_truncated_rank():
+    """<e_k, P^* C P e_l>_w over all grid points is a symmetric positive semi-definite matrix
+    (so E_x <= 0 exactly); the one-sided form at the same rank is not symmetric."""
+    rng = np.random.default_rng(23)
+    n, r = (4, 4, 5), (2, 3, 3)
+    S = _random_setup(rng, n, r, 3)
+    _, _, Dv = _explicit_pieces(S)
+    N = int(np.prod(n))
+    E = np.eye(N)
+    LG = np.array([O.apply_L_galerkin(E[k].reshape(n), S).ravel() for k in range(N)]).T
+    L1 = np.array([O.apply_L(E[k].reshape(n), S).ravel() for k in range(N)]).T
+    MG, M1 = Dv[:, None] * LG, Dv[:, None] * L1
+    scale = np.max(np.abs(MG))
+    assert np.max(np.abs(MG - MG.T)) < 1e-12 * scale
+    assert np.min(np.linalg.eigvalsh(0.5 * (MG + MG.T))) > -1e-12 * scale
+    assert np.max(np.abs(M1 - M1.T)) > 1e-3 * np.max(np.abs(M1))
+
+
+def test_galerkin_agrees_with_the_one_sided_form_on_the_span():
+    """For sigma and rho whose mode factors lie in span(U_d), P sigma = sigma and P rho = rho,
+    so <sigma, P^* C P rho>_w = <sigma, C P rho>_w."""
+    rng = np.random.default_rng(24)
+    n, r = (6, 7, 8), (3, 3, 4)
+    S = _random_setup(rng, n, r, 4)
+    _, _, Dv = _explicit_pieces(S)
+    Dv = Dv.reshape(n)
+
+    def in_span():
+        f = [S.U[d] @ rng.standard_normal(r[d]) for d in range(3)]
+        return np.einsum("a,b,c->abc", *f)
+    sig, rho = in_span() + in_span(), in_span()
+    a = float(np.sum(Dv * sig * O.apply_L_galerkin(rho, S)))
+    b = float(np.sum(Dv * sig * O.apply_L(rho, S)))
+    assert abs(a - b) < 1e-12 * abs(b)
+
+
+def test_galerkin_energy_in_core_space_equals_the_grid_energy():
+    s = W.config_small(n=10, n_orb=3, rank=6, T=5, L=5.0)
+    S = O.Setup.from_system(s)
+    psi = s.psi.astype(np.float64)
+    Wg = O.exchange_apply_galerkin(psi, S)
+    e_grid = 0.5 * float(np.sum(S.w3[None] * psi * Wg))
+    e_core = O.exchange_energy_galerkin(psi, S)
+    assert e_core < 0
+    assert abs(e_core - e_grid) < 1e-12 * abs(e_grid)
+    # the exchange matrix <psi_a, W_b>_w is exactly symmetric and negative semi-definite
+    M = np.einsum("axyz,bxyz->ab", psi * S.w3[None], Wg)
+    assert np.max(np.abs(M - M.T)) < 1e-12 * np.max(np.abs(M))
+    assert np.max(np.linalg.eigvalsh(0.5 * (M + M.T))) < 1e-12 * np.max(np.abs(M))
