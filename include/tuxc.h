@@ -98,6 +98,39 @@ int tx_tucker_setup(tx_ctx** ctx, const int n[3],
                     int T, const double* gauss_exponents, const double* gauss_weights,
                     int precision, tx_stream_t stream);
 
+/*
+ * tx_exchange_apply_galerkin / tx_exchange_energy_galerkin -- the same calls with the convolution
+ * projected onto the Tucker basis on both sides.  The one-sided operator of Eq. final is C P,
+ * P = (x)_d U_d U_d^T; this form applies P^* C P, where P^* = D^-1 P D is the adjoint of P in the
+ * inner product weighted by the quadrature weights D:
+ *     phi_ij = (sum_t mu_t G_ij x_d B_td) x_d (D_d^-1 U_d),     B_td = U_d^T D_d A_td  (r_d x r_d)
+ *     W_i    = - sum_j psi_j * phi_ij
+ *     E_x    = - 1/2 sum_ij <G_ij, sum_t mu_t G_ij x_d B_td>     (in core space, O(T r^4) per pair)
+ * With the nodal quadrature the exchange matrix <psi_a, W_b>_w is then exactly symmetric and
+ * negative semi-definite at any rank (the one-sided form is so only at full rank).  Arguments,
+ * layouts, aliasing rules and errors are those of tx_exchange_apply / tx_exchange_energy.  Both
+ * run in float32 on the CUDA cores whatever the context's precision.
+ */
+int tx_exchange_apply_galerkin(tx_ctx* ctx, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
+                               float* out, tx_stream_t stream);
+int tx_exchange_energy_galerkin(tx_ctx* ctx, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream);
+
+/*
+ * tx_set_quadrature -- how the 1-D convolution integrals are evaluated (Eqs. quadVal, discInteg).
+ *   order 0             nodal quadrature with the context's weights (the default):
+ *                       C_td[a][b] = w_b exp(-theta_t (x_a - x_b)^2)
+ *   order p in 1..8     finite-element quadrature: the 1-D field is interpolated by Lagrange
+ *                       elements of order p (element e holds nodes p e .. p e + p; n_d - 1 must be a
+ *                       multiple of p) and every element is integrated with `points` (1..64)
+ *                       Gauss-Legendre points:
+ *                       C_td[a][b] = sum_{e holds b} sum_q J_e w_q N_b(x_q) exp(-theta_t (x_a - x_q)^2)
+ * A_td = C_td U_d is recomputed in float64 on the device (mu_t folded into mode 3) and the operand
+ * copies of the context's precision are rebuilt.  The energy and the other inner products keep
+ * the context's weights.  Synchronises the context's last stream.  TX_ERR_INVALID_ARG for an
+ * order or point count out of range, TX_ERR_SHAPE if n_d - 1 is not a multiple of the order.
+ */
+int tx_set_quadrature(tx_ctx* ctx, int order, int points, tx_stream_t stream);
+
 /* Release every device allocation of the context (after synchronising its last stream). */
 void tx_destroy(tx_ctx* ctx);
 

@@ -27,7 +27,8 @@ EXPORTED = [
     "tx_profile_read", "tx_selftest_gemm", "tx_batch_plan", "tx_batch_launch", "tx_batch_capture",
     "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
     "tx_exchange_apply_static", "tx_describe_expansion_plan", "tx_set_wait_limit", "tx_selftest_wait",
-    "tx_exchange_energy_from_w", "tx_ace_projectors", "tx_ace_apply",
+    "tx_exchange_energy_from_w", "tx_ace_projectors", "tx_ace_apply", "tx_set_quadrature",
+    "tx_exchange_apply_galerkin", "tx_exchange_energy_galerkin",
 ]
 
 
@@ -79,6 +80,10 @@ def lib():
     L.tx_set_precision.restype = _I
     L.tx_exchange_apply.argtypes = [_P, _P, _I, _P, _I, _P, _P]
     L.tx_exchange_apply.restype = _I
+    L.tx_exchange_apply_galerkin.argtypes = [_P, _P, _I, _P, _I, _P, _P]
+    L.tx_exchange_apply_galerkin.restype = _I
+    L.tx_exchange_energy_galerkin.argtypes = [_P, _P, _I, _P, _P]
+    L.tx_exchange_energy_galerkin.restype = _I
     L.tx_exchange_apply_energy.argtypes = [_P, _P, _I, _P, _P, _P]
     L.tx_exchange_apply_energy.restype = _I
     L.tx_profile_enable.argtypes = [_I]
@@ -130,6 +135,8 @@ def lib():
     L.tx_ace_projectors.restype = _I
     L.tx_ace_apply.argtypes = [_P, _P, _I, _P, _I, _P, _P]
     L.tx_ace_apply.restype = _I
+    L.tx_set_quadrature.argtypes = [_P, _I, _I, _P]
+    L.tx_set_quadrature.restype = _I
     L.tx_status_string.argtypes = [_I]
     L.tx_status_string.restype = ctypes.c_char_p
     L.tx_last_error_message.argtypes = []
@@ -205,6 +212,11 @@ class Context:
         _check(lib().tx_set_precision(self.handle, int(p), _stream(stream)), "tx_set_precision")
         self.precision = p
 
+    def set_quadrature(self, order, points=0, stream=None):
+        """1-D convolution integrals: order 0 = nodal quadrature (default); order p >= 1 =
+        Lagrange elements of order p with `points` Gauss-Legendre points per element."""
+        _check(lib().tx_set_quadrature(self.handle, int(order), int(points), _stream(stream)), "tx_set_quadrature")
+
     def set_workspace_limit(self, nbytes):
         _check(lib().tx_set_workspace_limit(self.handle, int(nbytes)), "tx_set_workspace_limit")
 
@@ -244,7 +256,7 @@ def tx_tucker_setup(x, w, U, theta, mu, precision="fp32", stream=None) -> Contex
     return Context(x, w, U, theta, mu, precision=precision, stream=stream)
 
 
-def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None):
+def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None, _fn="tx_exchange_apply"):
     """out = K psi_tgt (psi_tgt None: the occupied block itself)."""
     ctx._block(psi_occ, "psi_occ")
     n_tgt = psi_occ.shape[0] if psi_tgt is None else ctx._block(psi_tgt, "psi_tgt").shape[0]
@@ -253,10 +265,17 @@ def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None
     ctx._block(out, "out")
     if n_tgt == 0:
         return out          # no targets (an empty tensor has a NULL pointer, which the C call reads as "occupied")
-    st = lib().tx_exchange_apply(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(psi_tgt),
-                                 0 if psi_tgt is None else n_tgt, _ptr(out), _stream(stream))
-    _check(st, "tx_exchange_apply")
+    st = getattr(lib(), _fn)(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(psi_tgt),
+                             0 if psi_tgt is None else n_tgt, _ptr(out), _stream(stream))
+    _check(st, _fn)
     return out
+
+
+def tx_exchange_apply_galerkin(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None):
+    """out = K_G psi_tgt with the convolution projected onto the Tucker basis on both sides
+    (P^* C P, P^* the weighted adjoint of the projector): an exactly symmetric, negative
+    semi-definite exchange matrix at any rank."""
+    return tx_exchange_apply(ctx, psi_occ, psi_tgt, out, stream, _fn="tx_exchange_apply_galerkin")
 
 
 def tx_exchange_apply_energy(ctx: Context, psi_occ, out=None, e_out=None, stream=None):
@@ -336,14 +355,19 @@ def tx_profile_read(name):
     return int(n.value), float(ms.value)
 
 
-def tx_exchange_energy(ctx: Context, psi_occ, e_out=None, stream=None):
+def tx_exchange_energy(ctx: Context, psi_occ, e_out=None, stream=None, _fn="tx_exchange_energy"):
     """E_x as a float64 device scalar."""
     ctx._block(psi_occ, "psi_occ")
     if e_out is None:
         e_out = torch.empty((), dtype=torch.float64, device=psi_occ.device)
-    st = lib().tx_exchange_energy(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(e_out), _stream(stream))
-    _check(st, "tx_exchange_energy")
+    st = getattr(lib(), _fn)(ctx.handle, _ptr(psi_occ), psi_occ.shape[0], _ptr(e_out), _stream(stream))
+    _check(st, _fn)
     return e_out
+
+
+def tx_exchange_energy_galerkin(ctx: Context, psi_occ, e_out=None, stream=None):
+    """E_x with the two-sided projection, evaluated in core space (O(T r^4) per pair)."""
+    return tx_exchange_energy(ctx, psi_occ, e_out, stream, _fn="tx_exchange_energy_galerkin")
 
 
 def tx_exchange_energy_grad(ctx: Context, psi_occ, grad=None, e_out=None, stream=None):

@@ -423,8 +423,8 @@ static void classify_targets(const tx_ctx* c, const float* occ, int n_occ, const
     }
 }
 
-extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
-                                 float* out, tx_stream_t stream) {
+static int exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt, float* out,
+                          tx_stream_t stream, int galerkin) {
     TX_TRY(check_ctx(c));
     DeviceGuard dg;
     TX_TRY(dg.use(c->device));
@@ -450,7 +450,18 @@ extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, con
     cs.occ = psi_occ;
     cs.tgt = psi_tgt ? psi_tgt : psi_occ;
     cs.out0 = out;
+    cs.galerkin = galerkin;
     return run_call(c, cs, s);
+}
+
+extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
+                                 float* out, tx_stream_t stream) {
+    return exchange_apply(c, psi_occ, n_occ, psi_tgt, n_tgt, out, stream, 0);
+}
+
+extern "C" int tx_exchange_apply_galerkin(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
+                                          float* out, tx_stream_t stream) {
+    return exchange_apply(c, psi_occ, n_occ, psi_tgt, n_tgt, out, stream, 1);
 }
 
 extern "C" int tx_exchange_apply_energy(tx_ctx* c, const float* psi_occ, int n_occ, float* out, double* e_dev,
@@ -476,7 +487,8 @@ extern "C" int tx_exchange_apply_energy(tx_ctx* c, const float* psi_occ, int n_o
     return run_call(c, cs, s);
 }
 
-extern "C" int tx_exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream) {
+static int exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream,
+                           int galerkin) {
     TX_TRY(check_ctx(c));
     DeviceGuard dg;
     TX_TRY(dg.use(c->device));
@@ -492,7 +504,17 @@ extern "C" int tx_exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, do
     cs.n_tgt = n_occ;
     cs.occ = cs.tgt = psi_occ;
     cs.e_dev = e_dev;
+    cs.galerkin = galerkin;
     return run_call(c, cs, s);
+}
+
+extern "C" int tx_exchange_energy(tx_ctx* c, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream) {
+    return exchange_energy(c, psi_occ, n_occ, e_dev, stream, 0);
+}
+
+extern "C" int tx_exchange_energy_galerkin(tx_ctx* c, const float* psi_occ, int n_occ, double* e_dev,
+                                           tx_stream_t stream) {
+    return exchange_energy(c, psi_occ, n_occ, e_dev, stream, 1);
 }
 
 extern "C" int tx_exchange_energy_grad(tx_ctx* c, const float* psi_occ, int n_occ, float* grad, double* e_dev,
@@ -572,4 +594,23 @@ extern "C" int tx_exchange_energy_from_w(tx_ctx* c, const float* psi, const floa
     const int nblocks = (int)std::max<long>(1, std::min<long>(1024, (total + 8191) / 8192));
     TX_TRY(ensure_ebatch(c, nblocks + 1));
     return weighted_dot(c, psi, W, n, c->d_ebatch, nblocks, 0.5, e_dev, s);
+}
+
+extern "C" int tx_set_quadrature(tx_ctx* c, int order, int points, tx_stream_t stream) {
+    TX_TRY(check_ctx(c));
+    if (order < 0 || order > 8) return fail(TX_ERR_INVALID_ARG, "element order must be 0 (nodal) .. 8");
+    if (order > 0 && (points < 1 || points > 64)) return fail(TX_ERR_INVALID_ARG, "points must be 1 .. 64");
+    for (int d = 0; order > 0 && d < 3; ++d)
+        if ((c->n[d] - 1) % order)
+            return fail(TX_ERR_SHAPE, "n_" + std::to_string(d + 1) + " - 1 is not a multiple of the element order");
+    DeviceGuard dg;
+    TX_TRY(dg.use(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    TX_TRY_CUDA(cudaStreamSynchronize(c->last_stream));
+    c->last_stream = s;
+    if (order == 0) TX_TRY(setup_factor_matrices(c, s));
+    else TX_TRY(setup_factor_matrices_fe(c, order, points, s));
+    // the operand copies of the tensor-core precisions are rebuilt from the new A_td
+    if (c->prec != TX_PREC_FP32) TX_TRY(tc_prepare(c, s));
+    return TX_OK;
 }

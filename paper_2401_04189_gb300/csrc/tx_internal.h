@@ -191,6 +191,8 @@ int weighted_dot(const tx_ctx* c, const float* A, const float* B, int count, dou
 
 // setup -- tx_setup.cu
 int setup_factor_matrices(tx_ctx* c, cudaStream_t s);
+// the same with finite-element quadrature (Lagrange elements of `order`, `points` Gauss points)
+int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s);
 
 // tensor-core path -- tx_tc.cu
 int tc_prepare(tx_ctx* c, cudaStream_t s);

@@ -119,6 +119,28 @@ int simt_batch(tx_ctx* c, const CallSpec& cs, const PairRec* recs, const PairRec
     return fail(TX_ERR_INVALID_ARG, "unknown call kind");
 }
 
+// One pair batch with the two-sided projection: the float32 projection, the core-space
+// convolution, then either the core-space energy or one reconstruction with D^-1 U and the
+// Hadamard epilogue.
+int galerkin_batch(tx_ctx* c, const CallSpec& cs, const GalerkinOps& o, const PairRec* recs, int p0, int np,
+                   float* S2, float* G, float* H, float* X1, float* X2, double* epart, cudaStream_t s) {
+    const bool subset = cs.mode == PAIRS_SUBSET;
+    FieldArgs f{};
+    f.SA = subset ? cs.occ : cs.tgt;
+    f.SB = cs.occ;
+    f.MUL0 = cs.occ;
+    f.MUL1 = cs.occ;
+    f.OUT0 = cs.out0;
+    f.OUT1 = cs.out0;
+    TX_TRY(simt_project_s2(c, recs, p0, np, f, 0, S2, s));
+    TX_TRY(gemm_mode1_project(c, S2, c->f_U[0], G, np, s));
+    TX_TRY(galerkin_core(c, o, G, X1, X2, H, np, s));
+    if (cs.kind == CALL_ENERGY) return galerkin_core_dot(c, recs, p0, G, H, np, epart, s);
+    float* Z = S2;   // [np][1][n1][r3 r2]: the size of S2
+    TX_TRY(gemm_mode1_expand(c, H, o.Ut[0], 1, Z, np, s));
+    return simt_expand_consume(c, recs, p0, np, f, Z, 1, o.Ut[1], o.Ut[2], EPI_OUT, epart, s);
+}
+
 }  // namespace
 
 int simt_adjoint_mode1(const tx_ctx* c, const float* R, float* H, int np, cudaStream_t s) {
@@ -133,13 +155,19 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     const long P = pair_count(cs.mode, cs.n_occ, cs.n_tgt);
     // every call kind of a tensor-core precision runs the tensor-core kernels (the adjoint's
     // first-mode sum over the terms and its single-term expansion run in float32)
-    const bool tc = c->prec != TX_PREC_FP32;
+    // (the two-sided projection runs in float32 on the CUDA cores in every precision)
+    const bool gk = cs.galerkin != 0;
+    const bool tc = c->prec != TX_PREC_FP32 && !gk;
     const int ntables = cs.kind == CALL_VJP ? 2 : 1;
     const size_t recs_bytes = align_up(sizeof(PairRec) * (size_t)P, 256) * ntables;
+    const size_t prefix = gk ? align_up(sizeof(float) * galerkin_operator_floats(c), 256) : 0;
     size_t per_pair;
     long epp;
     SimtLayout L = simt_layout(c);
-    if (tc) {
+    if (gk) {
+        per_pair = sizeof(float) * (L.s2 + 2 * L.g + 2 * (size_t)c->T * L.g);
+        epp = cs.kind == CALL_ENERGY ? 1 : simt_expand_consume_blocks(c);
+    } else if (tc) {
         per_pair = tc_batch_bytes_per_pair(c, cs.kind);
         epp = tc_epart_per_pair(c);
     } else {
@@ -147,17 +175,19 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
         epp = simt_expand_consume_blocks(c);
     }
     per_pair += sizeof(double) * epp;
-    size_t avail = c->ws_limit > recs_bytes + 4096 ? c->ws_limit - recs_bytes - 4096 : 0;
+    size_t avail = c->ws_limit > recs_bytes + prefix + 4096 ? c->ws_limit - recs_bytes - prefix - 4096 : 0;
     long Pb = std::max<long>(1, std::min<long>(P, (long)(avail / per_pair)));
     Pb = std::min<long>(Pb, 65535 / std::max(1, c->T));   // grid.z of the per-term GEMMs is T * pairs
     const long nb = (P + Pb - 1) / Pb;
     const size_t batch_bytes = align_up((size_t)Pb * per_pair, 256) + 4096;
-    TX_TRY(ensure_workspace(c, recs_bytes + batch_bytes));
+    TX_TRY(ensure_workspace(c, recs_bytes + prefix + batch_bytes));
     TX_TRY(ensure_ebatch(c, (int)nb));
     char* base = c->ws;
     PairRec* recs = (PairRec*)base;
     PairRec* recs2 = ntables == 2 ? (PairRec*)(base + recs_bytes / 2) : nullptr;
-    char* scratch = base + recs_bytes;
+    char* scratch = base + recs_bytes + prefix;
+    GalerkinOps gops{};
+    if (gk) TX_TRY(galerkin_operators(c, (float*)(base + recs_bytes), &gops, s));
 
     // zero the outputs that are accumulated into
     if (cs.kind == CALL_APPLY) TX_TRY_CUDA(cudaMemsetAsync(cs.out0, 0, sizeof(float) * N3 * cs.n_tgt, s));
@@ -172,12 +202,19 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     } else {
         TX_TRY(build_pairs(recs, cs.mode, ROLE_APPLY, cs.n_occ, cs.n_tgt, cs.k0, s));
     }
-    const bool energy = (cs.kind == CALL_ENERGY) || ((cs.kind == CALL_GRAD || cs.kind == CALL_APPLY) && cs.e_dev);
+    const bool energy = (cs.kind == CALL_ENERGY) || (!gk && (cs.kind == CALL_GRAD || cs.kind == CALL_APPLY) && cs.e_dev);
     for (long b = 0; b < nb; ++b) {
         const int p0 = (int)(b * Pb);
         const int np = (int)std::min<long>(Pb, P - p0);
         double* epart = (double*)(scratch + align_up((size_t)Pb * (per_pair - sizeof(double) * epp), 256));
-        if (tc) {
+        if (gk) {
+            float* S2 = (float*)scratch;
+            float* G = S2 + (size_t)Pb * L.s2;
+            float* H = G + (size_t)Pb * L.g;
+            float* X1 = H + (size_t)Pb * L.g;
+            float* X2 = X1 + (size_t)Pb * c->T * L.g;
+            TX_TRY(galerkin_batch(c, cs, gops, recs, p0, np, S2, G, H, X1, X2, epart, s));
+        } else if (tc) {
             BatchBuffers bb{recs, recs2, p0, np, scratch, epart};
             TX_TRY(tc_run_batch(c, cs, bb, s));
         } else {

@@ -18,7 +18,22 @@ struct CallSpec {
     float* out0 = nullptr;       // apply: K psi_tgt; grad: dE/dpsi; vjp: grad_occ
     float* out1 = nullptr;       // vjp: grad_tgt
     double* e_dev = nullptr;
+    int galerkin = 0;            // CALL_APPLY / CALL_ENERGY with the two-sided projection
 };
+
+// two-sided (Galerkin) projection (tx_galerkin.cu): B_td = U_d^T D_d A_td and D_d^-1 U_d
+struct GalerkinOps {
+    const float* B[3];           // [T][r_d][r_d], mu_t folded into mode 3
+    const float* Ut[3];          // [n_d][r_d]
+};
+size_t galerkin_operator_floats(const tx_ctx* c);
+int galerkin_operators(const tx_ctx* c, float* ops, GalerkinOps* g, cudaStream_t s);
+// H[p] = sum_t G[p] x_d B_td (X1, X2: [np][T][r1 r2 r3] scratch)
+int galerkin_core(const tx_ctx* c, const GalerkinOps& o, const float* G, float* X1, float* X2, float* H, int np,
+                  cudaStream_t s);
+// epart[p] = ew_p <G_p, H_p>
+int galerkin_core_dot(const tx_ctx* c, const PairRec* recs, int p0, const float* G, const float* H, int np,
+                      double* epart, cudaStream_t s);
 
 int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s);
 int ensure_workspace(tx_ctx* c, size_t bytes);

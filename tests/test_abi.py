@@ -106,7 +106,7 @@ def test_calls_on_null_context_are_rejected(L):
 
 
 def test_new_entry_points_reject_a_null_context(L):
-    """The ACE, energy-share, wait-limit and wait self-test entry points validate their context on
+    """The ACE, energy-share, quadrature, wait-limit and wait self-test entry points validate their context on
     the host before anything else (no device is touched)."""
     P_ = ctypes.c_void_p
     assert L.tx_ace_projectors(None, P_(0), 1, P_(0), P_(0), P_(0), P_(0)) == -8
@@ -114,4 +114,7 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.tx_exchange_energy_from_w(None, P_(0), P_(0), 1, P_(0), P_(0)) == -8
     assert L.tx_set_wait_limit(None, 0) == -8
     assert L.tx_selftest_wait(None, 1, P_(0)) == -8
+    assert L.tx_set_quadrature(None, 1, 3, P_(0)) == -8
+    assert L.tx_exchange_apply_galerkin(None, P_(0), 1, P_(0), 1, P_(0), P_(0)) == -8
+    assert L.tx_exchange_energy_galerkin(None, P_(0), 1, P_(0), P_(0)) == -8
     assert L.tx_status_string(-11).decode() == "TX_ERR_NOT_DEFINITE"
