@@ -252,18 +252,22 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
  * 128-row y tile where a plane has more rows) and the epilogue of one item overlaps the MMAs of
  * the next, wherever its limits hold (at most two x planes per CTA, energy factors equal to the
  * multipliers); one CTA per work item elsewhere.  Stage 3 reads the stage-2 output Y from TMEM
- * as a TF32 operand.  1: always one CTA per work item.  2 (bf16 only): a persistent form in which
- * converter warps round Y to bf16 into shared memory so that stage 3 also runs as bf16 (measured
- * slower than form 0 on the Pt- and TiO2-shaped blocks: the extra hop lengthens the per-term
- * chain of barriers).  All forms give the same result up to float32 summation order (form 2 up to
- * the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..2. */
+ * as a TF32 operand.  Where a plane's last y tile is short (at most 64 rows), the persistent form
+ * packs the last tiles of several planes into one 128-row item: their stage-2 products go to
+ * disjoint TMEM lanes of one stage-2 buffer (the stage-2 operand of each plane is a zero-padded
+ * window of A_t2), so stage 3 runs once for all of them instead of once per plane.  1: always
+ * one CTA per work item.  2 (bf16 only): a persistent form in which converter warps round Y to
+ * bf16 into shared memory so that stage 3 also runs as bf16 (measured slower than form 0 on the
+ * Pt- and TiO2-shaped blocks: the extra hop lengthens the per-term chain of barriers).  3: form 0
+ * without the packing of short y tiles.  All forms give the same result up to float32 summation
+ * order (form 2 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..3. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
 /* Host-only description of the expansion kernel (the final contraction of Eq. final with the
  * Hadamard product and the sum over j, the dominant kernel) that tx_exchange_apply and
  * tx_exchange_apply_energy launch for a context of this shape, precision and expansion form
- * (0, 1 or 2, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
- * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 12)
+ * (0 to 3, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
+ * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 13)
  * values to out:
  *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
  *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items), 4 persistent with
@@ -272,9 +276,10 @@ int tx_set_expansion_form(tx_ctx* ctx, int form);
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
  *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs, times y
- *   tiles where an item covers one y tile)
+ *   tiles where an item covers one y tile; with packed last y tiles, the full tiles plus one item
+ *   per group of packed planes)   [12] planes whose last y tiles share one item (0: not packed)
  * For the float32 precision every value is 0.  Returns TX_OK; TX_ERR_INVALID_ARG for NULL
- * arrays, nout < 1, T < 1 or a form outside 0..2; TX_ERR_SHAPE for sizes outside
+ * arrays, nout < 1, T < 1 or a form outside 0..3; TX_ERR_SHAPE for sizes outside
  * 2 <= n_d <= 4096, 1 <= r_d <= n_d; TX_ERR_UNSUPPORTED_PRECISION; TX_ERR_UNSUPPORTED_SHAPE
  * where tx_set_precision would refuse the shape. */
 int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out, int nout);

@@ -74,6 +74,13 @@ struct ConsumeArgs {
     // persistent single-pass kernel: work items (pair, slab), slabs per pair, epilogue region
     int nitems, nslab;
     int nyi;                   // persistent kernel: work items per slab (1, or one per y tile of 128 rows)
+    // persistent kernel, y tiles packed: the last y tile of a plane holds tail_rows rows, so the
+    // tails of tailp consecutive planes share one 128-row item (plane p in rows p * tail_r8 ..);
+    // its stage-2 A operand is, per plane, a window of the operator image at win_off + p * ya_bytes
+    // holding A_t2's last rows at those rows and zeros elsewhere.  0: every y tile its own item.
+    int tailp, tail_r8, tail_rows;
+    int per_pair;              // persistent kernel: work items per pair
+    uint32_t win_off;
     int nys;                   // bf16 persistent kernel: Y operand tiles in shared memory
     uint32_t ys_off, ys_bytes, ys_tile;   // ... their offset, stride per buffer, stride per tile
     uint32_t epi_off;
@@ -751,30 +758,31 @@ __global__ void __launch_bounds__(kThreads, 1)
 //            na full 128-byte-swizzled atoms `atom16` apart, then kt 32-byte-swizzled K steps
 //            `tail16` apart
 template <bool TF32, int KS>
-__device__ __forceinline__ void s2_mmas_k(uint32_t d, uint64_t ad, uint64_t bd, uint32_t a16, uint32_t b16, uint32_t id) {
+__device__ __forceinline__ void s2_mmas_k(uint32_t d, uint64_t ad, uint64_t bd, uint32_t a16, uint32_t b16, uint32_t id,
+                                          uint32_t acc0) {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
         mma_ss_w<TF32>(d, ad + (uint32_t)(k >> 2) * a16 + (uint32_t)(k & 3) * 2u,
-                       bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : 0u);
+                       bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : acc0);
 }
 template <bool TF32, int KS>
 __device__ __forceinline__ void s2_mmas(int ks, uint32_t d, uint64_t ad, uint64_t bd, uint32_t a16, uint32_t b16,
-                                        uint32_t id) {
+                                        uint32_t id, uint32_t acc0 = 0u) {
     if constexpr (KS > 0) {
-        s2_mmas_k<TF32, KS>(d, ad, bd, a16, b16, id);
+        s2_mmas_k<TF32, KS>(d, ad, bd, a16, b16, id, acc0);
     } else {
         switch (ks) {
-            case 1: s2_mmas_k<TF32, 1>(d, ad, bd, a16, b16, id); break;
-            case 2: s2_mmas_k<TF32, 2>(d, ad, bd, a16, b16, id); break;
-            case 3: s2_mmas_k<TF32, 3>(d, ad, bd, a16, b16, id); break;
-            case 4: s2_mmas_k<TF32, 4>(d, ad, bd, a16, b16, id); break;
-            case 5: s2_mmas_k<TF32, 5>(d, ad, bd, a16, b16, id); break;
-            case 6: s2_mmas_k<TF32, 6>(d, ad, bd, a16, b16, id); break;
-            case 8: s2_mmas_k<TF32, 8>(d, ad, bd, a16, b16, id); break;
+            case 1: s2_mmas_k<TF32, 1>(d, ad, bd, a16, b16, id, acc0); break;
+            case 2: s2_mmas_k<TF32, 2>(d, ad, bd, a16, b16, id, acc0); break;
+            case 3: s2_mmas_k<TF32, 3>(d, ad, bd, a16, b16, id, acc0); break;
+            case 4: s2_mmas_k<TF32, 4>(d, ad, bd, a16, b16, id, acc0); break;
+            case 5: s2_mmas_k<TF32, 5>(d, ad, bd, a16, b16, id, acc0); break;
+            case 6: s2_mmas_k<TF32, 6>(d, ad, bd, a16, b16, id, acc0); break;
+            case 8: s2_mmas_k<TF32, 8>(d, ad, bd, a16, b16, id, acc0); break;
             default:
                 for (int k = 0; k < ks; ++k)
                     mma_ss_w<TF32>(d, ad + (uint32_t)(k >> 2) * a16 + (uint32_t)(k & 3) * 2u,
-                                   bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : 0u);
+                                   bd + (uint32_t)(k >> 2) * b16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : acc0);
         }
     }
 }
@@ -1082,14 +1090,30 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     const int nmine = (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // item it = ((pair * nslab) + slab) * nyi + iy: with nyi > 1 an item covers one 128-row y
     // tile (iy) of its slab's planes (a.nY is then 1), so that phi and the Y buffers of grids
-    // with more than 128 rows per plane fit TMEM
+    // with more than 128 rows per plane fit TMEM.  With packed tails (a.tailp > 0, one plane per
+    // slab) a pair's items are its planes' full y tiles (slab, iy < nyi - 1), then its tail items
+    // (iy = nyi - 1, slab = index of the group of tailp planes).  Either way it = pair * per_pair
+    // + the item's index inside the pair.
     auto item_of = [&](int k, int& pl, int& slab, int& iy) {
         const int it = (int)blockIdx.x + k * (int)gridDim.x;
+        if (a.tailp) {
+            pl = it / a.per_pair;
+            const int j = it - pl * a.per_pair, ym = a.nyi - 1, nm = a.nslab * ym;
+            if (j < nm) {
+                slab = j / ym;
+                iy = j - slab * ym;
+            } else {
+                slab = j - nm;
+                iy = ym;
+            }
+            return;
+        }
         const int ps = it / a.nyi;
         iy = it - ps * a.nyi;
         pl = ps / a.nslab;
         slab = ps - pl * a.nslab;
     };
+    auto is_tail = [&](int iy) { return a.tailp > 0 && iy == a.nyi - 1; };
     auto YAs = [&](int s) { return smem + s * a.load_bytes; };
     auto Zs = [&](int s) { return YAs(s) + a.ya_bytes; };
     auto B3s = [&](int s) { return smem + a.a3_off + s * a.load3_bytes; };
@@ -1139,26 +1163,33 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         for (int k = 0; k < nmine && ok; ++k) {
             int pl, slab, iy;
             item_of(k, pl, slab, iy);
-            const int x0 = slab * BX;
-            for (int t = 0; t < NT; ++t) {
-                ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[s], ph ^ 1, a.err, 41));
-                if (!ok) break;
-                ++issued;
-                mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
-                const int zdep = pl * NT + t;
-                bulk_load_w(YAs(s), a.img + (size_t)t * a.img_stride, a.ya_bytes, &full_bar[s]);
-                if (a.zone) {
-                    tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, x0 * a.r3, zdep);
-                    for (int kk = 1; kk < na2; ++kk)
-                        tma_load_3d_w(Zs(s) + kk * z_atom, &mZ, &full_bar[s], kk * AK2, x0 * a.r3, zdep);
-                } else {
-                    for (int kk = 0; kk < na2; ++kk)
-                        for (int p = 0; p < BX; ++p)
-                            tma_load_3d_w(Zs(s) + kk * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s],
-                                          kk * AK2, (x0 + p) * a.r3, zdep);
+            const bool tail = is_tail(iy);
+            // a tail item takes one stage per plane and term: that plane's window of A_t2 and its Z
+            const int x0 = tail ? slab * a.tailp : slab * BX;
+            const int nsub = tail ? min(a.tailp, a.n1 - x0) : 1;
+            for (int t = 0; t < NT && ok; ++t)
+                for (int sp = 0; sp < nsub; ++sp) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[s], ph ^ 1, a.err, 41));
+                    if (!ok) break;
+                    ++issued;
+                    mbar_arrive_expect_tx_w(&full_bar[s], a.stage_tx);
+                    const int zdep = pl * NT + t;
+                    const int xz = x0 + sp;
+                    const uint8_t* asrc = a.img + (size_t)t * a.img_stride +
+                                          (tail ? a.win_off + (uint32_t)sp * a.ya_bytes : 0u);
+                    bulk_load_w(YAs(s), asrc, a.ya_bytes, &full_bar[s]);
+                    if (a.zone) {
+                        tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, xz * a.r3, zdep);
+                        for (int kk = 1; kk < na2; ++kk)
+                            tma_load_3d_w(Zs(s) + kk * z_atom, &mZ, &full_bar[s], kk * AK2, xz * a.r3, zdep);
+                    } else {
+                        for (int kk = 0; kk < na2; ++kk)
+                            for (int p = 0; p < BX; ++p)
+                                tma_load_3d_w(Zs(s) + kk * z_atom + (uint32_t)(p * a.gs) * 128u, &mZ, &full_bar[s],
+                                              kk * AK2, (xz + p) * a.r3, zdep);
+                    }
+                    if (++s == NL) { s = 0; ph ^= 1; }
                 }
-                if (++s == NL) { s = 0; ph ^= 1; }
-            }
         }
         if (!ok)
             for (int g = (issued > NL ? issued - NL : 0); g < issued; ++g) mbar_drain(&full_bar[g % NL], (g / NL) & 1, a.err);
@@ -1171,8 +1202,9 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             if (k >= nmine) return;
             int pl, slab, iy;
             item_of(k, pl, slab, iy);
-            const int x0 = slab * BX;
-            const int np_ = min(BX, a.n1 - x0);
+            const bool tail = is_tail(iy);
+            const int x0 = tail ? slab * a.tailp : slab * BX;
+            const int np_ = min(tail ? a.tailp : BX, a.n1 - x0);
             bulk_prefetch_l2_w(a.zsrc + ((size_t)pl * NT * a.n1 + x0) * a.z_plane + (size_t)t * zterm,
                                (uint32_t)np_ * a.z_plane);
         };
@@ -1204,29 +1236,37 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         for (int k = 0; k < nmine && ok; ++k) {
             int pl_, slab_, iy;
             item_of(k, pl_, slab_, iy);
-            for (int t = 0; t < NT; ++t, ++g) {
-                bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
-                // Y buffer yb was last read by stage 3 of term g - nyb
-                if (w && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
-                ok = __all_sync(0xffffffffu, w);
-                if (!ok) break;
-                tc_fence_after();
-                // the item's first y tile: rows iy * 128 of the A_t2 tile (1024 descriptor units)
-                const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4) + (uint32_t)iy * 1024u, zb = d0 + (smem_u32(Zs(s)) >> 4);
+            const bool tail = is_tail(iy);
+            const int nsub = tail ? min(a.tailp, a.n1 - slab_ * a.tailp) : 1;
+            for (int t = 0; t < NT && ok; ++t, ++g) {
                 const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
-                s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0);
-                if (more2)
-                    for (int i = 0; i < a.nY; ++i)
-                        for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
-                            const int N = pad16c(min(a.npc, BX - p0) * a.gs);
-                            const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
-                            s2_mmas<S2TF32, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs),
-                                                 ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u, ya_atom >> 4,
-                                                 z_atom >> 4, id2);
-                        }
-                mma_commit_w(&s2bar[yb]);
-                mma_commit_w(&empty_bar[s]);
-                if (++s == NL) { s = 0; ph ^= 1; }
+                // a tail item accumulates the windows of its planes into one Y buffer: each window
+                // is zero outside its plane's rows, so every plane lands in its own TMEM lanes
+                for (int sp = 0; sp < nsub; ++sp) {
+                    bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
+                    // Y buffer yb was last read by stage 3 of term g - nyb
+                    if (w && sp == 0 && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
+                    ok = __all_sync(0xffffffffu, w);
+                    if (!ok) break;
+                    tc_fence_after();
+                    // the item's first y tile: rows iy * 128 of the A_t2 tile (1024 descriptor units)
+                    const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4) + (tail ? 0u : (uint32_t)iy * 1024u),
+                                   zb = d0 + (smem_u32(Zs(s)) >> 4);
+                    s2_mmas<S2TF32, KS2>(a.ks2, tY, ya, zb, ya_atom >> 4, z_atom >> 4, id0, sp > 0 ? 1u : 0u);
+                    if (more2)
+                        for (int i = 0; i < a.nY; ++i)
+                            for (int p0 = (i == 0 ? a.npc : 0); p0 < BX; p0 += a.npc) {
+                                const int N = pad16c(min(a.npc, BX - p0) * a.gs);
+                                const uint32_t id2 = S2TF32 ? idesc_tf32(128, N) : idesc_bf16(128, N);
+                                s2_mmas<S2TF32, KS2>(a.ks2, tY + (uint32_t)(i * a.ycol_tile + p0 * a.gs),
+                                                     ya + (uint32_t)i * 1024u, zb + (uint32_t)(p0 * a.gs) * 8u,
+                                                     ya_atom >> 4, z_atom >> 4, id2);
+                            }
+                    if (sp == nsub - 1) mma_commit_w(&s2bar[yb]);
+                    mma_commit_w(&empty_bar[s]);
+                    if (++s == NL) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
                 if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
         }
@@ -1283,7 +1323,8 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             tc_fence_after();
             int pl, slab, iy;
             item_of(k, pl, slab, iy);
-            const int x0 = slab * BX;
+            const bool tail = is_tail(iy);
+            const int x0 = tail ? slab * a.tailp : slab * BX;
             const PairRec rec = a.recs[a.p0 + pl];
             // phi of this lane's row of tile jt (its chunks), into registers; then release the
             // accumulator
@@ -1303,19 +1344,31 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&phifree);
             double e = 0.0;
-            const int p = jt / a.nY, x = x0 + p, y0 = (iy + jt - p * a.nY) * 128 + q * 32;
+            // this lane's grid row (x, y): in a tail item lane row l of the tile is row l % tail_r8
+            // of the last y tile of plane x0 + l / tail_r8
+            int x, y;
+            bool rowin;
+            if (tail) {
+                const int l = q * 32 + lane, pp = l / a.tail_r8, yy = l - pp * a.tail_r8;
+                x = x0 + pp;
+                y = (a.nyi - 1) * 128 + yy;
+                rowin = pp < a.tailp && yy < a.tail_rows && x < a.n1;
+            } else {
+                const int p = jt / a.nY;
+                x = x0 + p;
+                y = (iy + jt - p * a.nY) * 128 + q * 32 + lane;
+                rowin = x < a.n1 && y < a.n2;
+            }
             const bool en = (a.flags & EPI_ENERGY) != 0;
             const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0;
             const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
             const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
-            if (has && x < a.n1 && y0 < a.n2 && (need0 || need1)) {
+            if (has && (need0 || need1) && __any_sync(0xffffffffu, rowin)) {
                 // each lane walks its own grid row: the orbital values come with direct 16-byte
                 // loads (a 64-byte row segment per chunk and orbital, all issued before use) and W
                 // is updated with 16-byte vector atomics, so no chunk waits on a shared-memory
                 // round trip and the pipeline keeps the shared memory for deeper operand rings
                 const long N3 = (long)a.n1 * a.n2 * a.n3;
-                const int y = y0 + lane;
-                const bool rowin = y < a.n2;
                 const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
                 const long rowoff = rowin ? ((long)x * a.n2 + y) * a.n3 : 0;
                 const float* mul0 = need0 ? a.MUL0 + (long)rec.m0 * N3 + rowoff : nullptr;
@@ -1365,7 +1418,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
             if ((a.flags & EPI_ENERGY) && warp == 0 && lane == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < 8; ++w) sum += red[k & 1][w];
-                a.epart[((long)pl * a.nslab + slab) * a.nyi + iy] = sum;
+                a.epart[(long)blockIdx.x + (long)k * gridDim.x] = sum;    // the item's index
             }
         }
     }
@@ -1382,9 +1435,29 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
 struct ImageArgs {
     int ks2, ks3, n3p;
     uint32_t ya_rows, ya_bytes, b3_bytes;
+    uint32_t stride;           // bytes per term of the image (the tiles, then any tail windows)
     uint8_t* img;
     int* err;
 };
+
+// Tail windows of the operator image (persistent kernel with packed y tiles): for term t and
+// plane slot p, a copy of the A_t2 tile whose rows p * r8 .. p * r8 + rows - 1 hold A_t2's rows
+// ybase .. ybase + rows - 1 and every other row is zero.  ybase and r8 are multiples of 8, so a
+// row keeps its 128-byte swizzle phase and is copied verbatim.
+__global__ void __launch_bounds__(256) k_tail_windows(uint8_t* img, uint32_t stride, uint32_t win_off, uint32_t ya_bytes,
+                                                      uint32_t ya_rows, int na2, int ybase, int rows, int r8) {
+    const int t = blockIdx.x, p = blockIdx.y;
+    const uint8_t* src = img + (size_t)t * stride;
+    uint8_t* dst = img + (size_t)t * stride + win_off + (size_t)p * ya_bytes;
+    const int total = na2 * (int)ya_rows * 8;   // 16-byte chunks of the window
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int row = q / 8, c = q % 8, k = row / (int)ya_rows, i = row - k * (int)ya_rows;
+        const int j = i - p * r8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (j >= 0 && j < rows) v = *(const uint4*)(src + ((size_t)k * ya_rows + ybase + j) * 128 + c * 16);
+        *(uint4*)(dst + ((size_t)k * ya_rows + i) * 128 + c * 16) = v;
+    }
+}
 
 template <bool S2TF32>
 __global__ void __launch_bounds__(32, 1)
@@ -1414,7 +1487,7 @@ __global__ void __launch_bounds__(32, 1)
         return;
     }
     const uint4* src = (const uint4*)smem;
-    uint4* dst = (uint4*)(g.img + (size_t)t * (g.ya_bytes + g.b3_bytes));
+    uint4* dst = (uint4*)(g.img + (size_t)t * g.stride);
     for (uint32_t i = threadIdx.x; i < (g.ya_bytes + g.b3_bytes) / 16; i += 32) dst[i] = src[i];
 }
 
@@ -1821,7 +1894,7 @@ __global__ void __launch_bounds__(32, 1)
         return;
     }
     const uint4* src = (const uint4*)smem;
-    uint4* dst = (uint4*)(g.img + (size_t)t * (g.ya_bytes + g.b3_bytes));
+    uint4* dst = (uint4*)(g.img + (size_t)t * g.stride);
     for (uint32_t i = threadIdx.x; i < (g.ya_bytes + g.b3_bytes) / 16; i += 32) dst[i] = src[i];
 }
 
@@ -1843,6 +1916,13 @@ struct ConsumePlan {
     int nload3;              // single-pass: stages of the stage-3 (mu_t A_t3) ring
     uint32_t load3;          // single-pass: stride of the stage-3 ring
     size_t smem;
+    // y-tile items with packed tails: the last y tile of each plane has tail_rows rows; tailp
+    // planes (tail_r8 = tail_rows rounded up to 8 rows each) share one item (0: not packed)
+    int tailp, tail_r8, tail_rows;
+    uint32_t img_stride() const { return ya + b3 + (uint32_t)tailp * ya; }
+    int items_per_slab_pair(int n1) const {   // work items per pair
+        return tailp ? (n1 / bx) * (nyi - 1) + (n1 + tailp - 1) / tailp : ((n1 + bx - 1) / bx) * (ts ? nyi : 1);
+    }
 };
 
 // Single-pass plan: bx planes, nload load stages and as many stage-2 output buffers in TMEM.
@@ -1866,6 +1946,13 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
         p->ysplit = true;
         p->nyi = p->nY;
         p->nY = 1;
+        // pack the short last y tiles of several planes into one item (one plane per slab)
+        const int rows = n2 - 128 * (p->nyi - 1), r8 = pad8(rows);
+        if (bx == 1 && c->consume_form != 3 && 128 / r8 >= 2) {
+            p->tailp = 128 / r8;
+            p->tail_r8 = r8;
+            p->tail_rows = rows;
+        }
     }
     p->npc = std::min(bx, 256 / p->gs);
     p->ks2 = (r2 + MK2 - 1) / MK2;
@@ -2160,7 +2247,7 @@ long tc_consume_blocks(const tx_ctx* c) {
     ConsumePlan p;
     const TcOperands* op = c->tc;
     if (!op || !choose_plan(c, op->tf32, op->split, &p)) return 1;
-    return (long)((c->n[0] + p.bx - 1) / p.bx) * (p.ts ? p.nyi : 1);
+    return p.items_per_slab_pair(c->n[0]);
 }
 
 // Persistent form of the single-pass kernel (the epilogue of one item overlaps the main loop of
@@ -2215,7 +2302,7 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
     ConsumePlan p;
     if (!choose_plan(c, tf32, split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
     const TpSplit t = (p.ts && !p.tb) ? tp_split(c, p, false, false) : TpSplit{};
-    const int v[12] = {p.tb ? 4 : (t.on ? 3 : (p.ts ? 2 : 1)),
+    const int v[13] = {p.tb ? 4 : (t.on ? 3 : (p.ts ? 2 : 1)),
                        p.bx,
                        t.on ? t.nl1 : p.nload,
                        p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
@@ -2226,8 +2313,9 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
                        p.ks2,
                        p.ks3,
                        p.n3p,
-                       (c->n[0] + p.bx - 1) / p.bx * (p.ts ? p.nyi : 1)};
-    for (int i = 0; i < nout && i < 12; ++i) out[i] = v[i];
+                       p.items_per_slab_pair(c->n[0]),
+                       p.tailp};
+    for (int i = 0; i < nout && i < 13; ++i) out[i] = v[i];
     return TX_OK;
 }
 
@@ -2256,6 +2344,7 @@ static int build_image_tb(tx_ctx* c, cudaStream_t s) {
     g.ya_rows = p.ya_rows;
     g.ya_bytes = p.ya;
     g.b3_bytes = p.b3;
+    g.stride = op->img_stride;
     g.img = (uint8_t*)op->img;
     g.err = c->d_err;
     const int smem = (int)op->img_stride + 1024;
@@ -2280,7 +2369,7 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
         if (plan_ts(c, op->tf32, 1, nl, &p, ysplit)) break;
     // the tile shapes below depend on (n, r, precision) only, not on the slab or the stages
     const int n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T, eb = op->esize;
-    op->img_stride = p.ya + p.b3;
+    op->img_stride = p.img_stride();
     if (cudaMalloc(&op->img, (size_t)T * op->img_stride) != cudaSuccess) {
         cudaGetLastError();
         op->img = nullptr;
@@ -2301,9 +2390,10 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
     g.ya_rows = p.ya_rows;
     g.ya_bytes = p.ya;
     g.b3_bytes = p.b3;
+    g.stride = op->img_stride;
     g.img = (uint8_t*)op->img;
     g.err = c->d_err;
-    const int smem = (int)op->img_stride + 1024;
+    const int smem = (int)(p.ya + p.b3) + 1024;
     if (op->tf32) {
         cudaFuncSetAttribute(tcc::k_operand_image<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         tcc::k_operand_image<true><<<(unsigned)T, 32, smem, s>>>(mA2, mA3f, mA3t, g);
@@ -2312,6 +2402,12 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
         tcc::k_operand_image<false><<<(unsigned)T, 32, smem, s>>>(mA2, mA3f, mA3t, g);
     }
     TX_LAUNCHED();
+    if (p.tailp) {
+        tcc::k_tail_windows<<<dim3((unsigned)T, (unsigned)p.tailp), 256, 0, s>>>(
+            (uint8_t*)op->img, op->img_stride, p.ya + p.b3, p.ya, p.ya_rows, (p.ks2 + 3) / 4, 128 * (p.nyi - 1),
+            p.tail_rows, p.tail_r8);
+        TX_LAUNCHED();
+    }
     return TX_OK;
 }
 
@@ -2350,7 +2446,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         // bytes per stage-2 stage (128-byte rows; zero-filled parts count): A_t2, Z planes
         const int na2 = (p.ks2 + 3) / 4;
         a.stage_tx = (uint32_t)(128 * (na2 * p.n2p + na2 * p.bx * r3));
-        if (!op->img || op->img_stride != p.ya + p.b3)
+        if (!op->img || op->img_stride != (p.tb ? p.ya + p.b3 : p.img_stride()))
             return fail(TX_ERR_CUDA, "operator image missing or built for another tile shape");
         a.img = (const uint8_t*)op->img;
         a.img_stride = op->img_stride;
@@ -2441,7 +2537,15 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         }
         a.nslab = (int)grid.x;
         a.nyi = p.nyi;
-        a.nitems = (int)grid.x * np * p.nyi;
+        a.per_pair = p.items_per_slab_pair(n1);
+        a.nitems = a.per_pair * np;
+        if (p.tailp) {
+            if (!tp) return fail(TX_ERR_UNSUPPORTED_SHAPE, "packed y tiles need the persistent kernel");
+            a.tailp = p.tailp;
+            a.tail_r8 = p.tail_r8;
+            a.tail_rows = p.tail_rows;
+            a.win_off = p.ya + p.b3;
+        }
         if (tp) {
             int dev = 0, nsm = 148;
             cudaGetDevice(&dev);

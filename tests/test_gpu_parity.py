@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _helpers import E_TOL, W_TOL, _log, assert_close, log_energy, max_row_rel, rel, to_gpu
+from _helpers import E_TOL, W_TOL, _log, assert_close, elem_rel, log_energy, max_row_rel, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -284,7 +284,7 @@ def test_expansion_forms_agree(prec, system):
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
         assert_close(outs[0][3:4], ref, prec, "forms-pt8")
     with pytest.raises(P.TuckerExchangeError):
-        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 3)
+        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 4)
 
 
 @pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent"), (64, "tf32", "persistent"),
@@ -292,9 +292,9 @@ def test_expansion_forms_agree(prec, system):
 def test_large_grid_two_y_tiles(prec, rank, kernel):
     """n = 160: two 128-row y tiles per plane.  At rank 64 (the TiO2-shaped workload) a whole
     plane's stage-2 output buffers (2 x 128 TMEM columns) and phi (2 x 160) exceed TMEM's 512
-    columns: bf16 and TF32 run the persistent kernel with one work item per y tile (phi 160
-    columns, four 64-column Y buffers); at rank 48 the one-CTA-per-item kernel.  Apply and energy
-    against the oracle."""
+    columns: bf16 and TF32 run the persistent kernel with one work item per full y tile (phi 160
+    columns, four 64-column Y buffers) and the 32-row last tiles of four planes packed into one
+    item; at rank 48 the one-CTA-per-item kernel.  Apply and energy against the oracle."""
     P = _P()
     assert P.tx_describe_expansion_plan((160, 160, 160), (rank,) * 3, 6, prec)["kernel"] == kernel
     s = W.config_small(n=160, n_orb=2, rank=rank, T=6, L=16.0)
@@ -309,6 +309,37 @@ def test_large_grid_two_y_tiles(prec, rank, kernel):
     e_ref = O.exchange_energy(s.psi, S)
     log_energy(prec, f"n160-r{rank}", e, e_ref)
     assert abs(e - e_ref) / abs(e_ref) < E_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("n,r,tail", [((27, 150, 160), (24, 64, 64), 5), ((12, 160, 160), (8, 64, 64), 4)])
+def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, r, tail):
+    """Planes of more than 128 rows whose last y tile is short: the persistent kernel packs the
+    last tiles of `tail` planes into one 128-row item (each plane's stage-2 operand a zero-padded
+    window of A_t2).  27 planes in groups of 5 leave a partial group of 2; 150 rows leave a
+    22-row tail (two zero rows of padding per plane).  Apply and energy against the unpacked form
+    (form 3: the same arithmetic per element, so float32 summation order only) and the oracle."""
+    P = _P()
+    d = P.tx_describe_expansion_plan(n, r, 6, prec)
+    assert d["kernel"] == "persistent" and d["tail_planes"] == tail
+    s = ragged_system(n=n, r=r, T=6, n_orb=3, seed=5)
+    S = O.Setup.from_system(s)
+    occ = to_gpu(s.psi)
+    outs, energies = [], []
+    for form in (0, 3):
+        ctx = P.Context.from_system(s, precision=prec)
+        P.tx_set_expansion_form(ctx, form)
+        outs.append(P.tx_exchange_apply(ctx, occ).cpu().numpy())
+        energies.append(float(P.tx_exchange_energy(ctx, occ).item()))
+        ctx.check_device_error()
+    assert rel(outs[0], outs[1]) < 1e-5
+    assert elem_rel(outs[0], outs[1])[0] < 1e-5
+    assert abs(energies[0] - energies[1]) <= 1e-5 * abs(energies[1])
+    ref = O.exchange_apply(s.psi, S)
+    assert_close(outs[0], ref, prec, f"packed-{n[0]}x{n[1]}")
+    e_ref = O.exchange_energy(s.psi, S)
+    log_energy(prec, f"packed-{n[0]}x{n[1]}", energies[0], e_ref)
+    assert abs(energies[0] - e_ref) / abs(e_ref) < E_TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16"])

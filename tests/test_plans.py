@@ -17,6 +17,10 @@ def _built():
     build.build()
 
 
+def pad8(v):
+    return (v + 7) // 8 * 8
+
+
 def pad16(v):
     return (v + 15) // 16 * 16
 
@@ -55,9 +59,16 @@ def test_tio2_shaped_bf16_plan_takes_one_y_tile_per_item():
     the persistent kernel takes one item per (pair, plane, y tile): phi 160 + four Y buffers of
     64 columns; the one-CTA-per-item form (form 1) falls back to the converter kernel."""
     d = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16")
-    assert d["kernel"] == "persistent" and d["planes"] == 1 and d["items_per_pair"] == 320
+    # 160 full 128-row tiles, then the 32-row last tiles of four planes per item: 160 + 40
+    assert d["kernel"] == "persistent" and d["planes"] == 1 and d["items_per_pair"] == 200
+    assert d["tail_planes"] == 4
     assert d["ybuffers"] == 4 and d["tmem_cols"] == 512
     assert d["stages2"] >= 2 and d["stages3"] >= 2
+    u = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=3)
+    assert u["kernel"] == "persistent" and u["items_per_pair"] == 320 and u["tail_planes"] == 0
+    # 150 rows: the last tile has 22 rows (24 with padding), five planes per item; 30 planes
+    v = P.tx_describe_expansion_plan((30, 150, 160), (24, 64, 64), 12, "bf16")
+    assert v["tail_planes"] == 5 and v["items_per_pair"] == 30 + 6
     assert P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=1)["kernel"] == "converter"
     b = P.tx_describe_expansion_plan((160, 160, 160), (64, 64, 64), 45, "bf16", form=2)
     assert b["kernel"] == "persistent_bf16" and b["items_per_pair"] == 320
@@ -74,7 +85,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
     split = prec.endswith("x3")
     mk = 8 if tf32 else 16
     planned = 0
-    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2)):
+    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2, 3)):
         rr = tuple(min(r, v) for v in n)
         try:
             d = P.tx_describe_expansion_plan(n, rr, T, prec, form)
@@ -86,10 +97,18 @@ def test_every_plan_respects_the_hardware_limits(prec):
         assert 0 < d["smem_bytes"] <= MAX_DYN_SMEM, key
         assert d["tmem_cols"] in (32, 64, 128, 256, 512), key
         slabs = -(-n[0] // d["planes"])
-        yi = d["items_per_pair"] // slabs       # work items per slab: 1, or one per 128-row y tile
-        assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
+        tp = d["tail_planes"]
+        if tp:                                  # packed last y tiles: full tiles, then tail groups
+            nyf = -(-n[1] // 128)
+            rows = n[1] - 128 * (nyf - 1)
+            assert d["planes"] == 1 and tp == 128 // pad8(rows) >= 2 and form in (0, 2), key
+            assert d["items_per_pair"] == n[0] * (nyf - 1) + -(-n[0] // tp), key
+            yi = nyf
+        else:
+            yi = d["items_per_pair"] // slabs   # work items per slab: 1, or one per 128-row y tile
+            assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
         if yi > 1:
-            assert d["kernel"] in ("persistent", "persistent_bf16") and form in (0, 2), key
+            assert d["kernel"] in ("persistent", "persistent_bf16") and form in (0, 2, 3), key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -107,7 +126,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
         assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
         if d["kernel"] == "persistent":
-            assert form in (0, 2) and d["threads"] == 384, key
+            assert form in (0, 2, 3) and d["threads"] == 384, key
             assert d["planes"] <= 2 and d["stages2"] <= 4, key
             tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
             assert tiles <= 2, key                                  # at most one phi tile per epilogue warp
@@ -127,7 +146,7 @@ def test_shapes_the_tensor_cores_cannot_take_are_refused():
         P.tx_describe_expansion_plan((12, 13, 300), (3, 4, 5), 3, "fp32")    # float32 kernels: n3 <= 256
     assert ei.value.status == -9
     for bad, status in [(((1, 8, 8), (1, 1, 1), 3, "bf16", 0), -2), (((8, 8, 8), (9, 1, 1), 3, "bf16", 0), -2),
-                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 3), -1)]:
+                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 4), -1)]:
         with pytest.raises(P.TuckerExchangeError) as ei:
             P.tx_describe_expansion_plan(*bad)
         assert ei.value.status == status, bad

@@ -284,7 +284,9 @@ def make_system_on_device(name: str, n: int, L: float, n_orb: int, rank: int, T:
     for c0 in range(0, N3, chunk):
         Pc = P[:, c0:c0 + chunk]
         S += (Pc * w3d[None, c0:c0 + chunk]) @ Pc.T
-    ev, V = torch.linalg.eigh(0.5 * (S + S.T))
+    # the small eigenproblems run on the host (LAPACK): the device solver library is not always
+    # loadable (e.g. under a profiler's injection)
+    ev, V = (v.to(device) for v in torch.linalg.eigh((0.5 * (S + S.T)).cpu()))
     if float(ev.min()) <= 1e-12 * float(ev.max()):
         raise ValueError("orbitals are numerically linearly dependent")
     X = (V * ev[None, :] ** -0.5) @ V.T
@@ -299,7 +301,7 @@ def make_system_on_device(name: str, n: int, L: float, n_orb: int, rank: int, T:
     Us = []
     for d in range(3):
         M = torch.movedim(rho, d, 0).reshape(n, -1)
-        evd, Vd = torch.linalg.eigh(M @ M.T)
+        evd, Vd = (v.to(device) for v in torch.linalg.eigh((M @ M.T).cpu()))
         Vd = Vd.flip(1)[:, :rank].cpu().numpy()
         sgn = np.sign(Vd[np.argmax(np.abs(Vd), axis=0), np.arange(Vd.shape[1])])
         Us.append(np.ascontiguousarray(Vd * sgn[None, :]))
