@@ -81,6 +81,8 @@ struct ConsumeArgs {
     int tailp, tail_r8, tail_rows;
     int per_pair;              // persistent kernel: work items per pair
     uint32_t win_off;
+    uint32_t img_ya_rows;      // rows per K atom of the A_t2 tile in the operator image (packed
+                               // items keep only 128 rows per atom in shared memory: ya_rows)
     int nys;                   // bf16 persistent kernel: Y operand tiles in shared memory
     uint32_t ys_off, ys_bytes, ys_tile;   // ... their offset, stride per buffer, stride per tile
     uint32_t epi_off;
@@ -1152,6 +1154,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     const uint32_t tmem = tmem_base;
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
+    const uint32_t img_atom = a.img_ya_rows * 128u, img_ya_bytes = img_atom * (uint32_t)((a.ks2 + 3) / 4);
     const int na3f = a.ks3 / 4;
     const int na2 = (a.ks2 + 3) / 4;
 
@@ -1176,8 +1179,14 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                     const int zdep = pl * NT + t;
                     const int xz = x0 + sp;
                     const uint8_t* asrc = a.img + (size_t)t * a.img_stride +
-                                          (tail ? a.win_off + (uint32_t)sp * a.ya_bytes : 0u);
-                    bulk_load_w(YAs(s), asrc, a.ya_bytes, &full_bar[s]);
+                                          (tail ? a.win_off + (uint32_t)sp * img_ya_bytes : 0u);
+                    if (a.tailp) {
+                        // packed items read rows 0..127 of each K atom only
+                        for (int kk = 0; kk < na2; ++kk)
+                            bulk_load_w(YAs(s) + kk * ya_atom, asrc + kk * img_atom, 128u * 128u, &full_bar[s]);
+                    } else {
+                        bulk_load_w(YAs(s), asrc, a.ya_bytes, &full_bar[s]);
+                    }
                     if (a.zone) {
                         tma_load_3d_w(Zs(s), &mZ, &full_bar[s], 0, xz * a.r3, zdep);
                         for (int kk = 1; kk < na2; ++kk)
@@ -1218,7 +1227,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 if (!ok) break;
                 ++issued;
                 mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
-                bulk_load_w(B3s(s), a.img + (size_t)t * a.img_stride + a.ya_bytes, a.b3_bytes, &full3[s]);
+                bulk_load_w(B3s(s), a.img + (size_t)t * a.img_stride + img_ya_bytes, a.b3_bytes, &full3[s]);
                 if (g > 0) prefetch(g + NL + 2);
                 if (++s == NL3) { s = 0; ph ^= 1; }
             }
@@ -1919,6 +1928,7 @@ struct ConsumePlan {
     // y-tile items with packed tails: the last y tile of each plane has tail_rows rows; tailp
     // planes (tail_r8 = tail_rows rounded up to 8 rows each) share one item (0: not packed)
     int tailp, tail_r8, tail_rows;
+    uint32_t sya_rows, sya;  // rows per K atom and bytes of the A_t2 tile in a shared-memory stage
     uint32_t img_stride() const { return ya + b3 + (uint32_t)tailp * ya; }
     int items_per_slab_pair(int n1) const {   // work items per pair
         return tailp ? (n1 / bx) * (nyi - 1) + (n1 + tailp - 1) / tailp : ((n1 + bx - 1) / bx) * (ts ? nyi : 1);
@@ -1983,7 +1993,10 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     // two rings: nload stages of [A_t2][Z] (stage 2), then as many stages of [mu_t A_t3]
     // (stage 3, up to kMaxLoad) as shared memory holds: its loads start only when stage 3 of
     // an earlier term has finished, so this ring needs the deeper lead
-    p->load = (p->ya + p->zb + 1023) & ~1023u;
+    // packed items read 128 rows per K atom of the A_t2 tile (or of a window): a stage keeps those
+    p->sya_rows = p->tailp ? 128u : p->ya_rows;
+    p->sya = (uint32_t)na2 * p->sya_rows * 128u;
+    p->load = (p->sya + p->zb + 1023) & ~1023u;
     p->load3 = (p->b3 + 1023) & ~1023u;
     p->nload = nload;
     p->a3_off = p->load * (uint32_t)nload;
@@ -2425,7 +2438,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     a.bx = p.bx; a.R = p.bx * n2; a.nY = p.nY; a.Nz = p.Nz; a.npc = p.npc; a.nT3 = p.nT3;
     a.n2p = p.n2p; a.n3p = p.n3p; a.ks2 = p.ks2; a.ks3 = p.ks3; a.nq = p.nq;
     a.nload = p.nload; a.na3 = p.na3; a.nyb = p.nyb;
-    a.ya_rows = p.ya_rows; a.z_rows = p.z_rows;
+    a.ya_rows = p.ya_rows; a.z_rows = p.z_rows; a.img_ya_rows = p.ya_rows;
     a.ya_bytes = p.ya; a.z_bytes = p.zb; a.b3_bytes = p.b3; a.a3_bytes = p.a3;
     a.load_bytes = p.load; a.a3_off = p.a3_off;
     // bytes the TMA delivers per stage (out-of-range rows and columns count: they are zero-filled)
@@ -2541,6 +2554,10 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         a.nitems = a.per_pair * np;
         if (p.tailp) {
             if (!tp) return fail(TX_ERR_UNSUPPORTED_SHAPE, "packed y tiles need the persistent kernel");
+            // every item reads 128 rows of A_t2 (or of a window) per K atom
+            a.stage_tx = (uint32_t)(128 * (na2 * 128 + na2 * p.bx * r3));
+            a.ya_rows = p.sya_rows;
+            a.ya_bytes = p.sya;
             a.tailp = p.tailp;
             a.tail_r8 = p.tail_r8;
             a.tail_rows = p.tail_rows;
