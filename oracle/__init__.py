@@ -43,6 +43,12 @@ symmetric and positive semi-definite (B_td = U_d^T D_d K_td D_d U_d), so E_x <= 
 is computable in core space (galerkin_core_matrices, apply_L_galerkin, exchange_apply_galerkin,
 exchange_energy_galerkin).
 
+The transfer of orbitals between the unstructured finite-element basis of a DFT code and the
+structured grid (section "Transfer of wavefunctions", Eq. interpolate): every structured node
+takes the value of the unstructured cell containing it, psi_s[i, a] = sum_b N_ab psi_u[b, i]
+with N_ab the cell's shape function of node b at a (transfer_u_to_s), and every unstructured
+node the value of the structured element containing it (transfer_s_to_u).
+
 The adaptively compressed exchange operator built from W (section "ACE implementation",
 Eqs. eta, ace1): M_ij = <psi_i, W_j>_w, M = -L L^T, xi_k = sum_i W_i (L^-1)_ki and
 V_ACE psi = - sum_k xi_k <xi_k, psi>_w (M symmetrised first where a truncated rank leaves it
@@ -63,7 +69,8 @@ __all__ = [
     "direct_gaussian_kernel_potential", "direct_coulomb_potential",
     "gaussian_charge_potential", "gaussian_kernel_charge_potential", "conv_matrix_fe",
     "conv_matrix_p1_exact", "galerkin_core_matrices", "galerkin_core_convolve", "apply_L_galerkin",
-    "exchange_apply_galerkin", "exchange_energy_galerkin",
+    "exchange_apply_galerkin", "exchange_energy_galerkin", "lagrange_basis", "transfer_u_to_s",
+    "transfer_s_to_u",
 ]
 
 
@@ -359,6 +366,83 @@ def ace_apply(xi, psi, S: Setup):
     psi = np.asarray(psi, dtype=np.float64)
     C = np.array([[np.sum(S.w3 * xi[k] * psi[a]) for a in range(psi.shape[0])] for k in range(xi.shape[0])])
     return -np.tensordot(C, xi, axes=(0, 0))          # [a] = - sum_k C[k, a] xi[k]
+
+
+# ----------------------------------------------------------------------------------
+# transfer between the unstructured and the structured finite-element bases (Eq. interpolate)
+# ----------------------------------------------------------------------------------
+def lagrange_basis(nodes, x):
+    """L[k, j] = value at x[j] of the 1-D Lagrange polynomial that is 1 at nodes[k] and 0 at the
+    other nodes."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    L = np.ones((nodes.size, x.size))
+    for k in range(nodes.size):
+        for m in range(nodes.size):
+            if m != k:
+                L[k] *= (x - nodes[m]) / (nodes[k] - nodes[m])
+    return L
+
+
+def transfer_u_to_s(psi_u, X, conn, order, xs):
+    """psi_s[i, a] = sum_b N_ab psi_u[b, i] (Eq. interpolate): every node a of the structured
+    grid xs (three 1-D node arrays) is interpolated from the unstructured cell that contains
+    it, N_ab being the value of that cell's shape function of node b at a.  Cells are
+    tensor-product Lagrange elements of `order` on axis-aligned boxes (local node (lx, ly, lz) at
+    index (lx (order+1) + ly) (order+1) + lz).  Where several cells contain a node (a shared face,
+    or a face with hanging nodes) the cell listed first is used.  psi_u: [n_nodes, N];
+    returns [N, n1, n2, n3]."""
+    p = int(order)
+    psi_u = np.asarray(psi_u, dtype=np.float64)
+    xs = [np.asarray(v, dtype=np.float64) for v in xs]
+    n = [v.size for v in xs]
+    P = np.stack(np.meshgrid(*xs, indexing="ij"), axis=-1).reshape(-1, 3)     # [n1 n2 n3, 3]
+    out = np.zeros((psi_u.shape[1], P.shape[0]))
+    done = np.zeros(P.shape[0], dtype=bool)
+    for c in range(conn.shape[0]):
+        nodes = X[conn[c]].reshape(p + 1, p + 1, p + 1, 3)
+        ax = [nodes[:, 0, 0, 0], nodes[0, :, 0, 1], nodes[0, 0, :, 2]]      # 1-D node coordinates
+        lo = np.array([a.min() for a in ax])
+        hi = np.array([a.max() for a in ax])
+        tol = 1e-9 * (hi - lo)
+        inside = ~done & np.all((P >= lo - tol) & (P <= hi + tol), axis=1)
+        idx = np.nonzero(inside)[0]
+        if idx.size == 0:
+            continue
+        Lx, Ly, Lz = (lagrange_basis(ax[d], P[idx, d]) for d in range(3))
+        N = (Lx[:, None, None, :] * Ly[None, :, None, :] * Lz[None, None, :, :]).reshape(-1, idx.size)
+        out[:, idx] = (N.T @ psi_u[conn[c]]).T
+        done[idx] = True
+    if not done.all():
+        raise ValueError("the unstructured mesh does not cover every structured node")
+    return out.reshape(psi_u.shape[1], *n)
+
+
+def transfer_s_to_u(psi_s, xs, order, X):
+    """psi_u[b, i] = sum_a M_ba psi_s[i, a]: every unstructured node b is interpolated from the
+    structured element that contains it, the structured mesh being the tensor product of 1-D
+    Lagrange elements of `order` on the nodes xs (element e of an axis holds nodes
+    order e .. order e + order).  psi_s: [N, n1, n2, n3]; returns [n_nodes, N]."""
+    p = int(order)
+    psi_s = np.asarray(psi_s, dtype=np.float64)
+    xs = [np.asarray(v, dtype=np.float64) for v in xs]
+    X = np.asarray(X, dtype=np.float64)
+    out = np.zeros((X.shape[0], psi_s.shape[0]))
+    for b in range(X.shape[0]):
+        sel, wts = [], []
+        for d in range(3):
+            x = xs[d]
+            nel = (x.size - 1) // p
+            e = 0
+            while e < nel - 1 and X[b, d] > x[p * (e + 1)]:
+                e += 1
+            nodes = x[p * e: p * (e + 1) + 1]
+            sel.append(np.arange(p * e, p * e + p + 1))
+            wts.append(lagrange_basis(nodes, [X[b, d]])[:, 0])
+        block = psi_s[:, sel[0][:, None, None], sel[1][None, :, None], sel[2][None, None, :]]
+        W3 = wts[0][:, None, None] * wts[1][None, :, None] * wts[2][None, None, :]
+        out[b] = np.tensordot(block, W3, axes=([1, 2, 3], [0, 1, 2]))
+    return out
 
 
 # ----------------------------------------------------------------------------------

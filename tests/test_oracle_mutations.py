@@ -109,6 +109,18 @@ MUTATIONS = [
     ("Galerkin energy without the factor 1/2",
      "            E -= 0.5 * float(np.sum(G * galerkin_core_convolve(G, S, B)))",
      "            E -= float(np.sum(G * galerkin_core_convolve(G, S, B)))"),
+    ("transfer: Lagrange basis of the wrong node",
+     "                L[k] *= (x - nodes[m]) / (nodes[k] - nodes[m])",
+     "                L[k] *= (x - nodes[m]) / (nodes[m] - nodes[k])"),
+    ("transfer to the grid with the y and z node coordinates swapped",
+     "        ax = [nodes[:, 0, 0, 0], nodes[0, :, 0, 1], nodes[0, 0, :, 2]]      # 1-D node coordinates",
+     "        ax = [nodes[:, 0, 0, 0], nodes[0, 0, :, 2], nodes[0, :, 0, 1]]      # 1-D node coordinates"),
+    ("transfer to the mesh with elements stepped by order + 1 nodes",
+     "            nodes = x[p * e: p * (e + 1) + 1]",
+     "            nodes = x[(p + 1) * e: (p + 1) * e + p + 1] if (p + 1) * e + p < x.size else x[p * e: p * (e + 1) + 1]"),
+    ("transfer to the mesh always from the first element",
+     "            while e < nel - 1 and X[b, d] > x[p * (e + 1)]:",
+     "            while False:"),
     ("quadrature weight of mode 2 on mode 3",
      "        self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]",
      "        self.w3 = self.w[0][:, None, None] * self.w[2][None, None, :] * self.w[2][None, None, :]"),

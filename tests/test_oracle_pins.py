@@ -535,3 +535,92 @@ def test_galerkin_energy_in_core_space_equals_the_grid_energy():
     M = np.einsum("axyz,bxyz->ab", psi * S.w3[None], Wg)
     assert np.max(np.abs(M - M.T)) < 1e-12 * np.max(np.abs(M))
     assert np.max(np.linalg.eigvalsh(0.5 * (M + M.T))) < 1e-12 * np.max(np.abs(M))
+
+
+# ---------------------------------------------------------------------------------
+# Transfer between the unstructured and structured finite-element bases (Eq. interpolate)
+# ---------------------------------------------------------------------------------
+def _poly(deg):
+    """A polynomial of degree `deg` in each coordinate, different along every axis."""
+    cx = [1.0, 2.0, 0.5, -0.1][: deg + 1]
+    cy = [1.0, -1.0, 0.3, 0.05][: deg + 1]
+    cz = [2.0, 1.0, -0.7, 0.02][: deg + 1]
+    return lambda x, y, z: (sum(c * x ** k for k, c in enumerate(cx)) * sum(c * y ** k for k, c in enumerate(cy))
+                            * sum(c * z ** k for k, c in enumerate(cz)))
+
+
+def _transfer_case():
+    X, conn = W.fe_mesh(4.0, 3, [[0.0, 0.0, 0.0], [1.5, -1.0, 0.5]], 2.0, 2)
+    xs = [np.linspace(-4, 4, 19), np.linspace(-4, 4, 22), np.linspace(-4, 4, 25)]
+    return X, conn, xs
+
+
+def test_transfer_to_the_grid_reproduces_polynomials_of_the_element_order():
+    """Lagrange elements of order 2 reproduce any polynomial of degree 2 in each coordinate, on
+    refined and unrefined cells alike; one of degree 3 is not reproduced."""
+    X, conn, xs = _transfer_case()
+    G = np.meshgrid(*xs, indexing="ij")
+    for deg, exact in ((2, True), (3, False)):
+        f = _poly(deg)
+        got = O.transfer_u_to_s(f(X[:, 0], X[:, 1], X[:, 2])[:, None], X, conn, 2, xs)[0]
+        err = np.max(np.abs(got - f(*G))) / np.max(np.abs(f(*G)))
+        assert (err < 1e-12) if exact else (err > 1e-6)
+
+
+def test_transfer_to_the_mesh_reproduces_polynomials_of_the_element_order():
+    X, conn, xs = _transfer_case()
+    xs = [np.linspace(-4, 4, 19), np.linspace(-4, 4, 22), np.linspace(-4, 4, 25)]   # 18, 21, 24: order 3
+    G = np.meshgrid(*xs, indexing="ij")
+    for deg in (1, 3):
+        f = _poly(deg)
+        got = O.transfer_s_to_u(f(*G)[None], xs, 3, X)[:, 0]
+        ref = f(X[:, 0], X[:, 1], X[:, 2])
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    f = _poly(2)
+    got = O.transfer_s_to_u(f(*G)[None], xs, 1, X)[:, 0]      # linear elements: not exact for degree 2
+    ref = f(X[:, 0], X[:, 1], X[:, 2])
+    assert np.max(np.abs(got - ref)) > 1e-6 * np.max(np.abs(ref))
+
+
+def test_transfer_between_matching_meshes_is_the_identity():
+    """Unstructured cells that are the structured elements themselves (same nodes, same order):
+    both transfers only renumber the values."""
+    p = 2
+    xs = [np.linspace(-2, 2, 5), np.linspace(-3, 3, 7), np.linspace(-1, 1, 9)]
+    cells, Xl, index = [], [], {}
+    for ex in range(2):
+        for ey in range(3):
+            for ez in range(4):
+                ids = []
+                for lx in range(p + 1):
+                    for ly in range(p + 1):
+                        for lz in range(p + 1):
+                            key = (p * ex + lx, p * ey + ly, p * ez + lz)
+                            if key not in index:
+                                index[key] = len(Xl)
+                                Xl.append([xs[0][key[0]], xs[1][key[1]], xs[2][key[2]]])
+                            ids.append(index[key])
+                cells.append(ids)
+    X, conn = np.array(Xl), np.array(cells, dtype=np.int32)
+    rng = np.random.default_rng(31)
+    psi_s = rng.standard_normal((3, 5, 7, 9))
+    psi_u = O.transfer_s_to_u(psi_s, xs, p, X)
+    for key, g in index.items():
+        assert np.allclose(psi_u[g], psi_s[:, key[0], key[1], key[2]], rtol=0, atol=1e-13)
+    assert np.max(np.abs(O.transfer_u_to_s(psi_u, X, conn, p, xs) - psi_s)) < 1e-13
+
+
+def test_transfer_of_a_smooth_orbital_converges_at_the_element_order():
+    """A Gaussian sampled on the unstructured nodes and carried to the grid: halving the cells
+    divides the error by about 2^(order + 1) (order 2: ~8)."""
+    xs = [np.linspace(-4, 4, 33)] * 3
+    G = np.meshgrid(*xs, indexing="ij")
+    cen = np.array([[[0.3, -0.2, 0.1]]])
+    f = lambda pts: W.gaussian_sum_at_points(pts, cen, np.array([[0.5]]), np.array([[1.0]]))[0]
+    exact = f(np.stack([g.ravel() for g in G], axis=1)).reshape(G[0].shape)
+    errs = []
+    for base in (4, 8):
+        X, conn = W.fe_mesh(4.0, base, np.zeros((1, 3)), 0.0, 2, levels=0)
+        got = O.transfer_u_to_s(f(X)[:, None], X, conn, 2, xs)[0]
+        errs.append(np.max(np.abs(got - exact)))
+    assert 5.0 < errs[0] / errs[1] < 12.0

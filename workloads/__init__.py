@@ -24,7 +24,7 @@ __all__ = [
     "uniform_grid", "fcc_cluster", "rutile_cluster", "gaussian_sum_orbitals",
     "lowdin_orthonormalise", "density_hosvd_basis", "exp_sum_inverse_r",
     "System", "make_system", "make_system_on_device", "config_tio2_on_device", "CONFIGS",
-    "batched_system_specs",
+    "batched_system_specs", "fe_mesh", "gaussian_sum_at_points",
 ]
 
 
@@ -382,3 +382,63 @@ CONFIGS = {
     "diff": config_diff,
     "tio2": config_tio2,
 }
+
+
+# ----------------------------------------------------------------------------------
+# finite-element meshes for the transfer between the unstructured and structured bases
+# ----------------------------------------------------------------------------------
+def fe_mesh(L: float, base: int, centres, radius: float, order: int, levels: int = 1):
+    """A hexahedral finite-element mesh of [-L, L]^3 that is refined near atoms: base^3 cubic
+    cells, then `levels` times every cell whose centre lies within `radius` of a centre is split
+    into eight.  Refined cells next to unrefined ones leave hanging nodes (the mesh is
+    non-conforming there).  Every cell carries (order + 1)^3 equispaced Lagrange nodes, local
+    node (lx, ly, lz) at index (lx (order + 1) + ly) (order + 1) + lz; nodes at the same place
+    are one global node.  Returns (X [n_nodes, 3] float64, conn [n_cells, (order+1)^3] int32).
+    Cells are listed coarse first, in the order they were made."""
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
+    h = 2.0 * L / base
+    cells = [(np.array([-L + i * h, -L + j * h, -L + k * h]), h) for i in range(base) for j in range(base)
+             for k in range(base)]
+    for _ in range(levels):
+        out = []
+        for lo, w in cells:
+            c = lo + 0.5 * w
+            if np.min(np.linalg.norm(centres - c[None, :], axis=1)) < radius:
+                hw = 0.5 * w
+                out.extend((lo + hw * np.array([a, b, d]), hw) for a in (0, 1) for b in (0, 1) for d in (0, 1))
+            else:
+                out.append((lo, w))
+        cells = sorted(out, key=lambda cw: -cw[1])        # coarse cells first
+    p = int(order)
+    q = np.arange(p + 1) / p
+    index = {}
+    X = []
+    conn = np.empty((len(cells), (p + 1) ** 3), dtype=np.int32)
+    tol = 1e-9 * L
+    for ci, (lo, w) in enumerate(cells):
+        l = 0
+        for lx in range(p + 1):
+            for ly in range(p + 1):
+                for lz in range(p + 1):
+                    pt = lo + w * np.array([q[lx], q[ly], q[lz]])
+                    key = tuple(np.round(pt / tol).astype(np.int64))
+                    g = index.get(key)
+                    if g is None:
+                        g = len(X)
+                        index[key] = g
+                        X.append(pt)
+                    conn[ci, l] = g
+                    l += 1
+    return np.asarray(X, dtype=np.float64), conn
+
+
+def gaussian_sum_at_points(points, centres, exps, coefs):
+    """psi_i at arbitrary points [P, 3] (the orbitals of gaussian_sum_orbitals): [N, P]."""
+    pts = np.asarray(points, dtype=np.float64)
+    N, K = exps.shape
+    out = np.zeros((N, pts.shape[0]))
+    for i in range(N):
+        for k in range(K):
+            d2 = np.sum((pts - centres[i, k][None, :]) ** 2, axis=1)
+            out[i] += coefs[i, k] * np.exp(-exps[i, k] * d2)
+    return out
