@@ -381,6 +381,7 @@ def main():
                    sample=f"{pairs} ordered pairs ({what}), {sec:.2f} s of FP64 numpy")
         if tio2 and not args.no_secondary:
             secondary = pt_secondary(P, W, dev, run_oracle)
+            secondary["transfer"] = transfer_secondary(P, W, ctx, psi[:n_tgt], out, peaks)
     if world > 1:
         dist.barrier()
     if rank == 0:
@@ -403,6 +404,55 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def transfer_secondary(P, W, ctx, psi_s, out_s, peaks):
+    """The transfer between an unstructured finite-element mesh and the structured grid (Eq.
+    interpolate) at the TiO2 shape: a hexahedral mesh of [-16, 16]^3 (8^3 cells of 4 bohr, each
+    cell within 2 bohr of one of the 240 rutile-like centres split in eight, order-2 Lagrange
+    nodes) and the 160^3 grid with order-3 elements, for the 256 target orbitals; both directions
+    timed (CUDA events, 3 repetitions after a warm-up).  Algorithmic bytes: each orbital value on
+    the mesh once, each grid value the direction touches once (all of them to the grid; those of
+    the grid elements holding mesh nodes back to the mesh), plus the stored map."""
+    import numpy as np
+    import torch
+    pu, ps = 2, 3
+    X, conn = W.fe_mesh(16.0, 8, W.rutile_cluster(240), 2.0, pu)
+    tr = P.Transfer(ctx, X, conn, pu, ps)
+    n_orb = psi_s.shape[0]
+    n_grid = psi_s[0].numel()
+    psi_u = torch.empty((X.shape[0], n_orb), dtype=torch.float32, device=psi_s.device)
+    res = {}
+    # grid values the reverse transfer reads: the nodes of the grid elements holding mesh nodes
+    xs = [np.linspace(-16.0, 16.0, k) for k in ctx.n]
+    touched = np.zeros(ctx.n, dtype=bool)
+    el = [np.searchsorted(xs[d][ps::ps][:-1], X[:, d], side="left") for d in range(3)]
+    for ex, ey, ez in set(zip(*el)):
+        touched[ps * ex: ps * ex + ps + 1, ps * ey: ps * ey + ps + 1, ps * ez: ps * ez + ps + 1] = True
+    nb, ns = (pu + 1) ** 3, (ps + 1) ** 3
+    u_bytes = X.shape[0] * n_orb * 4
+    bytes_of = {"mesh_to_grid": u_bytes + n_grid * n_orb * 4 + 4 * (conn.shape[0] + 1) + 4 * n_grid * (1 + nb)
+                + 4 * conn.size,
+                "grid_to_mesh": u_bytes + int(touched.sum()) * n_orb * 4 + 4 * X.shape[0] * (1 + ns)}
+    hbm = (peaks or {}).get("hbm_gbs")
+    for name, fn in (("grid_to_mesh", lambda: tr.s_to_u(psi_s, out=psi_u)),
+                     ("mesh_to_grid", lambda: tr.u_to_s(psi_u, out=out_s))):
+        fn()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(3):
+            fn()
+        a1.record()
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / 3
+        gbs = bytes_of[name] / (ms / 1e3) / 1e9
+        res[name] = dict(ms=ms, algorithmic_bytes=int(bytes_of[name]), achieved_gbs=gbs,
+                         frac_of_hbm=(gbs / hbm) if hbm else None)
+    tr.destroy()
+    return dict(mesh_nodes=int(X.shape[0]), mesh_cells=int(conn.shape[0]), orbitals=int(n_orb), order_mesh=pu,
+                order_grid=ps, hbm_peak_gbs=hbm, peak_source="measured" if hbm else None, results=res)
 
 
 def pt_secondary(P, W, dev, run_oracle_fn):

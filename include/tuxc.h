@@ -131,6 +131,44 @@ int tx_exchange_energy_galerkin(tx_ctx* ctx, const float* psi_occ, int n_occ, do
  */
 int tx_set_quadrature(tx_ctx* ctx, int order, int points, tx_stream_t stream);
 
+/*
+ * Transfer of orbitals between an unstructured finite-element basis and the structured grid of
+ * a context (section "Transfer of wavefunctions", Eq. interpolate):
+ *     psi_s[i][a] = sum_b N_ab psi_u[b][i]
+ * N_ab being the value at structured node a of the shape function of node b of the unstructured
+ * cell that contains a.  The map (which structured nodes lie in which cell, and their N rows) is
+ * computed once by tx_transfer_create and stored on the device; each transfer is then one
+ * batched per-cell product over all orbitals.  The reverse transfer interpolates the structured
+ * field (tensor-product Lagrange elements of order_s on the grid nodes) at every unstructured
+ * node.
+ *
+ * tx_transfer_create: ctx gives the structured grid (its nodes and device).  X: host float64
+ *   [n_nodes][3] node coordinates of the unstructured mesh; conn: host int32
+ *   [n_cells][(order_u + 1)^3] global node of each local node (lx, ly, lz) at index
+ *   (lx (order_u + 1) + ly) (order_u + 1) + lz; every cell is an axis-aligned box with its local
+ *   nodes on a tensor product of 1-D node sets (the Lagrange nodes may sit anywhere inside
+ *   it; the mesh may be refined with hanging nodes).  Where several cells contain a structured
+ *   node (a shared face) the cell listed first gives its value.  order_s: order of the
+ *   structured elements along every axis (n_d - 1 must be a multiple).  Orders 1 to 3.  The
+ *   inputs are copied; the transfer keeps no pointer to them nor to ctx.  Synchronous.
+ *   Errors: TX_ERR_INVALID_ARG (NULL or empty mesh, orders outside 1..3, a node index out of
+ *   range), TX_ERR_NOT_SETUP (bad ctx), TX_ERR_SHAPE (n_d - 1 not a multiple of order_s, or
+ *   structured nodes outside every cell), TX_ERR_OOM.
+ * tx_transfer_u_to_s: psi_u device float32 [n_nodes][n_orb] (orbital index fastest, as an FE code
+ *   stores them) -> psi_s device float32 [n_orb][n1][n2][n3].  Asynchronous on stream.
+ * tx_transfer_s_to_u: psi_s [n_orb][n1][n2][n3] -> psi_u [n_nodes][n_orb].  Asynchronous.
+ * tx_transfer_map_bytes: device bytes of the stored map (0 for a bad handle).
+ * tx_transfer_destroy: frees the map (NULL is a no-op); the caller orders it after the
+ *   transfers that use it.
+ */
+typedef struct tx_transfer tx_transfer;
+int tx_transfer_create(tx_transfer** out, tx_ctx* ctx, int order_s, const double* X, int n_nodes, const int* conn,
+                       int n_cells, int order_u);
+int tx_transfer_u_to_s(tx_transfer* tr, const float* psi_u, int n_orb, float* psi_s, tx_stream_t stream);
+int tx_transfer_s_to_u(tx_transfer* tr, const float* psi_s, int n_orb, float* psi_u, tx_stream_t stream);
+long tx_transfer_map_bytes(const tx_transfer* tr);
+void tx_transfer_destroy(tx_transfer* tr);
+
 /* Release every device allocation of the context (after synchronising its last stream). */
 void tx_destroy(tx_ctx* ctx);
 

@@ -28,7 +28,8 @@ EXPORTED = [
     "tx_batch_replay", "tx_batch_item_plan", "tx_plan_destroy", "tx_set_tile_plan", "tx_set_accumulation_chunk", "tx_set_expansion_form",
     "tx_exchange_apply_static", "tx_describe_expansion_plan", "tx_set_wait_limit", "tx_selftest_wait",
     "tx_exchange_energy_from_w", "tx_ace_projectors", "tx_ace_apply", "tx_set_quadrature",
-    "tx_exchange_apply_galerkin", "tx_exchange_energy_galerkin",
+    "tx_exchange_apply_galerkin", "tx_exchange_energy_galerkin", "tx_transfer_create", "tx_transfer_u_to_s",
+    "tx_transfer_s_to_u", "tx_transfer_map_bytes", "tx_transfer_destroy",
 ]
 
 
@@ -84,6 +85,16 @@ def lib():
     L.tx_exchange_apply_galerkin.restype = _I
     L.tx_exchange_energy_galerkin.argtypes = [_P, _P, _I, _P, _P]
     L.tx_exchange_energy_galerkin.restype = _I
+    L.tx_transfer_create.argtypes = [ctypes.POINTER(_P), _P, _I, _P, _I, _P, _I, _I]
+    L.tx_transfer_create.restype = _I
+    L.tx_transfer_u_to_s.argtypes = [_P, _P, _I, _P, _P]
+    L.tx_transfer_u_to_s.restype = _I
+    L.tx_transfer_s_to_u.argtypes = [_P, _P, _I, _P, _P]
+    L.tx_transfer_s_to_u.restype = _I
+    L.tx_transfer_map_bytes.argtypes = [_P]
+    L.tx_transfer_map_bytes.restype = ctypes.c_long
+    L.tx_transfer_destroy.argtypes = [_P]
+    L.tx_transfer_destroy.restype = None
     L.tx_exchange_apply_energy.argtypes = [_P, _P, _I, _P, _P, _P]
     L.tx_exchange_apply_energy.restype = _I
     L.tx_profile_enable.argtypes = [_I]
@@ -509,3 +520,56 @@ def tx_launch_count() -> int:
 
 def tx_reset_launch_count():
     lib().tx_reset_launch_count()
+
+
+class Transfer:
+    """Transfer of orbitals between an unstructured finite-element mesh (nodes X [n_nodes, 3],
+    cells conn [n_cells, (order_u + 1)^3]) and the structured grid of a context, whose elements
+    have order `order_s` (Eq. interpolate).  Orbitals on the mesh are [n_nodes, n_orb] (orbital
+    index fastest); on the grid [n_orb, n1, n2, n3]."""
+
+    def __init__(self, ctx: "Context", X, conn, order_u, order_s):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        if X.ndim != 2 or X.shape[1] != 3 or conn.ndim != 2 or conn.shape[1] != (int(order_u) + 1) ** 3:
+            raise ValueError("X must be [n_nodes, 3] and conn [n_cells, (order_u + 1)^3]")
+        self.ctx = ctx
+        self.n_nodes = X.shape[0]
+        h = _P()
+        _check(lib().tx_transfer_create(ctypes.byref(h), ctx.handle, int(order_s), X.ctypes.data, X.shape[0],
+                                        conn.ctypes.data, conn.shape[0], int(order_u)), "tx_transfer_create")
+        self.handle = h
+
+    def map_bytes(self) -> int:
+        return int(lib().tx_transfer_map_bytes(self.handle))
+
+    def u_to_s(self, psi_u, out=None, stream=None):
+        if psi_u.dtype != torch.float32 or not psi_u.is_contiguous() or psi_u.dim() != 2 or psi_u.shape[0] != self.n_nodes:
+            raise ValueError("psi_u must be contiguous float32 [n_nodes, n_orb]")
+        n_orb = psi_u.shape[1]
+        if out is None:
+            out = torch.empty((n_orb, *self.ctx.n), dtype=torch.float32, device=psi_u.device)
+        self.ctx._block(out, "psi_s")
+        _check(lib().tx_transfer_u_to_s(self.handle, _ptr(psi_u), n_orb, _ptr(out), _stream(stream)), "tx_transfer_u_to_s")
+        return out
+
+    def s_to_u(self, psi_s, out=None, stream=None):
+        self.ctx._block(psi_s, "psi_s")
+        n_orb = psi_s.shape[0]
+        if out is None:
+            out = torch.empty((self.n_nodes, n_orb), dtype=torch.float32, device=psi_s.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (self.n_nodes, n_orb):
+            raise ValueError("out must be contiguous float32 [n_nodes, n_orb]")
+        _check(lib().tx_transfer_s_to_u(self.handle, _ptr(psi_s), n_orb, _ptr(out), _stream(stream)), "tx_transfer_s_to_u")
+        return out
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().tx_transfer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -117,4 +117,10 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.tx_set_quadrature(None, 1, 3, P_(0)) == -8
     assert L.tx_exchange_apply_galerkin(None, P_(0), 1, P_(0), 1, P_(0), P_(0)) == -8
     assert L.tx_exchange_energy_galerkin(None, P_(0), 1, P_(0), P_(0)) == -8
+    h = P_()
+    assert L.tx_transfer_create(ctypes.byref(h), None, 1, P_(0), 1, P_(0), 1, 1) == -8
+    assert L.tx_transfer_u_to_s(None, P_(0), 1, P_(0), P_(0)) == -8
+    assert L.tx_transfer_s_to_u(None, P_(0), 1, P_(0), P_(0)) == -8
+    assert L.tx_transfer_map_bytes(None) == 0
+    L.tx_transfer_destroy(None)
     assert L.tx_status_string(-11).decode() == "TX_ERR_NOT_DEFINITE"
