@@ -35,6 +35,11 @@ Gauss-Legendre quadrature inside every element:
   C_td[a,b] = sum_e sum_q J_e w_q N_b(x_q) exp(-theta_t (x_a - x_q)^2)
 (conv_matrix_fe; Setup(..., quadrature=("fe", p, points))).
 
+A per-pair variant follows the paper's own decomposition (Eq. TuckerDecompField): every pair
+density gets its own bases from a sequentially truncated HOSVD (modes 1, 2, 3 in turn; the r_d
+leading eigenvectors of the mode-d Gram matrix of the partly projected tensor), and the
+convolution uses A_td,ij = C_td U_d,ij (sthosvd, pair_potential_sthosvd, exchange_apply_sthosvd).
+
 A two-sided (Galerkin) variant of the convolution, which the paper does not describe: the
 one-sided operator C P (P = (x)_d U_d U_d^T) is not symmetric in the w inner product at a
 truncated rank.  Projecting the output too, with the w-adjoint P^* = D^-1 P D, gives
@@ -70,7 +75,7 @@ __all__ = [
     "gaussian_charge_potential", "gaussian_kernel_charge_potential", "conv_matrix_fe",
     "conv_matrix_p1_exact", "galerkin_core_matrices", "galerkin_core_convolve", "apply_L_galerkin",
     "exchange_apply_galerkin", "exchange_energy_galerkin", "lagrange_basis", "transfer_u_to_s",
-    "transfer_s_to_u",
+    "transfer_s_to_u", "sthosvd", "pair_potential_sthosvd", "exchange_apply_sthosvd",
 ]
 
 
@@ -167,8 +172,9 @@ class Setup:
                 return conv_matrix_fe(self.x[d], self.theta[t], self.quadrature[1], self.quadrature[2])
             return conv_matrix(self.x[d], self.w[d], self.theta[t])
 
-        # A[t][d] = C_td U_d, an [n_d, r_d] matrix
-        self.A = [[C(d, t) @ self.U[d] for d in range(3)] for t in range(self.T)]
+        # C[t][d], the 1-D convolution matrices, and A[t][d] = C_td U_d, an [n_d, r_d] matrix
+        self.C = [[C(d, t) for d in range(3)] for t in range(self.T)]
+        self.A = [[self.C[t][d] @ self.U[d] for d in range(3)] for t in range(self.T)]
         self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]
 
     @classmethod
@@ -280,6 +286,49 @@ def exchange_apply_vjp(psi_occ, psi_tgt, grad_out, S: Setup):
             g_tgt[k] -= occ[j] * zeta
             g_occ[j] -= Wb[k] * pair_potential(tgt[k], occ[j], S) + tgt[k] * zeta
     return g_occ, g_tgt
+
+
+# ----------------------------------------------------------------------------------
+# per-pair Tucker bases: sequentially truncated HOSVD of every pair density (Eq. TuckerDecompField)
+# ----------------------------------------------------------------------------------
+def sthosvd(rho, ranks):
+    """Sequentially truncated HOSVD: for d = 1, 2, 3 in turn, U_d = the r_d leading eigenvectors
+    (eigenvalues descending) of the Gram matrix of the mode-d unfolding of the current tensor,
+    which is then projected onto them in mode d.  Returns (G, [U1, U2, U3]) with
+    rho ~ G x1 U1 x2 U2 x3 U3."""
+    G = np.asarray(rho, dtype=np.float64)
+    Us = []
+    for d in range(3):
+        M = np.moveaxis(G, d, 0).reshape(G.shape[d], -1)
+        ev, V = np.linalg.eigh(M @ M.T)
+        U = V[:, ::-1][:, : int(ranks[d])]
+        G = mode_product(G, U.T, d)
+        Us.append(U)
+    return G, Us
+
+
+def pair_potential_sthosvd(psi_a, psi_b, S: Setup, ranks):
+    """phi_ab with the pair's own Tucker bases (Eqs. TuckerDecompField, final):
+    phi = sum_t mu_t G x1 (C_t1 U1) x2 (C_t2 U2) x3 (C_t3 U3) with (G, U_d) = sthosvd(rho_ab)."""
+    G, Us = sthosvd(np.asarray(psi_a, np.float64) * np.asarray(psi_b, np.float64), ranks)
+    phi_p = np.zeros(np.shape(psi_a))
+    for t in range(S.T):
+        Yp = G
+        for d in range(3):
+            Yp = mode_product(Yp, S.C[t][d] @ Us[d], d)
+        phi_p += S.mu[t] * Yp
+    return phi_p
+
+
+def exchange_apply_sthosvd(psi_occ, S: Setup, ranks, psi_tgt=None):
+    """W_i = - sum_j psi_j * phi_ij with per-pair Tucker bases of ranks (r1, r2, r3)."""
+    occ = np.asarray(psi_occ, dtype=np.float64)
+    tgt = occ if psi_tgt is None else np.asarray(psi_tgt, dtype=np.float64)
+    W = np.zeros_like(tgt)
+    for i in range(tgt.shape[0]):
+        for j in range(occ.shape[0]):
+            W[i] -= occ[j] * pair_potential_sthosvd(tgt[i], occ[j], S, ranks)
+    return W
 
 
 # ----------------------------------------------------------------------------------

@@ -121,6 +121,18 @@ MUTATIONS = [
     ("transfer to the mesh always from the first element",
      "            while e < nel - 1 and X[b, d] > x[p * (e + 1)]:",
      "            while False:"),
+    ("STHOSVD keeps the trailing eigenvectors",
+     "        U = V[:, ::-1][:, : int(ranks[d])]",
+     "        U = V[:, : int(ranks[d])]"),
+    ("STHOSVD computes every mode's Gram matrix from the original density",
+     "        G = mode_product(G, U.T, d)\n        Us.append(U)",
+     "        Us.append(U)"),
+    ("per-pair potential drops mu_t",
+     "        phi_p += S.mu[t] * Yp",
+     "        phi_p += Yp"),
+    ("per-pair potential with the convolution matrix transposed",
+     "            Yp = mode_product(Yp, S.C[t][d] @ Us[d], d)",
+     "            Yp = mode_product(Yp, S.C[t][d].T @ Us[d], d)"),
     ("quadrature weight of mode 2 on mode 3",
      "        self.w3 = self.w[0][:, None, None] * self.w[1][None, :, None] * self.w[2][None, None, :]",
      "        self.w3 = self.w[0][:, None, None] * self.w[2][None, None, :] * self.w[2][None, None, :]"),

@@ -624,3 +624,59 @@ def test_transfer_of_a_smooth_orbital_converges_at_the_element_order():
         got = O.transfer_u_to_s(f(X)[:, None], X, conn, 2, xs)[0]
         errs.append(np.max(np.abs(got - exact)))
     assert 5.0 < errs[0] / errs[1] < 12.0
+
+
+# ---------------------------------------------------------------------------------
+# Per-pair Tucker bases (sequentially truncated HOSVD, Eq. TuckerDecompField)
+# ---------------------------------------------------------------------------------
+def test_sthosvd_error_is_the_sum_of_the_discarded_eigenvalues():
+    """For the sequentially truncated HOSVD the squared error of the reconstruction is exactly
+    the sum over modes of the eigenvalues discarded at that mode's step (each step removes an
+    orthogonal part); truncating nothing reconstructs the tensor."""
+    rng = np.random.default_rng(41)
+    rho = rng.standard_normal((9, 10, 11)) + np.einsum("a,b,c->abc", *[rng.standard_normal(k) for k in (9, 10, 11)]) * 4
+    ranks = (4, 5, 6)
+    G, Us = O.sthosvd(rho, ranks)
+    rec = G
+    for d in range(3):
+        rec = O.mode_product(rec, Us[d], d)
+    discarded = 0.0
+    T = rho
+    for d in range(3):
+        M = np.moveaxis(T, d, 0).reshape(T.shape[d], -1)
+        ev = np.sort(np.linalg.eigvalsh(M @ M.T))[::-1]
+        discarded += ev[ranks[d]:].sum()
+        T = O.mode_product(T, Us[d].T, d)
+    err2 = float(np.sum((rho - rec) ** 2))
+    assert abs(err2 - discarded) < 1e-10 * np.sum(rho ** 2)
+    G, Us = O.sthosvd(rho, rho.shape)
+    rec = G
+    for d in range(3):
+        rec = O.mode_product(rec, Us[d], d)
+    assert _rel(rec, rho) < 1e-12
+
+
+def test_per_pair_bases_at_full_rank_give_the_direct_sum():
+    rng = np.random.default_rng(42)
+    n = (6, 7, 8)
+    S = _random_setup(rng, n, (3, 3, 3), 3)
+    a, b = rng.standard_normal(n), rng.standard_normal(n)
+    phi = O.pair_potential_sthosvd(a, b, S, n)
+    ref = O.direct_gaussian_kernel_potential(a * b, S.x, S.w, S.theta, S.mu)
+    assert _rel(phi, ref) < 1e-12
+
+
+def test_per_pair_bases_capture_a_separable_density_at_rank_one():
+    """A rank-(1,1,1) pair density (a product of separable orbitals) is reproduced exactly by
+    rank-1 per-pair bases, whatever the shared basis, so its potential is the direct sum."""
+    rng = np.random.default_rng(43)
+    n = (7, 8, 9)
+    S = _random_setup(rng, n, (2, 2, 2), 3)
+    fa = [rng.standard_normal(k) for k in n]
+    fb = [rng.standard_normal(k) for k in n]
+    a, b = np.einsum("a,b,c->abc", *fa), np.einsum("a,b,c->abc", *fb)
+    phi = O.pair_potential_sthosvd(a, b, S, (1, 1, 1))
+    ref = O.direct_gaussian_kernel_potential(a * b, S.x, S.w, S.theta, S.mu)
+    assert _rel(phi, ref) < 1e-12
+    # the shared rank-2 random basis does not capture it
+    assert _rel(O.pair_potential(a, b, S), ref) > 1e-3
