@@ -116,6 +116,21 @@ int tx_exchange_apply_galerkin(tx_ctx* ctx, const float* psi_occ, int n_occ, con
 int tx_exchange_energy_galerkin(tx_ctx* ctx, const float* psi_occ, int n_occ, double* e_dev, tx_stream_t stream);
 
 /*
+ * tx_exchange_apply_sthosvd -- out = K psi_tgt with per-pair Tucker bases, the paper's own
+ * decomposition (Eq. TuckerDecompField): every pair density rho_ij = psi_i psi_j gets its bases
+ * from a sequentially truncated HOSVD (modes 1, 2, 3 in turn: U_d,ij = the r_d leading
+ * eigenvectors of the Gram matrix of the mode-d unfolding of the partly projected density, the
+ * context's ranks r_d), and phi_ij = sum_t mu_t G_ij x_d (C_td U_d,ij) (Eq. final) with the
+ * context's 1-D convolution matrices C_td (its quadrature); the context's shared bases are not
+ * used.  W_i = - sum_j psi_j * phi_ij.  Arguments, layouts, aliasing rules and errors are those of
+ * tx_exchange_apply; runs in float32 on the CUDA cores whatever the context's precision (the
+ * eigenvectors from a Jacobi method in float32); TX_ERR_UNSUPPORTED_SHAPE for n_d > 160.  The
+ * first call makes float32 copies of C_td (T n_d^2 floats per mode).
+ */
+int tx_exchange_apply_sthosvd(tx_ctx* ctx, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
+                              float* out, tx_stream_t stream);
+
+/*
  * tx_set_quadrature -- how the 1-D convolution integrals are evaluated (Eqs. quadVal, discInteg).
  *   order 0             nodal quadrature with the context's weights (the default):
  *                       C_td[a][b] = w_b exp(-theta_t (x_a - x_b)^2)

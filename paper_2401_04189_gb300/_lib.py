@@ -29,7 +29,7 @@ EXPORTED = [
     "tx_exchange_apply_static", "tx_describe_expansion_plan", "tx_set_wait_limit", "tx_selftest_wait",
     "tx_exchange_energy_from_w", "tx_ace_projectors", "tx_ace_apply", "tx_set_quadrature",
     "tx_exchange_apply_galerkin", "tx_exchange_energy_galerkin", "tx_transfer_create", "tx_transfer_u_to_s",
-    "tx_transfer_s_to_u", "tx_transfer_map_bytes", "tx_transfer_destroy",
+    "tx_transfer_s_to_u", "tx_transfer_map_bytes", "tx_transfer_destroy", "tx_exchange_apply_sthosvd",
 ]
 
 
@@ -83,6 +83,8 @@ def lib():
     L.tx_exchange_apply.restype = _I
     L.tx_exchange_apply_galerkin.argtypes = [_P, _P, _I, _P, _I, _P, _P]
     L.tx_exchange_apply_galerkin.restype = _I
+    L.tx_exchange_apply_sthosvd.argtypes = [_P, _P, _I, _P, _I, _P, _P]
+    L.tx_exchange_apply_sthosvd.restype = _I
     L.tx_exchange_energy_galerkin.argtypes = [_P, _P, _I, _P, _P]
     L.tx_exchange_energy_galerkin.restype = _I
     L.tx_transfer_create.argtypes = [ctypes.POINTER(_P), _P, _I, _P, _I, _P, _I, _I]
@@ -280,6 +282,12 @@ def tx_exchange_apply(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None
                              0 if psi_tgt is None else n_tgt, _ptr(out), _stream(stream))
     _check(st, _fn)
     return out
+
+
+def tx_exchange_apply_sthosvd(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None):
+    """out = K psi_tgt with per-pair Tucker bases from a sequentially truncated HOSVD of every
+    pair density (ranks = the context's ranks)."""
+    return tx_exchange_apply(ctx, psi_occ, psi_tgt, out, stream, _fn="tx_exchange_apply_sthosvd")
 
 
 def tx_exchange_apply_galerkin(ctx: Context, psi_occ, psi_tgt=None, out=None, stream=None):

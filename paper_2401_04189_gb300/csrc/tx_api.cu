@@ -174,6 +174,7 @@ static void free_ctx(tx_ctx* c) {
         cudaFree(c->f_U[d]);
         cudaFree(c->f_A[d]);
         cudaFree(c->f_w[d]);
+        cudaFree(c->f_C[d]);
     }
     cudaFree(c->d_theta);
     cudaFree(c->d_mu);
@@ -424,7 +425,7 @@ static void classify_targets(const tx_ctx* c, const float* occ, int n_occ, const
 }
 
 static int exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt, float* out,
-                          tx_stream_t stream, int galerkin) {
+                          tx_stream_t stream, int galerkin, int per_pair = 0) {
     TX_TRY(check_ctx(c));
     DeviceGuard dg;
     TX_TRY(dg.use(c->device));
@@ -451,7 +452,13 @@ static int exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const floa
     cs.tgt = psi_tgt ? psi_tgt : psi_occ;
     cs.out0 = out;
     cs.galerkin = galerkin;
+    cs.per_pair = per_pair;
     return run_call(c, cs, s);
+}
+
+extern "C" int tx_exchange_apply_sthosvd(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
+                                         float* out, tx_stream_t stream) {
+    return exchange_apply(c, psi_occ, n_occ, psi_tgt, n_tgt, out, stream, 0, 1);
 }
 
 extern "C" int tx_exchange_apply(tx_ctx* c, const float* psi_occ, int n_occ, const float* psi_tgt, int n_tgt,
@@ -610,6 +617,9 @@ extern "C" int tx_set_quadrature(tx_ctx* c, int order, int points, tx_stream_t s
     c->last_stream = s;
     if (order == 0) TX_TRY(setup_factor_matrices(c, s));
     else TX_TRY(setup_factor_matrices_fe(c, order, points, s));
+    c->quad_order = order;
+    c->quad_points = order > 0 ? points : 0;
+    c->c_valid = false;
     // the operand copies of the tensor-core precisions are rebuilt from the new A_td
     if (c->prec != TX_PREC_FP32) TX_TRY(tc_prepare(c, s));
     return TX_OK;

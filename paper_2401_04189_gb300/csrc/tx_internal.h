@@ -96,6 +96,9 @@ struct tx_ctx {
     float* f_U[3];       // [n_d][r_d]
     float* f_A[3];       // [T][n_d][r_d]; mu_t folded into mode 3
     float* f_w[3];       // [n_d]
+    float* f_C[3];       // [T][n_d][n_d] convolution matrices, mu_t folded into mode 3 (per-pair path; lazy)
+    bool c_valid;        // f_C matches the current quadrature
+    int quad_order, quad_points;   // 0 = nodal quadrature; else finite elements (tx_set_quadrature)
     // tensor-core operands (null for TX_PREC_FP32)
     tx::TcOperands* tc;
     // workspace
@@ -176,7 +179,7 @@ int simt_project_s2(const tx_ctx* c, const PairRec* recs, int p0, int np, const 
 // expansion consumer: modes 2 and 3 for every term, Hadamard epilogue, energy partials
 int simt_expand_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const FieldArgs& f,
                         const float* Z, int nterms, const float* M2, const float* M3, int flags,
-                        double* epart, cudaStream_t s);
+                        double* epart, cudaStream_t s, long m2_ps = 0, long m3_ps = 0);
 int simt_expand_consume_blocks(const tx_ctx* c);
 // adjoint stage: R[p][t][x][g][b] = sum_{y,z} A_t2[y][b] A_t3[z][g] (prod)[x][y][z]
 int simt_adjoint_r(const tx_ctx* c, const PairRec* recs, int p0, int np, const FieldArgs& f,
@@ -189,10 +192,12 @@ int finalize_energy(const double* batches, int nb, double scale, double* e_dev, 
 int weighted_dot(const tx_ctx* c, const float* A, const float* B, int count, double* partial, int nblocks, double scale,
                  double* e_dev, cudaStream_t s);
 
-// setup -- tx_setup.cu
-int setup_factor_matrices(tx_ctx* c, cudaStream_t s);
+// setup -- tx_setup.cu (with_c: also write the float32 convolution matrices f_C)
+int setup_factor_matrices(tx_ctx* c, cudaStream_t s, bool with_c = false);
 // the same with finite-element quadrature (Lagrange elements of `order`, `points` Gauss points)
-int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s);
+int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s, bool with_c = false);
+// f_C allocated and filled for the context's current quadrature
+int ensure_conv_matrices(tx_ctx* c, cudaStream_t s);
 
 // tensor-core path -- tx_tc.cu
 int tc_prepare(tx_ctx* c, cudaStream_t s);

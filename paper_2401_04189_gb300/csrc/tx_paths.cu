@@ -50,12 +50,14 @@ int gemm_mode1_adjoint(const tx_ctx* c, const float* R, float* H, int np, cudaSt
     return simt_gemm(g, s);
 }
 
-// Z[p][t][x][(g,b)] = sum_a M1_t[x][a] G[p][(g,b)][a]   (mode 1 of the expansion, every term)
-int gemm_mode1_expand(const tx_ctx* c, const float* G, const float* M1, int nt, float* Z, int np, cudaStream_t s) {
+// Z[p][t][x][(g,b)] = sum_a M1_t[x][a] G[p][(g,b)][a]   (mode 1 of the expansion, every term;
+// M1 per pair when m1_ps > 0)
+int gemm_mode1_expand(const tx_ctx* c, const float* G, const float* M1, int nt, float* Z, int np, cudaStream_t s,
+                      long m1_ps = 0) {
     const int n1 = c->n[0], r1 = c->r[0], rr = c->r[1] * c->r[2];
     GemmArgs g{};
     g.M = n1; g.N = rr; g.K = r1;
-    g.A = M1; g.a_m = r1; g.a_k = 1; g.a_b1 = (long)n1 * r1; g.a_b2 = 0;
+    g.A = M1; g.a_m = r1; g.a_k = 1; g.a_b1 = (long)n1 * r1; g.a_b2 = m1_ps;
     g.B = G; g.b_k = 1; g.b_n = r1; g.b_b1 = 0; g.b_b2 = (long)rr * r1;
     g.C = Z; g.c_m = rr; g.c_n = 1; g.c_b1 = (long)n1 * rr; g.c_b2 = (long)nt * n1 * rr;
     g.nb1 = nt; g.nb2 = np; g.alpha = 1.f; g.accumulate = 0;
@@ -149,6 +151,10 @@ int simt_adjoint_mode1(const tx_ctx* c, const float* R, float* H, int np, cudaSt
 int simt_expand_mode1(const tx_ctx* c, const float* G, const float* M1, int nt, float* Z, int np, cudaStream_t s) {
     return gemm_mode1_expand(c, G, M1, nt, Z, np, s);
 }
+int simt_expand_mode1_pp(const tx_ctx* c, const float* G, const float* M1, long m1_pair_stride, int nt, float* Z,
+                         int np, cudaStream_t s) {
+    return gemm_mode1_expand(c, G, M1, nt, Z, np, s, m1_pair_stride);
+}
 
 int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     const long N3 = (long)c->n[0] * c->n[1] * c->n[2];
@@ -157,14 +163,19 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     // first-mode sum over the terms and its single-term expansion run in float32)
     // (the two-sided projection runs in float32 on the CUDA cores in every precision)
     const bool gk = cs.galerkin != 0;
-    const bool tc = c->prec != TX_PREC_FP32 && !gk;
+    const bool pp = cs.per_pair != 0;
+    const bool tc = c->prec != TX_PREC_FP32 && !gk && !pp;
     const int ntables = cs.kind == CALL_VJP ? 2 : 1;
     const size_t recs_bytes = align_up(sizeof(PairRec) * (size_t)P, 256) * ntables;
     const size_t prefix = gk ? align_up(sizeof(float) * galerkin_operator_floats(c), 256) : 0;
     size_t per_pair;
     long epp;
     SimtLayout L = simt_layout(c);
-    if (gk) {
+    if (pp) {
+        TX_TRY(sthosvd_check(c));
+        per_pair = sizeof(float) * sthosvd_floats_per_pair(c);
+        epp = simt_expand_consume_blocks(c);
+    } else if (gk) {
         per_pair = sizeof(float) * (L.s2 + 2 * L.g + 2 * (size_t)c->T * L.g);
         epp = cs.kind == CALL_ENERGY ? 1 : simt_expand_consume_blocks(c);
     } else if (tc) {
@@ -188,6 +199,7 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     char* scratch = base + recs_bytes + prefix;
     GalerkinOps gops{};
     if (gk) TX_TRY(galerkin_operators(c, (float*)(base + recs_bytes), &gops, s));
+    if (pp) TX_TRY(ensure_conv_matrices(c, s));
 
     // zero the outputs that are accumulated into
     if (cs.kind == CALL_APPLY) TX_TRY_CUDA(cudaMemsetAsync(cs.out0, 0, sizeof(float) * N3 * cs.n_tgt, s));
@@ -202,12 +214,14 @@ int run_call(tx_ctx* c, const CallSpec& cs, cudaStream_t s) {
     } else {
         TX_TRY(build_pairs(recs, cs.mode, ROLE_APPLY, cs.n_occ, cs.n_tgt, cs.k0, s));
     }
-    const bool energy = (cs.kind == CALL_ENERGY) || (!gk && (cs.kind == CALL_GRAD || cs.kind == CALL_APPLY) && cs.e_dev);
+    const bool energy = (cs.kind == CALL_ENERGY) || (!gk && !pp && (cs.kind == CALL_GRAD || cs.kind == CALL_APPLY) && cs.e_dev);
     for (long b = 0; b < nb; ++b) {
         const int p0 = (int)(b * Pb);
         const int np = (int)std::min<long>(Pb, P - p0);
         double* epart = (double*)(scratch + align_up((size_t)Pb * (per_pair - sizeof(double) * epp), 256));
-        if (gk) {
+        if (pp) {
+            TX_TRY(sthosvd_batch(c, cs, recs, p0, np, (float*)scratch, epart, s));
+        } else if (gk) {
             float* S2 = (float*)scratch;
             float* G = S2 + (size_t)Pb * L.s2;
             float* H = G + (size_t)Pb * L.g;

@@ -19,7 +19,17 @@ struct CallSpec {
     float* out1 = nullptr;       // vjp: grad_tgt
     double* e_dev = nullptr;
     int galerkin = 0;            // CALL_APPLY / CALL_ENERGY with the two-sided projection
+    int per_pair = 0;            // CALL_APPLY with per-pair Tucker bases (sequentially truncated HOSVD)
 };
+
+// per-pair Tucker bases (tx_sthosvd.cu)
+size_t sthosvd_floats_per_pair(const tx_ctx* c);
+int sthosvd_check(const tx_ctx* c);
+int sthosvd_batch(tx_ctx* c, const CallSpec& cs, const PairRec* recs, int p0, int np, float* scratch, double* epart,
+                  cudaStream_t s);
+// Z[p][t][x][(g,b)] = sum_a M1_p[t][x][a] G[p][(g,b)][a] with per-pair operators (stride per pair)
+int simt_expand_mode1_pp(const tx_ctx* c, const float* G, const float* M1, long m1_pair_stride, int nt, float* Z,
+                         int np, cudaStream_t s);
 
 // two-sided (Galerkin) projection (tx_galerkin.cu): B_td = U_d^T D_d A_td and D_d^-1 U_d
 struct GalerkinOps {

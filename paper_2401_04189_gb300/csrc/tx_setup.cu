@@ -17,7 +17,7 @@ namespace {
 __global__ void k_conv_factor(const double* __restrict__ x, const double* __restrict__ w,
                               const double* __restrict__ U, const double* __restrict__ theta,
                               const double* __restrict__ mu, int n, int r, int fold_mu,
-                              double* __restrict__ A64, float* __restrict__ A32) {
+                              double* __restrict__ A64, float* __restrict__ A32, float* __restrict__ C32) {
     extern __shared__ double kv[];   // [n]: row a of C_td
     const int a = blockIdx.x, t = blockIdx.y;
     const double th = theta[t];
@@ -27,6 +27,8 @@ __global__ void k_conv_factor(const double* __restrict__ x, const double* __rest
     }
     __syncthreads();
     const double scale = fold_mu ? mu[t] : 1.0;
+    if (C32)
+        for (int b = threadIdx.x; b < n; b += blockDim.x) C32[((long)t * n + a) * n + b] = (float)(scale * kv[b]);
     for (int k = threadIdx.x; k < r; k += blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < n; ++b) s = fma(kv[b], U[(long)b * r + k], s);
@@ -44,7 +46,7 @@ __global__ void k_conv_factor(const double* __restrict__ x, const double* __rest
 __global__ void k_conv_factor_fe(const double* __restrict__ x, const double* __restrict__ U,
                                  const double* __restrict__ theta, const double* __restrict__ mu, int n, int r,
                                  int fold_mu, int p, int q, const double* __restrict__ gx, const double* __restrict__ gw,
-                                 double* __restrict__ A64, float* __restrict__ A32) {
+                                 double* __restrict__ A64, float* __restrict__ A32, float* __restrict__ C32) {
     extern __shared__ double kv[];   // [n]: row a of C_td
     const int a = blockIdx.x, t = blockIdx.y;
     const double th = theta[t], xa = x[a];
@@ -71,6 +73,8 @@ __global__ void k_conv_factor_fe(const double* __restrict__ x, const double* __r
     }
     __syncthreads();
     const double scale = fold_mu ? mu[t] : 1.0;
+    if (C32)
+        for (int b = threadIdx.x; b < n; b += blockDim.x) C32[((long)t * n + a) * n + b] = (float)(scale * kv[b]);
     for (int k = threadIdx.x; k < r; k += blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < n; ++b) s = fma(kv[b], U[(long)b * r + k], s);
@@ -106,7 +110,7 @@ static void gauss_legendre(int q, double* xg, double* wg) {
     }
 }
 
-int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s) {
+int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s, bool with_c) {
     double hx[64], hw[64];
     gauss_legendre(points, hx, hw);
     double* d = nullptr;
@@ -122,7 +126,8 @@ int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s) {
         const int n = c->n[dd], r = c->r[dd];
         k_conv_factor_fe<<<dim3(n, c->T), 128, sizeof(double) * n, s>>>(c->d_x[dd], c->d_U[dd], c->d_theta, c->d_mu, n, r,
                                                                          dd == 2 ? 1 : 0, order, points, d, d + points,
-                                                                         c->d_A64[dd], c->f_A[dd]);
+                                                                         c->d_A64[dd], c->f_A[dd],
+                                                                         with_c ? c->f_C[dd] : nullptr);
         count_launch();
         if (cudaGetLastError() != cudaSuccess) st = fail(TX_ERR_CUDA, "k_conv_factor_fe launch");
     }
@@ -131,14 +136,37 @@ int setup_factor_matrices_fe(tx_ctx* c, int order, int points, cudaStream_t s) {
     return st;
 }
 
-int setup_factor_matrices(tx_ctx* c, cudaStream_t s) {
+int setup_factor_matrices(tx_ctx* c, cudaStream_t s, bool with_c) {
     for (int d = 0; d < 3; ++d) {
         const int n = c->n[d], r = c->r[d];
         const size_t smem = sizeof(double) * n;
         k_conv_factor<<<dim3(n, c->T), 128, smem, s>>>(c->d_x[d], c->d_w[d], c->d_U[d], c->d_theta, c->d_mu, n, r,
-                                                        d == 2 ? 1 : 0, c->d_A64[d], c->f_A[d]);
+                                                        d == 2 ? 1 : 0, c->d_A64[d], c->f_A[d],
+                                                        with_c ? c->f_C[d] : nullptr);
         TX_LAUNCHED();
     }
+    return TX_OK;
+}
+
+}  // namespace tx
+
+namespace tx {
+
+// float32 copies of the convolution matrices C_td (mu_t folded into mode 3), made on first use
+// (the per-pair path needs them) with the context's current quadrature
+int ensure_conv_matrices(tx_ctx* c, cudaStream_t s) {
+    if (c->c_valid) return TX_OK;
+    for (int d = 0; d < 3; ++d)
+        if (!c->f_C[d]) {
+            if (cudaMalloc(&c->f_C[d], sizeof(float) * (size_t)c->T * c->n[d] * c->n[d]) != cudaSuccess) {
+                cudaGetLastError();
+                c->f_C[d] = nullptr;
+                return fail(TX_ERR_OOM, "convolution matrices");
+            }
+        }
+    if (c->quad_order > 0) TX_TRY(setup_factor_matrices_fe(c, c->quad_order, c->quad_points, s, true));
+    else TX_TRY(setup_factor_matrices(c, s, true));
+    c->c_valid = true;
     return TX_OK;
 }
 

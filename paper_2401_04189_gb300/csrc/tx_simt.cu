@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) k_consume(Dims d, const PairRec* __restri
                                                  float* __restrict__ OUT0, float* __restrict__ OUT1,
                                                  const float* __restrict__ w1, const float* __restrict__ w2,
                                                  const float* __restrict__ w3, int flags,
-                                                 double* __restrict__ epart) {
+                                                 double* __restrict__ epart, long m2_ps, long m3_ps) {
     extern __shared__ float sm[];
     const int ldz = d.r2 + 1;
     const int ld3 = (d.r3 % 2 == 0) ? d.r3 + 1 : d.r3;
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(256) k_consume(Dims d, const PairRec* __restri
     const long zslice = (long)d.r3 * d.r2;
     for (int t = 0; t < nt; ++t) {
         const float* zt = Z + (((long)pl * nt + t) * d.n1 + x) * zslice;
-        const float* m2 = M2 + (long)t * d.n2 * d.r2;
-        const float* m3 = M3 + (long)t * d.n3 * d.r3;
+        const float* m2 = M2 + pl * m2_ps + (long)t * d.n2 * d.r2;
+        const float* m3 = M3 + pl * m3_ps + (long)t * d.n3 * d.r3;
         __syncthreads();
         for (int e = tid; e < d.r3 * d.r2; e += 256) Zs[(e / d.r2) * ldz + e % d.r2] = zt[e];
         for (int e = tid; e < d.n3 * d.r3; e += 256) A3s[(e / d.r3) * ld3 + e % d.r3] = m3[e];
@@ -413,7 +413,8 @@ int simt_expand_consume_blocks(const tx_ctx* c) {
 }
 
 int simt_expand_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const FieldArgs& f, const float* Z,
-                        int nterms, const float* M2, const float* M3, int flags, double* epart, cudaStream_t s) {
+                        int nterms, const float* M2, const float* M3, int flags, double* epart, cudaStream_t s,
+                        long m2_ps, long m3_ps) {
     const Dims d = dims_of(c);
     if (d.n3 > 32 * CZC) return fail(TX_ERR_UNSUPPORTED_SHAPE, "float32 path supports n3 <= 256");
     const int ld3 = (d.r3 % 2 == 0) ? d.r3 + 1 : d.r3;
@@ -422,7 +423,7 @@ int simt_expand_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, co
     dim3 grid((d.n2 + CYT - 1) / CYT, d.n1, np);
     const int ps = prof_begin("consume", s);
     k_consume<<<grid, 256, smem, s>>>(d, recs, p0, Z, nterms, M2, M3, f.SA, f.SB, f.MUL0, f.MUL1, f.OUT0, f.OUT1,
-                                      c->f_w[0], c->f_w[1], c->f_w[2], flags, epart);
+                                      c->f_w[0], c->f_w[1], c->f_w[2], flags, epart, m2_ps, m3_ps);
     prof_end(ps, s);
     TX_LAUNCHED();
     return TX_OK;

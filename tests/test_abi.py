@@ -123,4 +123,5 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.tx_transfer_s_to_u(None, P_(0), 1, P_(0), P_(0)) == -8
     assert L.tx_transfer_map_bytes(None) == 0
     L.tx_transfer_destroy(None)
+    assert L.tx_exchange_apply_sthosvd(None, P_(0), 1, P_(0), 1, P_(0), P_(0)) == -8
     assert L.tx_status_string(-11).decode() == "TX_ERR_NOT_DEFINITE"

@@ -368,6 +368,56 @@ def test_finite_element_quadrature_matches_oracle(prec, order, points):
     assert_close(got0, ref0, prec, "fe-back-to-nodal")
 
 
+@pytest.mark.parametrize("targets", ["self", "subset", "general"])
+def test_per_pair_bases_match_oracle(targets):
+    """Per-pair Tucker bases (sequentially truncated HOSVD of every pair density, Eq.
+    TuckerDecompField) on ragged shapes against the oracle's.  The bases themselves are fixed
+    only up to signs and rotations inside degenerate eigenspaces, so the potential (which
+    depends on the projectors) is compared; float32 Jacobi eigenvectors (orthogonal to about
+    1e-6) and float32 Gram matrices put the bound at 10x the float32 path's (measured 4e-6 to
+    1.1e-5).  A bf16 context runs the same float32 kernels."""
+    P = _P()
+    s = ragged_system()
+    S = O.Setup.from_system(s)
+    occ = to_gpu(s.psi)
+    rng = np.random.default_rng(9)
+    tgt = (s.psi[:3] * 0.7 + 0.2 * rng.standard_normal(s.psi[:3].shape) * np.abs(s.psi[:3]).max()).astype(np.float32)
+    for prec in ("fp32", "bf16"):
+        ctx = P.Context.from_system(s, precision=prec)
+        if targets == "self":
+            ref = O.exchange_apply_sthosvd(s.psi, S, s.r)
+            got = P.tx_exchange_apply_sthosvd(ctx, occ)
+        elif targets == "subset":
+            ref = O.exchange_apply_sthosvd(s.psi, S, s.r, psi_tgt=s.psi[1:4])
+            got = P.tx_exchange_apply_sthosvd(ctx, occ, occ[1:4])
+        else:
+            ref = O.exchange_apply_sthosvd(s.psi, S, s.r, psi_tgt=tgt)
+            got = P.tx_exchange_apply_sthosvd(ctx, occ, to_gpu(tgt))
+        ctx.check_device_error()
+        got = got.cpu().numpy()
+        err, err_e = rel(got, ref), elem_rel(got, ref)[0]
+        _log(dict(what=f"sthosvd-{targets}", prec=prec, frob=err, elem=err_e))
+        assert err < 2e-5 and err_e < 4e-5, (err, err_e)
+    # the shared basis gives a different operator at this rank
+    assert rel(O.exchange_apply(s.psi, S, psi_tgt=None if targets == "self" else
+                                (s.psi[1:4] if targets == "subset" else tgt)), ref) > 1e-3
+
+
+def test_per_pair_bases_at_full_rank_are_exact():
+    """At full rank every projector is the identity, so the result is unique whatever
+    eigenvectors the solver returns; the float32 Jacobi rotations leave the eigenvector matrices
+    orthogonal to about 1e-6 only, which puts the bound at 5x the float32 path's (measured
+    5.5e-6)."""
+    P = _P()
+    s = ragged_system(n=(12, 14, 16), r=(12, 14, 16), T=5, n_orb=3, seed=8)
+    S = O.Setup.from_system(s)
+    ref = O.exchange_apply_sthosvd(s.psi, S, s.r)
+    ctx = P.Context.from_system(s, precision="fp32")
+    got = P.tx_exchange_apply_sthosvd(ctx, to_gpu(s.psi)).cpu().numpy()
+    ctx.check_device_error()
+    assert_close(got, ref, "fp32", "sthosvd-full-rank", scale=5)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("targets", ["self", "subset", "general"])
 def test_galerkin_apply_matches_oracle(prec, targets):
