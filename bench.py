@@ -485,6 +485,18 @@ def pt_secondary(P, W, dev, run_oracle_fn):
         got = out[0:1].double().cpu().numpy()
         res[prec] = dict(value=64 * 64 / (ms / 1000.0), unit="pairs/s", ms_per_step=ms, steps=steps,
                          err_vs_oracle=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        if prec == "fp32":
+            # the same block with per-pair Tucker bases (sequentially truncated HOSVD of every pair
+            # density, float32): one warm-up and one timed apply
+            P.tx_exchange_apply_sthosvd(ctx, psi, out=out)
+            torch.cuda.synchronize()
+            a0.record()
+            P.tx_exchange_apply_sthosvd(ctx, psi, out=out)
+            a1.record()
+            torch.cuda.synchronize()
+            ctx.check_device_error()
+            ms = a0.elapsed_time(a1)
+            res["fp32_per_pair_bases"] = dict(value=64 * 64 / (ms / 1000.0), unit="pairs/s", ms_per_step=ms, steps=1)
         ctx.destroy()
     return dict(workload="Pt-cluster-shaped block", n=96, orbitals=64, rank=40, terms=40,
                 err_sample="row 0 against all 64 orbitals", results=res)
