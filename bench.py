@@ -11,9 +11,11 @@ computed once).  psi (30.2 GB) and W (4.2 GB) are far larger than L2 (129 MB): n
 
 `--workload pt` runs the Pt-cluster-shaped block instead (96^3, 64 orbitals, rank 40, 40 terms,
 one tx_exchange_apply_energy of all 64 against all 64 per step); the default run also reports it
-in `secondary` (bf16, the split-precision tf32x3 form and the float32 CUDA-core form).
+in `secondary` (bf16, the split-precision tf32x3 form and the float32 CUDA-core form), with the
+mesh transfer and the per-pair-bases path.  `--workload batch` times the replay of one captured
+graph over the uneven batch of 16 systems.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32x3|fp32|...] [--workload tio2|pt]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32x3|fp32|...] [--workload tio2|pt|batch]
   python bench.py --impl reference     # the FP64 oracle on the host cores, same metric and workload
 
 Under torchrun each rank applies K to its own copy of the block (independent replicas, weak
@@ -52,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto")
-    ap.add_argument("--workload", default="tio2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="tio2", choices=sorted(WORKLOADS) + ["batch"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
@@ -240,6 +242,8 @@ def main():
     prec = args.precision
     if prec == "auto":
         prec = getattr(P, "DEFAULT_BENCH_PRECISION", "fp32")
+    if args.workload == "batch":
+        return batch_main(args, P, W, dev, prec, world, rank)
     cfg = dict(WORKLOADS[args.workload])
     t_setup = time.perf_counter()
     if args.workload == "tio2":
@@ -406,6 +410,71 @@ def main():
     return 0
 
 
+def batch_main(args, P, W, dev, prec, world, rank):
+    """`--workload batch`: the uneven batch (16 systems, seed 100 + s: n in {48..112}, 8-128
+    orbitals, ranks 20-48, 30-40 terms; every system applies K to all its orbitals), run as one
+    batch plan whose expansion tile plans the autotuner picks, captured in one CUDA graph; the
+    graph replay is timed.  Metric: ordered pair applications of all systems per second."""
+    import tempfile as _tf
+    import torch
+    specs = W.batched_system_specs(16, 100)
+    t0 = time.perf_counter()
+    systems = [W.make_system_on_device("batched", sp["n"], sp["L"], sp["n_orb"], sp["rank"], sp["T"], sp["seed"],
+                                       W.fcc_cluster(8, 2.6), 3, (0.2, 3.0), device=dev) for sp in specs]
+    setup_s = time.perf_counter() - t0
+    ctxs = [P.Context.from_system(s, precision=prec) for s, _ in systems]
+    ordered = sum(psi.shape[0] ** 2 for _, psi in systems)
+    unique = sum(psi.shape[0] * (psi.shape[0] + 1) // 2 for _, psi in systems)
+    flops = sum(flops_per_pair(s.n[0], s.r[0], s.T) * psi.shape[0] * (psi.shape[0] + 1) // 2 for s, psi in systems)
+    with _tf.TemporaryDirectory() as td:
+        t1 = time.perf_counter()
+        plan = P.BatchPlan([dict(ctx=c, psi_occ=psi) for c, (_, psi) in zip(ctxs, systems)],
+                           tune_table=os.path.join(td, "tune.txt"), autotune=True)
+        tune_s = time.perf_counter() - t1
+    stream = torch.cuda.Stream()
+    plan.capture(stream)
+    for _ in range(max(3, args.warmup)):
+        plan.replay(stream)
+    stream.synchronize()
+    for c in ctxs:
+        c.check_device_error()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    steps = args.steps or 3
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(steps):
+        plan.replay(stream)
+    a1.record(stream)
+    stream.synchronize()
+    ck = clocks.stop()
+    for c in ctxs:
+        c.check_device_error()
+    ms = a0.elapsed_time(a1) / steps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    tfs = flops / (ms / 1e3) / 1e12
+    peak = (peaks or {}).get("bf16_tflops_sustained")
+    line = dict(metric=METRIC, value=world * ordered / (ms / 1e3), unit="pairs/s", n_gpus=world, steps=steps,
+                warmup=max(3, args.warmup), ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype=dtype_name(prec), data="synthetic",
+                config=dict(workload="uneven batch of 16 systems", systems=[
+                    dict(n=sp["n"], orbitals=sp["n_orb"], rank=sp["rank"], terms=sp["T"]) for sp in specs],
+                    pairs_ordered=ordered, pairs_unique=unique, precision=prec, graph="one captured graph, replayed",
+                    l2="inputs larger than L2", parallelism=f"replicas x{world}", input_setup_s=round(setup_s, 1),
+                    autotune_s=round(tune_s, 1)),
+                algorithmic_tflops=tfs, algorithmic_frac_of_peak=(tfs / peak) if peak else None,
+                tile_plans=[list(plan.item_plan(i)) for i in range(len(ctxs))], clocks=ck,
+                roofline=None, cpu_baseline=None, e2e=None, gpu_launches=None)
+    plan.destroy()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def transfer_secondary(P, W, ctx, psi_s, out_s, peaks):
     """The transfer between an unstructured finite-element mesh and the structured grid (Eq.
     interpolate) at the TiO2 shape: a hexahedral mesh of [-16, 16]^3 (8^3 cells of 4 bohr, each
@@ -510,7 +579,11 @@ def dtype_name(prec):
 # the current kernel on a smaller case of the same shape (traffic grows in proportion to the
 # pairs), scaled by the pairs a bench launch processes.  Keyed by (kernel, precision, workload);
 # None where no capture of the current kernel exists.
-DRAM_BYTES_PER_PAIR = {}
+# DRAM read + write bytes per distinct pair of the dominant kernel, from one ncu capture of the
+# same kernel (same tile plan) on the TiO2-shaped block cut to 8 targets x 24 occupied orbitals
+# (164 distinct pairs in one launch: 22.16 GB read, 1.95 GB written); the kernel streams each
+# pair's Z, orbitals and W the same way at any block size, so the bytes scale with the pairs.
+DRAM_BYTES_PER_PAIR = {("tc_consume", "bf16", "tio2"): (22.163e9 + 1.954e9) / 164}
 
 
 def roofline(dom, prof, n, r, T, unique, steps, prec, peaks, ck, workload="pt"):

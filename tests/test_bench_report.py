@@ -44,7 +44,9 @@ def test_roofline_of_the_expansion_kernel(monkeypatch):
     assert roof["traffic"] == pytest.approx(22.0e6 * unique * steps / launches)
     # no capture for another workload: no traffic figure
     assert bench.roofline("tc_consume", {"tc_consume": (launches, ms_total)}, n, r, T, unique, steps, "bf16", peaks,
-                          None, "tio2")["traffic"] is None
+                          None, "batch")["traffic"] is None
+    # the TiO2-shaped capture: 164 pairs in one launch, 22.16 GB read and 1.95 GB written
+    assert bench.DRAM_BYTES_PER_PAIR[("tc_consume", "bf16", "tio2")] == pytest.approx(24.117e9 / 164, rel=1e-3)
 
 
 def test_roofline_peaks_per_precision():
