@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--workload", default="tio2", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--expansion-form", type=int, default=0,
+                    help="expansion kernel form (tx_set_expansion_form; 0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
@@ -264,6 +266,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = P.Context.from_system(s, precision=prec)
     ctx.set_workspace_limit(16 << 30)          # pair batches of up to 16 GiB of intermediates
+    if args.expansion_form:
+        P.tx_set_expansion_form(ctx, args.expansion_form)
     out = torch.empty((n_tgt,) + tuple(psi.shape[1:]), dtype=torch.float32, device=dev)
     e = torch.empty((), dtype=torch.float64, device=dev)
     tio2 = args.workload == "tio2"
@@ -394,7 +398,8 @@ def main():
                     ms_per_step=ms_max, higher_is_better=True, scaling="weak", vs_baseline=None,
                     dtype=dtype_name(prec), data="synthetic",
                     config=dict(cfg, occupied=n_occ, targets=n_tgt, pairs_ordered=ordered, pairs_unique=unique,
-                                precision=prec, l2=l2, parallelism=f"replicas x{world}",
+                                precision=prec, expansion_form=args.expansion_form, l2=l2,
+                                parallelism=f"replicas x{world}",
                                 input_setup_s=round(setup_s, 1)),
                     unique_pair_potentials_per_s=world * unique / (ms_max / 1000.0),
                     algorithmic_tflops=world * fl / (ms_max / 1000.0) / 1e12,

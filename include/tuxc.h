@@ -312,19 +312,24 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
  * one CTA per work item.  2 (bf16 only): a persistent form in which converter warps round Y to
  * bf16 into shared memory so that stage 3 also runs as bf16 (measured slower than form 0 on the
  * Pt- and TiO2-shaped blocks: the extra hop lengthens the per-term chain of barriers).  3: form 0
- * without the packing of short y tiles.  All forms give the same result up to float32 summation
- * order (form 2 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..3. */
+ * without the packing of short y tiles.  4 (bf16 only, where r3 rounded up to 8 is a multiple of
+ * 32 and an item holds at most two planes): form 0 with Y rounded to bf16 in place in TMEM by
+ * two groups of converter warps, so that stage 3 runs as a bf16 MMA with A read from TMEM; phi is
+ * double-buffered in TMEM and read by a four-warp epilogue (measured 10% slower than form 0 on
+ * the TiO2-shaped block).  All forms give the same result up to float32 summation order (forms 2
+ * and 4 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..4. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
 /* Host-only description of the expansion kernel (the final contraction of Eq. final with the
  * Hadamard product and the sum over j, the dominant kernel) that tx_exchange_apply and
  * tx_exchange_apply_energy launch for a context of this shape, precision and expansion form
- * (0 to 3, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
+ * (0 to 4, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
  * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 13)
  * values to out:
  *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
  *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items), 4 persistent with
- *       stage 3 in bf16 as well (bf16 precision)
+ *       stage 3 in bf16 from shared memory (form 2), 5 persistent with stage 3 in bf16 from
+ *       TMEM (form 4)
  *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
@@ -332,7 +337,7 @@ int tx_set_expansion_form(tx_ctx* ctx, int form);
  *   tiles where an item covers one y tile; with packed last y tiles, the full tiles plus one item
  *   per group of packed planes)   [12] planes whose last y tiles share one item (0: not packed)
  * For the float32 precision every value is 0.  Returns TX_OK; TX_ERR_INVALID_ARG for NULL
- * arrays, nout < 1, T < 1 or a form outside 0..3; TX_ERR_SHAPE for sizes outside
+ * arrays, nout < 1, T < 1 or a form outside 0..4; TX_ERR_SHAPE for sizes outside
  * 2 <= n_d <= 4096, 1 <= r_d <= n_d; TX_ERR_UNSUPPORTED_PRECISION; TX_ERR_UNSUPPORTED_SHAPE
  * where tx_set_precision would refuse the shape. */
 int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out, int nout);

@@ -799,6 +799,16 @@ __device__ __forceinline__ void s3_mmas_k(uint32_t d, uint32_t aT, uint64_t b3, 
         mma_ts_tf32_w(d, aT + 8u * k, bd, id, k > 0 ? 1u : acc0);
     }
 }
+// stage 3 of the bf16-in-TMEM form: A = Y rounded to bf16 in TMEM (8 columns per K step of 16),
+// B = mu_t A_t3 in bf16, 128-byte swizzled K-major atoms of 4 K steps
+template <int KS>
+__device__ __forceinline__ void s3b_mmas(int ks, uint32_t d, uint32_t aT, uint64_t b3, uint32_t atom16, uint32_t id,
+                                         uint32_t acc0) {
+    const int n = KS > 0 ? KS : ks;
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+        mma_ts_bf16_w(d, aT + 8u * k, b3 + (uint32_t)(k >> 2) * atom16 + (uint32_t)(k & 3) * 2u, id, k > 0 ? 1u : acc0);
+}
 template <int KS>
 __device__ __forceinline__ void s3_mmas(int ks, uint32_t d, uint32_t aT, uint64_t b3, uint64_t b3t, uint32_t atom16,
                                         uint32_t tail16, uint32_t id, uint32_t acc0) {
@@ -1075,15 +1085,19 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
 // stage-3 producer and Z prefetches, 11 stage-3 MMAs of every plane.  Used when every epilogue
 // warp holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
 constexpr int kTpMaxZ = 96;                           // phi registers per epilogue lane
+constexpr int kThreadsTpB = 512;                      // bf16-in-TMEM form: warps 4-7 and 12-15 convert, 0-3 epilogue
 constexpr uint32_t kTpEpiBytes = 0;                   // the epilogue reads the orbitals directly
 
-template <bool S2TF32, int KS2, int KS3>
-__global__ void __launch_bounds__(kThreadsTp, 1)
+template <bool S2TF32, int KS2, int KS3, bool BF3 = false>
+__global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
     k_consume_tp(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ EpiMaps em, ConsumeArgs a) {
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
+    constexpr int NTHR = BF3 ? kThreadsTpB : kThreadsTp;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
     __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, phifree, s3fin[2], ebar[8];
+    __shared__ uint64_t cvtbar[kMaxYBuf];      // BF3: Y of the buffer converted to bf16
+    __shared__ uint64_t phid[2], phif[2];      // BF3: phi buffer b complete / read by the epilogue
     __shared__ uint32_t tmem_base;
     __shared__ double red[2][8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1130,6 +1144,11 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
         for (int b = 0; b < kMaxYBuf; ++b) {
             mbar_init(&s2bar[b], 1);
             mbar_init(&ybar[b], 1);
+            mbar_init(&cvtbar[b], 4);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&phid[b], 1);
+            mbar_init(&phif[b], 4);
         }
         mbar_init(&phidone, 1);
         mbar_init(&phifree, 8);
@@ -1141,7 +1160,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     // Z tile rows that no copy writes feed Y columns that stage 3 multiplies by zeros
     for (int s = 0; s < NL; ++s) {
         uint4* z = (uint4*)Zs(s);
-        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += kThreadsTp) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < (int)(a.z_bytes / 16); i += NTHR) z[i] = make_uint4(0, 0, 0, 0);
     }
     fence_async_smem();
     if (warp == 8) {
@@ -1153,6 +1172,7 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
+    const uint32_t phi_cols = (uint32_t)(a.nT3 * a.n3p);      // BF3: phi is double-buffered
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
     const uint32_t img_atom = a.img_ya_rows * 128u, img_ya_bytes = img_atom * (uint32_t)((a.ks2 + 3) / 4);
     const int na3f = a.ks3 / 4;
@@ -1285,16 +1305,22 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
     } else if (warp == 11) {
         // ---------------- stage-3 MMA issuer: every plane and y tile ----------------
         const uint64_t d0 = sdesc_sw128(0);
-        const uint32_t id3 = idesc_tf32(128, a.n3p);
+        const uint32_t id3 = BF3 ? idesc_bf16(128, a.n3p) : idesc_tf32(128, a.n3p);
         int s3 = 0, yb = 0;
         uint32_t ph3 = 0, yph = 0;
         bool ok = true;
         for (int k = 0; k < nmine && ok; ++k)
             for (int t = 0; t < NT; ++t) {
-                bool w = mbar_wait(&s2bar[yb], yph, a.err, 44);
+                // BF3: Y is read once the converters have rounded it to bf16 in place
+                bool w = mbar_wait(BF3 ? &cvtbar[yb] : &s2bar[yb], yph, a.err, 44);
                 if (w) w = mbar_wait(&full3[s3], ph3, a.err, 48);
-                // the accumulator is free once the epilogue of the previous item holds phi
-                if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
+                // the accumulator is free once the epilogue of the previous item holds phi (BF3:
+                // once the epilogue of item k - 2 has read this item's phi buffer)
+                if constexpr (BF3) {
+                    if (w && t == 0 && k > 1) w = mbar_wait(&phif[k & 1], (uint32_t)(((k - 2) >> 1) & 1), a.err, 50);
+                } else {
+                    if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
+                }
                 ok = __all_sync(0xffffffffu, w);
                 if (!ok) break;
                 tc_fence_after();
@@ -1303,18 +1329,174 @@ __global__ void __launch_bounds__(kThreadsTp, 1)
                 const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
                 const uint32_t acc0 = t > 0 ? 1u : 0u;
                 for (int p = 0; p < BX; ++p)
-                    for (int i = 0; i < a.nY; ++i)
-                        s3_mmas<KS3>(a.ks3, tPhi + (uint32_t)((p * a.nY + i) * a.n3p), tY + (uint32_t)(i * a.ycol_tile + p * a.gs),
-                                     b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
+                    for (int i = 0; i < a.nY; ++i) {
+                        const uint32_t dT = tPhi + (BF3 ? (uint32_t)(k & 1) * phi_cols : 0u) +
+                                            (uint32_t)((p * a.nY + i) * a.n3p);
+                        const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
+                        if constexpr (BF3)
+                            s3b_mmas<KS3>(a.ks3, dT, aT, b3, b3_atom >> 4, id3, acc0);
+                        else
+                            s3_mmas<KS3>(a.ks3, dT, aT, b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
+                    }
                 mma_commit_w(&ybar[yb]);
                 mma_commit_w(&empty3[s3]);
-                if (t == NT - 1) mma_commit_w(&phidone);
+                if (t == NT - 1) mma_commit_w(BF3 ? &phid[k & 1] : &phidone);
                 if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
                 if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
         // the CTA must not release TMEM while these MMAs run
         mma_commit_w(&s3fin[1]);
         mbar_drain(&s3fin[1], 0, a.err);
+    } else if (BF3 && warp >= 4) {
+        // ---------------- BF3 converters: Y -> bf16 in place ----------------
+        // Two groups of four warps (4-7 and 12-15), one warp per TMEM lane quadrant, take
+        // alternate Gaussian terms.  A plane's float32 Y is read into registers 64 columns at a
+        // time, rounded to bf16 pairs and written back into the first 32 of those columns (chunk
+        // c into columns 32c .. 32c + 31, which chunks 0 .. c have already been read from), so
+        // stage 3 finds a K-major bf16 A operand in the first gs / 2 columns of the plane.
+        const int grp = warp >= 12 ? 1 : 0;
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        int yb = 0, g = 0;
+        uint32_t yph = 0;
+        bool ok = true;
+        for (int k = 0; k < nmine && ok; ++k)
+            for (int t = 0; t < NT; ++t, ++g) {
+                if ((g & 1) == grp) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&s2bar[yb], yph, a.err, 51));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t tY = tmem + lanes + (uint32_t)yb * a.y_cols;
+                    for (int i = 0; i < a.nY; ++i)
+                        for (int p = 0; p < BX; ++p) {
+                            const uint32_t base = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
+                            for (int c = 0; c < a.gs / 64; ++c) {
+                                uint32_t v[4][16], o[2][16];
+                                tmem_ld16(base + 64u * c, v[0]);
+                                tmem_ld16(base + 64u * c + 16u, v[1]);
+                                tmem_ld16(base + 64u * c + 32u, v[2]);
+                                tmem_ld16(base + 64u * c + 48u, v[3]);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                    for (int j = 0; j < 8; ++j) {
+                                        o[h][j] = pack_bf16x2(v[2 * h][2 * j], v[2 * h][2 * j + 1]);
+                                        o[h][8 + j] = pack_bf16x2(v[2 * h + 1][2 * j], v[2 * h + 1][2 * j + 1]);
+                                    }
+                                tmem_st16(base + 32u * c, o[0]);
+                                tmem_st16(base + 32u * c + 16u, o[1]);
+                            }
+                            if (a.gs % 64) {           // a last 32-column chunk
+                                const int c = a.gs / 64;
+                                uint32_t v0[16], v1[16], o[16];
+                                tmem_ld16(base + 64u * c, v0);
+                                tmem_ld16(base + 64u * c + 16u, v1);
+                                tmem_ld_wait();
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    o[j] = pack_bf16x2(v0[2 * j], v0[2 * j + 1]);
+                                    o[8 + j] = pack_bf16x2(v1[2 * j], v1[2 * j + 1]);
+                                }
+                                tmem_st16(base + 32u * c, o);
+                            }
+                        }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&cvtbar[yb]);
+                }
+                if (++yb == NYB) { yb = 0; yph ^= 1; }
+            }
+    } else if (BF3) {
+        // ---------------- BF3 epilogue, warps 0-3 (one lane quadrant each) ----------------
+        // phi is double-buffered in TMEM, so the epilogue reads it chunk by chunk (16 columns)
+        // while the next item accumulates into the other buffer, and releases the buffer when
+        // the item is done.  Each lane walks its own grid row as in the other epilogue.
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        for (int k = 0; k < nmine; ++k) {
+            const bool live = mbar_wait_idle(&phid[k & 1], (uint32_t)((k >> 1) & 1), a.err, 45);
+            tc_fence_after();
+            int pl, slab, iy;
+            item_of(k, pl, slab, iy);
+            const bool tail = is_tail(iy);
+            const int x0 = tail ? slab * a.tailp : slab * BX;
+            const PairRec rec = a.recs[a.p0 + pl];
+            const bool en = (a.flags & EPI_ENERGY) != 0;
+            const bool o0 = (a.flags & EPI_OUT) && a.OUT0 && rec.o0 >= 0;
+            const bool o1 = (a.flags & EPI_OUT) && a.OUT1 && rec.o1 >= 0;
+            const bool need0 = o0 || (en && a.emul), need1 = o1 || (en && a.emul);
+            const long N3 = (long)a.n1 * a.n2 * a.n3;
+            double e = 0.0;
+            for (int jt = 0; live && jt < a.nT3; ++jt) {
+                int x, y;
+                bool rowin;
+                if (tail) {
+                    const int l = warp * 32 + lane, pp = l / a.tail_r8, yy = l - pp * a.tail_r8;
+                    x = x0 + pp;
+                    y = (a.nyi - 1) * 128 + yy;
+                    rowin = pp < a.tailp && yy < a.tail_rows && x < a.n1;
+                } else {
+                    const int p = jt / a.nY;
+                    x = x0 + p;
+                    y = (iy + jt - p * a.nY) * 128 + warp * 32 + lane;
+                    rowin = x < a.n1 && y < a.n2;
+                }
+                if (!(need0 || need1) || !__any_sync(0xffffffffu, rowin)) continue;
+                const float wxy = rowin ? a.w1[x] * a.w2[y] : 0.f;
+                const long rowoff = rowin ? ((long)x * a.n2 + y) * a.n3 : 0;
+                const float* mul0 = need0 ? a.MUL0 + (long)rec.m0 * N3 + rowoff : nullptr;
+                const float* mul1 = need1 ? a.MUL1 + (long)rec.m1 * N3 + rowoff : nullptr;
+                float* out0 = o0 ? a.OUT0 + (long)rec.o0 * N3 + rowoff : nullptr;
+                float* out1 = o1 ? a.OUT1 + (long)rec.o1 * N3 + rowoff : nullptr;
+                const uint32_t tb = tPhi + lanes + (uint32_t)(k & 1) * phi_cols + (uint32_t)(jt * a.n3p);
+                for (int zc = 0; zc < a.n3; zc += 16) {
+                    uint32_t ph[16];
+                    tmem_ld16(tb + (uint32_t)zc, ph);
+                    tmem_ld_wait();
+                    if (!rowin) continue;
+                    float4 m0v[4], m1v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int z = zc + 4 * c;
+                        m0v[c] = (need0 && z < a.n3) ? __ldg((const float4*)(mul0 + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        m1v[c] = (need1 && z < a.n3) ? __ldg((const float4*)(mul1 + z)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    float eb = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int z = zc + 4 * c;
+                        if (z >= a.n3) break;                    // n3 % 4 == 0
+                        const float4 phi = make_float4(__uint_as_float(ph[4 * c]), __uint_as_float(ph[4 * c + 1]),
+                                                       __uint_as_float(ph[4 * c + 2]), __uint_as_float(ph[4 * c + 3]));
+                        const float4 w3 = *(const float4*)(a.w3 + z);
+                        const float4 wv = make_float4(wxy * w3.x, wxy * w3.y, wxy * w3.z, wxy * w3.w);
+                        float4 f = phi;
+                        if (a.flags & EPI_MULW) f = make_float4(f.x * wv.x, f.y * wv.y, f.z * wv.z, f.w * wv.w);
+                        const float4 m0 = m0v[c], m1 = m1v[c];
+                        if (o0) atomicAdd((float4*)(out0 + z), make_float4(-m0.x * f.x, -m0.y * f.y, -m0.z * f.z, -m0.w * f.w));
+                        if (o1) atomicAdd((float4*)(out1 + z), make_float4(-m1.x * f.x, -m1.y * f.y, -m1.z * f.z, -m1.w * f.w));
+                        if (en && a.emul)
+                            eb += wv.x * m1.x * m0.x * phi.x + wv.y * m1.y * m0.y * phi.y + wv.z * m1.z * m0.z * phi.z +
+                                  wv.w * m1.w * m0.w * phi.w;
+                    }
+                    e += (double)eb;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&phif[k & 1]);
+            if (a.flags & EPI_ENERGY) {
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+                if (lane == 0) red[k & 1][warp] = e * rec.ew;
+            }
+            // the four epilogue warps meet once per item (named barrier 1): energy partial
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if ((a.flags & EPI_ENERGY) && warp == 0 && lane == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < 4; ++w) sum += red[k & 1][w];
+                a.epart[(long)blockIdx.x + (long)k * gridDim.x] = sum;
+            }
+        }
     } else {
         // ---------------- epilogue warps 0-7 ----------------
         // With two tiles per item, warp (q, h) takes tile h; with one tile, the two warps of a
@@ -1929,6 +2111,7 @@ struct ConsumePlan {
     // planes (tail_r8 = tail_rows rounded up to 8 rows each) share one item (0: not packed)
     int tailp, tail_r8, tail_rows;
     uint32_t sya_rows, sya;  // rows per K atom and bytes of the A_t2 tile in a shared-memory stage
+    bool bf3;                // persistent form with Y rounded to bf16 in TMEM: stage 3 in bf16 (form 4)
     uint32_t img_stride() const { return ya + b3 + (uint32_t)tailp * ya; }
     int items_per_slab_pair(int n1) const {   // work items per pair
         return tailp ? (n1 / bx) * (nyi - 1) + (n1 + tailp - 1) / tailp : ((n1 + bx - 1) / bx) * (ts ? nyi : 1);
@@ -1966,14 +2149,18 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     }
     p->npc = std::min(bx, 256 / p->gs);
     p->ks2 = (r2 + MK2 - 1) / MK2;
-    p->ks3 = (r3 + 7) / 8;
+    // form 4 (bf16): stage 3 takes Y rounded to bf16 in TMEM, 32 columns at a time
+    // (the persistent kernel only: at most two planes per item)
+    p->bf3 = !tf32 && c->consume_form == 4 && p->gs % 32 == 0 && bx <= 2 && bx * p->nY <= 2;
+    p->ks3 = p->bf3 ? (r3 + 15) / 16 : (r3 + 7) / 8;
     // columns of one y tile of Y: each plane chunk writes pad16(planes * gs) columns from p0 * gs
     p->ycol_tile = 0;
     for (int p0 = 0; p0 < bx; p0 += p->npc)
         p->ycol_tile = std::max(p->ycol_tile, p0 * p->gs + pad16(std::min(p->npc, bx - p0) * p->gs));
     p->y_cols = (uint32_t)(p->nY * p->ycol_tile);
     p->nT3 = bx * p->nY;
-    const uint32_t phi = (uint32_t)(p->nT3 * p->n3p);
+    // (form 4 keeps two phi buffers, so that its epilogue reads one while the next item fills the other)
+    const uint32_t phi = (uint32_t)(p->nT3 * p->n3p) * (p->bf3 ? 2u : 1u);
     // one Y buffer per load stage when TMEM allows (the kernel then needs no Y-buffer barrier)
     p->nyb = std::min(nload, tcc::kMaxYBuf);
     while (p->nyb > 2 && p->nyb * p->y_cols + phi > 512) --p->nyb;
@@ -1989,7 +2176,8 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     p->z_rows = (uint32_t)p->ycol_tile;         // rows every stage-2 MMA may read
     p->ya = (uint32_t)na2 * p->ya_rows * 128u;
     p->zb = (uint32_t)na2 * p->z_rows * 128u;
-    p->b3 = (uint32_t)(p->ks3 / 4) * p->n3p * 128u + (uint32_t)(p->ks3 % 4) * p->n3p * 32u;
+    p->b3 = p->bf3 ? (uint32_t)((p->ks3 + 3) / 4) * p->n3p * 128u
+                   : (uint32_t)(p->ks3 / 4) * p->n3p * 128u + (uint32_t)(p->ks3 % 4) * p->n3p * 32u;
     // two rings: nload stages of [A_t2][Z] (stage 2), then as many stages of [mu_t A_t3]
     // (stage 3, up to kMaxLoad) as shared memory holds: its loads start only when stage 3 of
     // an earlier term has finished, so this ring needs the deeper lead
@@ -2315,14 +2503,15 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
     ConsumePlan p;
     if (!choose_plan(c, tf32, split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
     const TpSplit t = (p.ts && !p.tb) ? tp_split(c, p, false, false) : TpSplit{};
-    const int v[13] = {p.tb ? 4 : (t.on ? 3 : (p.ts ? 2 : 1)),
+    const int v[13] = {p.tb ? 4 : (t.on ? (p.bf3 ? 5 : 3) : (p.ts ? 2 : 1)),
                        p.bx,
                        t.on ? t.nl1 : p.nload,
                        p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
                        p.ts ? p.nyb : 0,
                        (int)p.tmem_cols,
                        (int)(t.on ? t.smem : p.smem),
-                       p.tb ? tcc::kThreadsTb : (t.on ? tcc::kThreadsTp : (p.ts ? tcc::kThreadsTs : tcc::kThreads)),
+                       p.tb ? tcc::kThreadsTb
+                            : (t.on ? (p.bf3 ? tcc::kThreadsTpB : tcc::kThreadsTp) : (p.ts ? tcc::kThreadsTs : tcc::kThreads)),
                        p.ks2,
                        p.ks3,
                        p.n3p,
@@ -2383,6 +2572,39 @@ int tc_build_operand_image(tx_ctx* c, cudaStream_t s) {
     // the tile shapes below depend on (n, r, precision) only, not on the slab or the stages
     const int n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2], T = c->T, eb = op->esize;
     op->img_stride = p.img_stride();
+    if (p.bf3) {
+        // [A_t2 tile][mu_t A_t3 tile in bf16] per term (then the packed-tile windows)
+        if (cudaMalloc(&op->img, (size_t)T * op->img_stride) != cudaSuccess) {
+            cudaGetLastError();
+            op->img = nullptr;
+            return fail(TX_ERR_OOM, "expansion operator image");
+        }
+        CUtensorMap mA2b, mA3b;
+        const int l2 = ldk(r2, 2), l3 = ldk(r3, 2);
+        TX_TRY(make_map(&mA2b, op->st.A2, 2, l2, n2, T, l2, (uint64_t)n2 * l2, 64, (uint32_t)p.n2p));
+        TX_TRY(make_map(&mA3b, op->st.A3, 2, l3, n3, T, l3, (uint64_t)n3 * l3, 64, (uint32_t)p.n3p));
+        tcc::ImageArgs g{};
+        g.ks2 = p.ks2;
+        g.ks3 = p.ks3;
+        g.n3p = p.n3p;
+        g.ya_rows = p.ya_rows;
+        g.ya_bytes = p.ya;
+        g.b3_bytes = p.b3;
+        g.stride = op->img_stride;
+        g.img = (uint8_t*)op->img;
+        g.err = c->d_err;
+        const int smem = (int)(p.ya + p.b3) + 1024;
+        cudaFuncSetAttribute(tcc::k_operand_image_b16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        tcc::k_operand_image_b16<0><<<(unsigned)T, 32, smem, s>>>(mA2b, mA3b, g);
+        TX_LAUNCHED();
+        if (p.tailp) {
+            tcc::k_tail_windows<<<dim3((unsigned)T, (unsigned)p.tailp), 256, 0, s>>>(
+                (uint8_t*)op->img, op->img_stride, p.ya + p.b3, p.ya, p.ya_rows, (p.ks2 + 3) / 4, 128 * (p.nyi - 1),
+                p.tail_rows, p.tail_r8);
+            TX_LAUNCHED();
+        }
+        return TX_OK;
+    }
     if (cudaMalloc(&op->img, (size_t)T * op->img_stride) != cudaSuccess) {
         cudaGetLastError();
         op->img = nullptr;
@@ -2533,7 +2755,11 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         // rank runs the dispatching form (see s2_mmas / s3_mmas)
         using Kern = void (*)(const CUtensorMap, const tcc::EpiMaps, tcc::ConsumeArgs);
         Kern kern;
-        if (tp) {
+        if (tp && p.bf3) {
+            kern = (Kern)tcc::k_consume_tp<false, 0, 0, true>;
+            if (p.ks2 == 4 && p.ks3 == 4) kern = tcc::k_consume_tp<false, 4, 4, true>;
+            if (p.ks2 == 3 && p.ks3 == 3) kern = tcc::k_consume_tp<false, 3, 3, true>;
+        } else if (tp) {
             kern = op->tf32 ? (Kern)tcc::k_consume_tp<true, 0, 0> : (Kern)tcc::k_consume_tp<false, 0, 0>;
 #define TX_TP_CASE(TF, K2, K3) \
     if (op->tf32 == TF && p.ks2 == K2 && p.ks3 == K3) kern = tcc::k_consume_tp<TF, K2, K3>;
@@ -2571,7 +2797,8 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         }
         const int ps = prof_begin("tc_consume", s);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, tp ? tcc::kThreadsTp : tcc::kThreadsTs, smem, s>>>(mZ, em, a);
+        if (p.bf3 && !tp) return fail(TX_ERR_UNSUPPORTED_SHAPE, "bf16 stage 3 in TMEM needs the persistent kernel");
+        kern<<<grid, tp ? (p.bf3 ? tcc::kThreadsTpB : tcc::kThreadsTp) : tcc::kThreadsTs, smem, s>>>(mZ, em, a);
         prof_end(ps, s);
         TX_LAUNCHED();
         return TX_OK;

@@ -284,7 +284,7 @@ def test_expansion_forms_agree(prec, system):
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
         assert_close(outs[0][3:4], ref, prec, "forms-pt8")
     with pytest.raises(P.TuckerExchangeError):
-        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 4)
+        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 5)
 
 
 @pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent"), (64, "tf32", "persistent"),
@@ -318,7 +318,8 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
     last tiles of `tail` planes into one 128-row item (each plane's stage-2 operand a zero-padded
     window of A_t2).  27 planes in groups of 5 leave a partial group of 2; 150 rows leave a
     22-row tail (two zero rows of padding per plane).  Apply and energy against the unpacked form
-    (form 3: the same arithmetic per element, so float32 summation order only) and the oracle."""
+    (form 3: the same arithmetic per element, so float32 summation order only) and the oracle;
+    for bf16 also form 4 (stage 3 in bf16 from TMEM) against the oracle."""
     P = _P()
     d = P.tx_describe_expansion_plan(n, r, 6, prec)
     assert d["kernel"] == "persistent" and d["tail_planes"] == tail
@@ -326,7 +327,8 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
     S = O.Setup.from_system(s)
     occ = to_gpu(s.psi)
     outs, energies = [], []
-    for form in (0, 3):
+    forms = (0, 3, 4) if prec == "bf16" else (0, 3)
+    for form in forms:
         ctx = P.Context.from_system(s, precision=prec)
         P.tx_set_expansion_form(ctx, form)
         outs.append(P.tx_exchange_apply(ctx, occ).cpu().numpy())
@@ -337,6 +339,11 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
     assert abs(energies[0] - energies[1]) <= 1e-5 * abs(energies[1])
     ref = O.exchange_apply(s.psi, S)
     assert_close(outs[0], ref, prec, f"packed-{n[0]}x{n[1]}")
+    if prec == "bf16":
+        # form 4: Y rounded to bf16 in TMEM, stage 3 in bf16 (packed tiles, two phi buffers)
+        assert P.tx_describe_expansion_plan(n, r, 6, prec, 4)["kernel"] == "persistent_bf16_tmem"
+        assert_close(outs[2], ref, prec, f"packed-{n[0]}x{n[1]}-bf16tmem")
+        assert abs(energies[2] - energies[0]) <= E_TOL[prec] * abs(energies[0])
     e_ref = O.exchange_energy(s.psi, S)
     log_energy(prec, f"packed-{n[0]}x{n[1]}", energies[0], e_ref)
     assert abs(energies[0] - e_ref) / abs(e_ref) < E_TOL[prec]

@@ -85,7 +85,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
     split = prec.endswith("x3")
     mk = 8 if tf32 else 16
     planned = 0
-    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2, 3)):
+    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2, 3, 4)):
         rr = tuple(min(r, v) for v in n)
         try:
             d = P.tx_describe_expansion_plan(n, rr, T, prec, form)
@@ -101,14 +101,14 @@ def test_every_plan_respects_the_hardware_limits(prec):
         if tp:                                  # packed last y tiles: full tiles, then tail groups
             nyf = -(-n[1] // 128)
             rows = n[1] - 128 * (nyf - 1)
-            assert d["planes"] == 1 and tp == 128 // pad8(rows) >= 2 and form in (0, 2), key
+            assert d["planes"] == 1 and tp == 128 // pad8(rows) >= 2 and form in (0, 2, 4), key
             assert d["items_per_pair"] == n[0] * (nyf - 1) + -(-n[0] // tp), key
             yi = nyf
         else:
             yi = d["items_per_pair"] // slabs   # work items per slab: 1, or one per 128-row y tile
             assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
         if yi > 1:
-            assert d["kernel"] in ("persistent", "persistent_bf16") and form in (0, 2, 3), key
+            assert d["kernel"] in ("persistent", "persistent_bf16", "persistent_bf16_tmem") and form in (0, 2, 3, 4), key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -123,10 +123,16 @@ def test_every_plan_respects_the_hardware_limits(prec):
             assert d["ksteps3"] == -(-rr[2] // 16) and d["ybuffers"] >= 2 and d["stages3"] >= 2, key
             assert d["planes"] <= (2 if yi > 1 else 4) and d["stages2"] <= 4, key
             continue
+        if d["kernel"] == "persistent_bf16_tmem":
+            # Y rounded to bf16 in TMEM by eight converter warps, two phi buffers, four epilogue warps
+            assert prec == "bf16" and form == 4 and d["threads"] == 512, key
+            assert d["ksteps3"] == -(-rr[2] // 16) and pad8(rr[2]) % 32 == 0, key
+            assert d["ybuffers"] >= 2 and d["stages3"] >= 2 and d["planes"] <= 2, key
+            continue
         assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
         if d["kernel"] == "persistent":
-            assert form in (0, 2, 3) and d["threads"] == 384, key
+            assert form in (0, 2, 3, 4) and d["threads"] == 384, key
             assert d["planes"] <= 2 and d["stages2"] <= 4, key
             tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
             assert tiles <= 2, key                                  # at most one phi tile per epilogue warp
@@ -146,7 +152,7 @@ def test_shapes_the_tensor_cores_cannot_take_are_refused():
         P.tx_describe_expansion_plan((12, 13, 300), (3, 4, 5), 3, "fp32")    # float32 kernels: n3 <= 256
     assert ei.value.status == -9
     for bad, status in [(((1, 8, 8), (1, 1, 1), 3, "bf16", 0), -2), (((8, 8, 8), (9, 1, 1), 3, "bf16", 0), -2),
-                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 4), -1)]:
+                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 5), -1)]:
         with pytest.raises(P.TuckerExchangeError) as ei:
             P.tx_describe_expansion_plan(*bad)
         assert ei.value.status == status, bad
