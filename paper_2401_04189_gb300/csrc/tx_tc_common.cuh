@@ -55,20 +55,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for the phase with the given parity.  Gives up after kWaitLimitNs (or as soon as
-// another thread has given up), records (code, site) in err[0..1] and returns false.
+// Waits for the phase with the given parity.  Gives up after the wait limit (or once another
+// thread has given up), records (code, site) in err[0..1] and returns false.  The error word
+// and the limit live in global memory, so they are read only every 1,024 probes: a load that
+// misses stalls the warp for hundreds of cycles, during which it would not see its phase
+// complete (each probe may suspend the thread briefly, so the checks still come often).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    const uint64_t lim = wait_limit_ns(err);
+    uint32_t n = 0;
     while (true) {
-#pragma unroll 1
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (*(volatile int*)err != 0) return false;
-        if (globaltimer() - t0 > lim) {
-            if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
-            return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((++n & 1023u) == 0) {
+            if (*(volatile int*)err != 0) return false;
+            if (globaltimer() - t0 > wait_limit_ns(err)) {
+                if (atomicCAS(err, 0, 1) == 0) atomicExch(err + 1, site);
+                return false;
+            }
         }
     }
 }
