@@ -424,8 +424,10 @@ def batch_main(args, P, W, dev, prec, world, rank):
     import torch
     specs = W.batched_system_specs(16, 100)
     t0 = time.perf_counter()
-    systems = [W.make_system_on_device("batched", sp["n"], sp["L"], sp["n_orb"], sp["rank"], sp["T"], sp["seed"],
-                                       W.fcc_cluster(8, 2.6), 3, (0.2, 3.0), device=dev) for sp in specs]
+    systems = []
+    for sp in specs:
+        a, kw = W.batched_system_args(sp)
+        systems.append(W.make_system_on_device("batched", *a, device=dev, **kw))
     setup_s = time.perf_counter() - t0
     ctxs = [P.Context.from_system(s, precision=prec) for s, _ in systems]
     ordered = sum(psi.shape[0] ** 2 for _, psi in systems)
@@ -459,6 +461,17 @@ def batch_main(args, P, W, dev, prec, world, rank):
     for c in ctxs:
         c.check_device_error()
     ms = a0.elapsed_time(a1) / steps
+    # for comparison: the same systems as separate calls, one after another on one stream
+    outs = [torch.empty_like(psi) for _, psi in systems]
+    with torch.cuda.stream(stream):
+        for rep in range(2):
+            if rep == 1:
+                a0.record(stream)
+            for c, (_, psi), o in zip(ctxs, systems, outs):
+                P.tx_exchange_apply(c, psi, out=o, stream=stream)
+        a1.record(stream)
+    stream.synchronize()
+    seq_ms = a0.elapsed_time(a1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     tfs = flops / (ms / 1e3) / 1e12
@@ -473,6 +486,7 @@ def batch_main(args, P, W, dev, prec, world, rank):
                     autotune_s=round(tune_s, 1)),
                 algorithmic_tflops=tfs, algorithmic_frac_of_peak=(tfs / peak) if peak else None,
                 tile_plans=[list(plan.item_plan(i)) for i in range(len(ctxs))], clocks=ck,
+                sequential_calls_ms=seq_ms,
                 roofline=None, cpu_baseline=None, e2e=None, gpu_launches=None)
     plan.destroy()
     if rank == 0:

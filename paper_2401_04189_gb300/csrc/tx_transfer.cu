@@ -32,6 +32,7 @@ struct tx_transfer {
     int n[3];
     int n_nodes, n_cells, pu, ps;
     long n_map;                // structured nodes (every one is mapped to a cell)
+    int max_cell;              // most structured nodes in one cell
     int* d_cell_start;         // [n_cells + 1] offsets into snode / N
     int* d_snode;              // [n_map] flat structured index of each mapped node, grouped by cell
     float* d_N;                // [n_map][(pu + 1)^3]
@@ -47,21 +48,25 @@ namespace {
 constexpr uint32_t kTransferMagic = 0x54555446u;
 constexpr int kChunk = 32;     // orbitals per pass
 
-// One CTA per cell: the cell's orbital rows (kUChunk orbitals at a time) are staged in shared
-// memory; each thread takes one structured node of the cell, keeps its N row in registers and
-// writes that node for every orbital of the chunk (neighbouring threads on neighbouring nodes,
-// so each orbital's writes are runs along z).
+// One CTA per (cell, block of kUNodes of its structured nodes): the cell's orbital rows
+// (kUChunk orbitals at a time) are staged in shared memory; each thread takes one structured
+// node, keeps its N row in registers and writes that node for every orbital of the chunk
+// (neighbouring threads on neighbouring nodes, so each orbital's writes are runs along z).
+// Splitting the large cells over several CTAs keeps all SMs busy when coarse and refined cells
+// hold very different numbers of nodes.
 constexpr int kUChunk = 128;
+constexpr int kUNodes = 256;
 
 template <int NB>
 __global__ void __launch_bounds__(256) k_u_to_s(const int* __restrict__ cell_start, const int* __restrict__ snode,
                                                 const float* __restrict__ N, const int* __restrict__ conn,
                                                 const float* __restrict__ psi_u, int n_orb, long n3,
                                                 float* __restrict__ psi_s) {
-    extern __shared__ float v[];   // [NB][kUChunk]
+    extern __shared__ __align__(16) float v[];   // [NB][kUChunk]
     const int c = blockIdx.x;
-    const int k0 = cell_start[c], m = cell_start[c + 1] - k0;
-    if (m == 0) return;
+    const int kc = cell_start[c], kb = blockIdx.y * kUNodes;
+    const int k0 = kc + kb, m = min(kUNodes, cell_start[c + 1] - k0);
+    if (m <= 0) return;
     for (int i0 = 0; i0 < n_orb; i0 += kUChunk) {
         const int ni = min(kUChunk, n_orb - i0);
         __syncthreads();
@@ -76,11 +81,22 @@ __global__ void __launch_bounds__(256) k_u_to_s(const int* __restrict__ cell_sta
 #pragma unroll
             for (int b = 0; b < NB; ++b) w[b] = __ldg(Nk + b);
             float* dst = psi_s + (long)i0 * n3 + snode[k0 + k];
-            for (int ii = 0; ii < ni; ++ii) {
-                float s = 0.f;
+            // four orbitals per pass: one 16-byte shared-memory broadcast feeds four FMAs (the
+            // staged chunk is zero beyond ni, so the reads stay inside it; the stores are guarded)
+            for (int ii = 0; ii < ni; ii += 4) {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-                for (int b = 0; b < NB; ++b) s = fmaf(w[b], v[b * kUChunk + ii], s);
-                dst[(long)ii * n3] = s;
+                for (int b = 0; b < NB; ++b) {
+                    const float4 q = *reinterpret_cast<const float4*>(v + b * kUChunk + ii);
+                    s0 = fmaf(w[b], q.x, s0);
+                    s1 = fmaf(w[b], q.y, s1);
+                    s2 = fmaf(w[b], q.z, s2);
+                    s3 = fmaf(w[b], q.w, s3);
+                }
+                dst[(long)ii * n3] = s0;
+                if (ii + 1 < ni) dst[(long)(ii + 1) * n3] = s1;
+                if (ii + 2 < ni) dst[(long)(ii + 2) * n3] = s2;
+                if (ii + 3 < ni) dst[(long)(ii + 3) * n3] = s3;
             }
         }
     }
@@ -262,6 +278,8 @@ extern "C" int tx_transfer_create(tx_transfer** out, tx_ctx* c, int order_s, con
     t->pu = pu;
     t->ps = ps;
     t->n_map = (long)snode.size();
+    t->max_cell = 0;
+    for (int cc = 0; cc < n_cells; ++cc) t->max_cell = std::max(t->max_cell, cell_start[cc + 1] - cell_start[cc]);
     std::vector<int> connv(conn, conn + (long)n_cells * nb);
     int st = upload(&t->d_cell_start, cell_start, "cell offsets");
     if (st == TX_OK) st = upload(&t->d_snode, snode, "structured nodes");
@@ -287,10 +305,11 @@ extern "C" int tx_transfer_u_to_s(tx_transfer* t, const float* psi_u, int n_orb,
     cudaStream_t s = (cudaStream_t)stream;
     const long N3 = (long)t->n[0] * t->n[1] * t->n[2];
     const size_t sm1 = sizeof(float) * 8 * kUChunk, sm2 = sizeof(float) * 27 * kUChunk, sm3 = sizeof(float) * 64 * kUChunk;
+    const dim3 grid((unsigned)t->n_cells, (unsigned)std::max(1, (t->max_cell + kUNodes - 1) / kUNodes));
     switch (t->pu) {
-        case 1: k_u_to_s<8><<<t->n_cells, 256, sm1, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
-        case 2: k_u_to_s<27><<<t->n_cells, 256, sm2, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
-        default: k_u_to_s<64><<<t->n_cells, 256, sm3, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
+        case 1: k_u_to_s<8><<<grid, 256, sm1, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
+        case 2: k_u_to_s<27><<<grid, 256, sm2, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
+        default: k_u_to_s<64><<<grid, 256, sm3, s>>>(t->d_cell_start, t->d_snode, t->d_N, t->d_conn, psi_u, n_orb, N3, psi_s); break;
     }
     TX_LAUNCHED();
     return TX_OK;

@@ -24,7 +24,7 @@ __all__ = [
     "uniform_grid", "fcc_cluster", "rutile_cluster", "gaussian_sum_orbitals",
     "lowdin_orthonormalise", "density_hosvd_basis", "exp_sum_inverse_r",
     "System", "make_system", "make_system_on_device", "config_tio2_on_device", "CONFIGS",
-    "batched_system_specs", "fe_mesh", "gaussian_sum_at_points",
+    "batched_system_specs", "batched_system_args", "fe_mesh", "gaussian_sum_at_points",
 ]
 
 
@@ -371,9 +371,23 @@ def batched_system_specs(count=16, base_seed=100):
     return specs
 
 
+# orbitals of the uneven batch: Gaussian sums on 4 of the 32 atoms of an fcc cluster, 3 per atom,
+# so that blocks of up to 128 orbitals stay linearly independent (the overlap matrix of 128
+# orbitals drawn on one 8-atom cluster is singular to working precision)
+BATCH_CENTRES, BATCH_GAUSS_PER_CENTRE, BATCH_CENTRES_PER_ORBITAL = 32, 3, 4
+
+
+def batched_system_args(spec):
+    """Positional and keyword arguments of make_system / make_system_on_device for one system
+    of the uneven batch."""
+    return ((spec["n"], spec["L"], spec["n_orb"], spec["rank"], spec["T"], spec["seed"],
+             fcc_cluster(BATCH_CENTRES, 2.6), BATCH_GAUSS_PER_CENTRE, (0.2, 3.0)),
+            dict(centres_per_orbital=BATCH_CENTRES_PER_ORBITAL))
+
+
 def config_batched_system(spec) -> System:
-    return make_system("batched", spec["n"], spec["L"], spec["n_orb"], spec["rank"], spec["T"],
-                       spec["seed"], fcc_cluster(8, 2.6), 3, (0.2, 3.0))
+    a, kw = batched_system_args(spec)
+    return make_system("batched", *a, **kw)
 
 
 CONFIGS = {
