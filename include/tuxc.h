@@ -316,28 +316,37 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
  * 32 and an item holds at most two planes): form 0 with Y rounded to bf16 in place in TMEM by
  * two groups of converter warps, so that stage 3 runs as a bf16 MMA with A read from TMEM; phi is
  * double-buffered in TMEM and read by a four-warp epilogue (measured 10% slower than form 0 on
- * the TiO2-shaped block).  All forms give the same result up to float32 summation order (forms 2
- * and 4 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG outside 0..4. */
+ * the TiO2-shaped block).  5 (bf16 only, at most two planes per item, T >= 2): form 0 with two
+ * warps issuing the stage-2 MMAs and two the stage-3 MMAs, each pair taking alternate Gaussian
+ * terms (the stage-3 pair hands a token back and forth so that phi accumulates in term order);
+ * phi is double-buffered in TMEM and read in place by eight epilogue warps (measured 2% faster
+ * than form 0 on the TiO2-shaped block, slower on the Pt-shaped one, where the second phi buffer
+ * leaves room for one plane per item instead of two).  All forms give the same result up to
+ * float32 summation order (forms 2 and 4 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG
+ * outside 0..5. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
 
 /* Host-only description of the expansion kernel (the final contraction of Eq. final with the
  * Hadamard product and the sum over j, the dominant kernel) that tx_exchange_apply and
  * tx_exchange_apply_energy launch for a context of this shape, precision and expansion form
- * (0 to 4, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
- * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 13)
+ * (0 to 5, as tx_set_expansion_form) with the built-in tile plan.  Needs no device and no
+ * context.  n[3], r[3]: grid sizes and Tucker ranks; T: Gaussian terms.  Writes min(nout, 14)
  * values to out:
  *   [0] kernel: 0 float32 CUDA cores, 1 converter kernel (split precisions), 2 one CTA per
  *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items), 4 persistent with
  *       stage 3 in bf16 from shared memory (form 2), 5 persistent with stage 3 in bf16 from
- *       TMEM (form 4)
+ *       TMEM (form 4), 6 persistent with two MMA-issuing warps per stage (form 5)
  *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
  *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs, times y
  *   tiles where an item covers one y tile; with packed last y tiles, the full tiles plus one item
- *   per group of packed planes)   [12] planes whose last y tiles share one item (0: not packed)
+ *   per group of packed planes; converter kernel with z parts: planes x y tiles x z parts)
+ *   [12] planes whose last y tiles share one item (0: not packed)   [13] converter kernel: parts
+ *   of the z columns, one per item, where a whole plane's phi does not fit (then one plane and
+ *   one 128-row y tile per item, and [10] is the columns of one part; 0: whole planes)
  * For the float32 precision every value is 0.  Returns TX_OK; TX_ERR_INVALID_ARG for NULL
- * arrays, nout < 1, T < 1 or a form outside 0..4; TX_ERR_SHAPE for sizes outside
+ * arrays, nout < 1, T < 1 or a form outside 0..5; TX_ERR_SHAPE for sizes outside
  * 2 <= n_d <= 4096, 1 <= r_d <= n_d; TX_ERR_UNSUPPORTED_PRECISION; TX_ERR_UNSUPPORTED_SHAPE
  * where tx_set_precision would refuse the shape. */
 int tx_describe_expansion_plan(const int n[3], const int r[3], int T, int precision, int form, int* out, int nout);

@@ -502,14 +502,15 @@ def tx_set_expansion_form(ctx, form):
     """Single-pass precisions: 0 = automatic (persistent expansion kernel where it applies, short
     last y tiles of several planes packed into one item; default), 1 = one CTA per item,
     2 = persistent with stage 3 in bf16 (bf16 only), 3 = automatic without the packing,
-    4 = persistent with Y rounded to bf16 in TMEM so that stage 3 runs in bf16 (bf16 only)."""
+    4 = persistent with Y rounded to bf16 in TMEM so that stage 3 runs in bf16 (bf16 only),
+    5 = persistent with two stage-2 and two stage-3 MMA issuing warps (bf16 only)."""
     _check(lib().tx_set_expansion_form(ctx.handle, int(form)), "tx_set_expansion_form")
 
 
 PLAN_FIELDS = ("kernel", "planes", "stages2", "stages3", "ybuffers", "tmem_cols", "smem_bytes", "threads",
-               "ksteps2", "ksteps3", "n3p", "items_per_pair", "tail_planes")
+               "ksteps2", "ksteps3", "n3p", "items_per_pair", "tail_planes", "z_parts")
 PLAN_KERNELS = {0: "float32", 1: "converter", 2: "per_item", 3: "persistent", 4: "persistent_bf16",
-                5: "persistent_bf16_tmem"}
+                5: "persistent_bf16_tmem", 6: "persistent_dual_issue"}
 
 
 def tx_describe_expansion_plan(n, r, T, precision, form=0):

@@ -114,9 +114,9 @@ extern "C" int tx_set_accumulation_chunk(tx_ctx* c, int terms) {
 
 extern "C" int tx_set_expansion_form(tx_ctx* c, int form) {
     if (!c || c->magic != kMagic) return fail(TX_ERR_NOT_SETUP, "context is NULL or was destroyed");
-    if (form < 0 || form > 4)
+    if (form < 0 || form > 5)
         return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic), 1 (one CTA per item), 2 (bf16 stage 3), 3 "
-                                        "(automatic without packed y tiles) or 4 (bf16 stage 3 from TMEM)");
+                                        "(automatic without packed y tiles), 4 (bf16 stage 3 from TMEM) or 5 (dual MMA issuers)");
     if (form == c->consume_form) return TX_OK;
     c->consume_form = form;
     // the two forms' kernels read per-term operator images of different layouts
@@ -128,9 +128,9 @@ extern "C" int tx_describe_expansion_plan(const int n[3], const int r[3], int T,
                                           int nout) {
     if (!n || !r || !out || nout < 1) return fail(TX_ERR_INVALID_ARG, "n, r and out must not be NULL; nout >= 1");
     if (T < 1) return fail(TX_ERR_INVALID_ARG, "T must be >= 1");
-    if (form < 0 || form > 4)
+    if (form < 0 || form > 5)
         return fail(TX_ERR_INVALID_ARG, "form must be 0 (automatic), 1 (one CTA per item), 2 (bf16 stage 3), 3 "
-                                        "(automatic without packed y tiles) or 4 (bf16 stage 3 from TMEM)");
+                                        "(automatic without packed y tiles), 4 (bf16 stage 3 from TMEM) or 5 (dual MMA issuers)");
     if (precision < TX_PREC_FP32 || precision > TX_PREC_BF16X3)
         return fail(TX_ERR_UNSUPPORTED_PRECISION, "unknown precision");
     for (int d = 0; d < 3; ++d) {

@@ -86,6 +86,9 @@ struct ConsumeArgs {
     int nys;                   // bf16 persistent kernel: Y operand tiles in shared memory
     uint32_t ys_off, ys_bytes, ys_tile;   // ... their offset, stride per buffer, stride per tile
     uint32_t epi_off;
+    // split kernel, y/z items: each CTA covers one 128-row y tile (of nyi per plane) and one part
+    // of nzi of the z columns (n3p of them) of one plane; 0: the CTA covers its whole slab
+    int yz, nzi;
 };
 
 constexpr int kThreads = 320;
@@ -149,7 +152,8 @@ __device__ __forceinline__ void convert_chunk(const float* v, uint4& hi, uint4& 
 // rows(jt, r, x, y) gives the grid point (x, y) of row r of tile jt and whether it exists.
 template <typename Rows>
 __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const PairRec& rec, uint8_t* smem,
-                                                   uint32_t tPhi, int nTiles, int warp, int lane, Rows rows) {
+                                                   uint32_t tPhi, int nTiles, int warp, int lane, Rows rows,
+                                                   int z0 = 0) {
     const int q = warp & 3, h = warp >> 2;
     double e = 0.0;
     const long N3 = (long)a.n1 * a.n2 * a.n3;
@@ -174,11 +178,13 @@ __device__ __forceinline__ double consume_epilogue(const ConsumeArgs& a, const P
     float4* lbuf = (float4*)(smem + kStgBytes) + warp * (2 * 8 * 2 * 32);   // [buf][it][m][lane]
     const int sub = lane >> 4;
     const int ncb = (a.n3p + 63) / 64, nblk = nTiles * ncb;
-    // row, grid offset and validity of iteration `it` of block `blk` for this lane
+    // row, grid offset and validity of iteration `it` of block `blk` for this lane (phi column
+    // zl of the item is grid column z = z0 + zl)
     auto locate = [&](int blk, int it, int& x, int& y, int& z, int& idx) -> bool {
         const int jt = blk / ncb, cb = (blk - jt * ncb) * 64;
-        z = cb + 4 * (lane & 15);
-        if (!rows(jt, q * 32 + 2 * h + 4 * it + sub, x, y) || z >= a.n3) return false;
+        const int zl = cb + 4 * (lane & 15);
+        z = z0 + zl;
+        if (!rows(jt, q * 32 + 2 * h + 4 * it + sub, x, y) || z >= a.n3 || zl >= a.n3p) return false;
         idx = (x * a.n2 + y) * a.n3 + z;       // < 256^3; a multiple of 4 (n3 % 4 == 0)
         return true;
     };
@@ -430,7 +436,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ double red[8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slab = blockIdx.x, pl = blockIdx.y;
+    // with y/z items (one plane per slab) blockIdx.x = (slab * nyi + iy) * nzi + iz: rows
+    // y0 .. y0 + 127 of the plane and the columns z0 .. z0 + n3p - 1
+    const int nyz = a.yz ? a.nyi * a.nzi : 1;
+    const int slab = (int)blockIdx.x / nyz, iyz = (int)blockIdx.x - slab * nyz, pl = blockIdx.y;
+    const int y0 = a.yz ? (iyz / a.nzi) * 128 : 0, z0 = a.yz ? (iyz % a.nzi) * a.n3p : 0;
     const int x0 = slab * a.bx;
     const PairRec rec = a.recs[a.p0 + pl];
     const int NL = a.nload, NA = a.na3, BX = a.bx;
@@ -508,8 +518,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int tt = term_of(t);
                 const int zdep = pl * a.nt + tt;
                 for (int k = 0; k < a.ks2; ++k) {
-                    tma_load_3d(YAs(s) + k * ya_sub, &mA2, &full_bar[s], k * MK, 0, tt);
-                    if constexpr (SPLIT) tma_load_3d(YAs(s) + a.ya_bytes + k * ya_sub, &mA2lo, &full_bar[s], k * MK, 0, tt);
+                    tma_load_3d(YAs(s) + k * ya_sub, &mA2, &full_bar[s], k * MK, y0, tt);
+                    if constexpr (SPLIT) tma_load_3d(YAs(s) + a.ya_bytes + k * ya_sub, &mA2lo, &full_bar[s], k * MK, y0, tt);
                     // plane p's rows start at row p * Nz (a multiple of 16) of the Z tile
                     for (int p = 0; p < BX; ++p) {
                         const uint32_t off = k * z_sub + (uint32_t)(p * a.Nz) * 32u;
@@ -519,9 +529,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 for (int k = 0; k < a.ks3; ++k) {
-                    tma_load_3d(B3s(s) + k * a.n3p * 32u, &mA3, &full_bar[s], k * MK, 0, tt);
+                    tma_load_3d(B3s(s) + k * a.n3p * 32u, &mA3, &full_bar[s], k * MK, z0, tt);
                     if constexpr (SPLIT)
-                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 32u, &mA3lo, &full_bar[s], k * MK, 0, tt);
+                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 32u, &mA3lo, &full_bar[s], k * MK, z0, tt);
                 }
             }
             if (!ok)
@@ -635,6 +645,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         double e = 0.0;
         auto rows_of = [&](int jt, int r, int& x, int& y) {
             const int m3 = jt * 128 + r;
+            if (a.yz) {                      // one plane, rows y0 .. y0 + 127
+                y = y0 + m3;
+                x = x0;
+                return m3 < 128 && y < a.n2 && x < a.n1;
+            }
             const int xl = m3 / a.n2;
             y = m3 - xl * a.n2;
             x = x0 + xl;
@@ -654,8 +669,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int p = h; p < BX; p += 2) {
                     for (int i = 0; i < a.nY; ++i) {
                         const int y = i * 128 + q * 32 + lane;
-                        const bool valid = y < a.n2;
-                        const uint32_t m3 = (uint32_t)(p * a.n2 + y);
+                        const bool valid = y0 + y < a.n2;
+                        const uint32_t m3 = (uint32_t)(a.yz ? y : p * a.n2 + y);
                         const uint32_t col = tY + ((uint32_t)(q * 32) << 16) + (uint32_t)((i * BX + p) * a.Nz);
                         for (int g0 = 0; g0 < a.r3; g0 += 64) {
                             const int nck = min(4, (min(a.Nz, g0 + 64) - g0) / 16);
@@ -730,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("bar.sync 1, 256;" ::: "memory");
             tc_fence_after();
-            e += consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, rows_of);
+            e += consume_epilogue(a, rec, smem, tPhi, a.nT3, warp, lane, rows_of, z0);
         } else {
             asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight warps meet here on every path
         }
@@ -744,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if ((a.flags & EPI_ENERGY) && threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += red[w];
-        a.epart[(long)pl * gridDim.x + slab] = s;
+        a.epart[(long)pl * gridDim.x + blockIdx.x] = s;
     }
     if (warp == 8) tmem_dealloc(tmem, a.tmem_cols);
 }
@@ -1086,18 +1101,24 @@ __global__ void __launch_bounds__(kThreadsTs, 1)
 // warp holds at most one tile (bx <= 2, bx * nY <= 2) and n3p <= 96.
 constexpr int kTpMaxZ = 96;                           // phi registers per epilogue lane
 constexpr int kThreadsTpB = 512;                      // bf16-in-TMEM form: warps 4-7 and 12-15 convert, 0-3 epilogue
+constexpr int kThreadsTpD = 448;                      // dual-issuer form: second stage-2 and stage-3 MMA warps (12, 13)
 constexpr uint32_t kTpEpiBytes = 0;                   // the epilogue reads the orbitals directly
 
-template <bool S2TF32, int KS2, int KS3, bool BF3 = false>
-__global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
+template <bool S2TF32, int KS2, int KS3, bool BF3 = false, bool DUAL = false>
+__global__ void __launch_bounds__(BF3 ? kThreadsTpB : (DUAL ? kThreadsTpD : kThreadsTp), 1)
     k_consume_tp(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ EpiMaps em, ConsumeArgs a) {
+    static_assert(!(BF3 && DUAL), "one form at a time");
     constexpr int AK2 = S2TF32 ? 32 : 64;    // stage-2 elements per 128-byte atom (4 MMA K steps)
-    constexpr int NTHR = BF3 ? kThreadsTpB : kThreadsTp;
+    constexpr int NTHR = BF3 ? kThreadsTpB : (DUAL ? kThreadsTpD : kThreadsTp);
+    constexpr bool PHI2 = BF3 || DUAL;       // phi double-buffered in TMEM, read by the epilogue in place
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], full3[kMaxLoad], empty3[kMaxLoad];
     __shared__ uint64_t s2bar[kMaxYBuf], ybar[kMaxYBuf], phidone, phifree, s3fin[2], ebar[8];
     __shared__ uint64_t cvtbar[kMaxYBuf];      // BF3: Y of the buffer converted to bf16
-    __shared__ uint64_t phid[2], phif[2];      // BF3: phi buffer b complete / read by the epilogue
+    __shared__ uint64_t phid[2], phif[2];      // BF3, DUAL: phi buffer b complete / read by the epilogue
+    __shared__ uint64_t tok[2];                // DUAL: stage-3 MMAs of the even (0) / odd (1) terms issued
+    __shared__ uint64_t tok2[2];               // DUAL: stage-2 operands of the even / odd terms arrived
+    __shared__ uint64_t fin2[2];               // DUAL: final commits of MMA warps 12 and 13
     __shared__ uint32_t tmem_base;
     __shared__ double red[2][8];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1147,8 +1168,11 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
             mbar_init(&cvtbar[b], 4);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&phid[b], 1);
-            mbar_init(&phif[b], 4);
+            mbar_init(&phid[b], DUAL ? 2 : 1);
+            mbar_init(&phif[b], DUAL ? 8 : 4);
+            mbar_init(&tok[b], 1);
+            mbar_init(&tok2[b], 1);
+            mbar_init(&fin2[b], 1);
         }
         mbar_init(&phidone, 1);
         mbar_init(&phifree, 8);
@@ -1172,7 +1196,7 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t tPhi = tmem + (uint32_t)NYB * a.y_cols;
-    const uint32_t phi_cols = (uint32_t)(a.nT3 * a.n3p);      // BF3: phi is double-buffered
+    const uint32_t phi_cols = (uint32_t)(a.nT3 * a.n3p);      // BF3, DUAL: phi is double-buffered
     const uint32_t ya_atom = a.ya_rows * 128u, z_atom = a.z_rows * 128u, b3_atom = (uint32_t)a.n3p * 128u;
     const uint32_t img_atom = a.img_ya_rows * 128u, img_ya_bytes = img_atom * (uint32_t)((a.ks2 + 3) / 4);
     const int na3f = a.ks3 / 4;
@@ -1237,7 +1261,10 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
             bulk_prefetch_l2_w(a.zsrc + ((size_t)pl * NT * a.n1 + x0) * a.z_plane + (size_t)t * zterm,
                                (uint32_t)np_ * a.z_plane);
         };
-        for (int g = 1; g <= NL + 2; ++g) prefetch(g);
+        // (the dual-issuer form leaves the Z tiles to the copies themselves: a prefetch holds the
+        // issuing warp for hundreds of cycles, which this warp cannot spare at its term rate)
+        if (!DUAL)
+            for (int g = 1; g <= NL + 2; ++g) prefetch(g);
         int issued = 0, s = 0, g = 0;
         uint32_t ph = 0;
         bool ok = true;
@@ -1248,13 +1275,20 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 ++issued;
                 mbar_arrive_expect_tx_w(&full3[s], a.b3_bytes);
                 bulk_load_w(B3s(s), a.img + (size_t)t * a.img_stride + img_ya_bytes, a.b3_bytes, &full3[s]);
-                if (g > 0) prefetch(g + NL + 2);
+                if (!DUAL && g > 0) prefetch(g + NL + 2);
                 if (++s == NL3) { s = 0; ph ^= 1; }
             }
         if (!ok)
             for (int q = (issued > NL3 ? issued - NL3 : 0); q < issued; ++q) mbar_drain(&full3[q % NL3], (q / NL3) & 1, a.err);
-    } else if (warp == 9) {
+    } else if (warp == 9 || (DUAL && warp == 12)) {
         // ------------------------------ stage-2 MMA issuer ------------------------------
+        // (dual-issuer form: warp 9 takes the even terms g of this CTA's sequence, warp 12 the
+        // odd ones; each walks the whole sequence to keep the ring stages and Y buffers in step.
+        // Terms of different parity write different Y buffers, so their MMAs need no order, but
+        // the waits do: a warp waits for the stages of term g only after the other has seen
+        // those of term g - 1 arrive (a token), so that every wait finds its barrier at most one
+        // phase behind, as with a single consumer)
+        const int mine = DUAL ? (warp == 12 ? 1 : 0) : -1;
         const uint64_t d0 = sdesc_sw128(0);
         const int n0 = pad16c(min(a.npc, BX) * a.gs);
         const uint32_t id0 = S2TF32 ? idesc_tf32(128, n0) : idesc_bf16(128, n0);
@@ -1268,15 +1302,24 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
             const bool tail = is_tail(iy);
             const int nsub = tail ? min(a.tailp, a.n1 - slab_ * a.tailp) : 1;
             for (int t = 0; t < NT && ok; ++t, ++g) {
+                if (DUAL && (g & 1) != mine) {
+                    for (int sp = 0; sp < nsub; ++sp)
+                        if (++s == NL) { s = 0; ph ^= 1; }
+                    if (++yb == NYB) { yb = 0; yph ^= 1; }
+                    continue;
+                }
                 const uint32_t tY = tmem + (uint32_t)yb * a.y_cols;
                 // a tail item accumulates the windows of its planes into one Y buffer: each window
                 // is zero outside its plane's rows, so every plane lands in its own TMEM lanes
                 for (int sp = 0; sp < nsub; ++sp) {
-                    bool w = mbar_wait(&full_bar[s], ph, a.err, 42);
+                    bool w = true;
+                    if (DUAL && sp == 0 && g > 0) w = mbar_wait(&tok2[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), a.err, 53);
+                    if (w) w = mbar_wait(&full_bar[s], ph, a.err, 42);
                     // Y buffer yb was last read by stage 3 of term g - nyb
                     if (w && sp == 0 && g >= NYB) w = mbar_wait(&ybar[yb], yph ^ 1, a.err, 43);
                     ok = __all_sync(0xffffffffu, w);
                     if (!ok) break;
+                    if (DUAL && sp == nsub - 1 && lane == 0) mbar_arrive(&tok2[g & 1]);
                     tc_fence_after();
                     // the item's first y tile: rows iy * 128 of the A_t2 tile (1024 descriptor units)
                     const uint64_t ya = d0 + (smem_u32(YAs(s)) >> 4) + (tail ? 0u : (uint32_t)iy * 1024u),
@@ -1300,27 +1343,40 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
             }
         }
         // the CTA must not release TMEM while these MMAs run
-        mma_commit_w(&s3fin[0]);
-        mbar_drain(&s3fin[0], 0, a.err);
-    } else if (warp == 11) {
+        uint64_t* fb = (DUAL && warp == 12) ? &fin2[0] : &s3fin[0];
+        mma_commit_w(fb);
+        mbar_drain(fb, 0, a.err);
+    } else if (warp == 11 || (DUAL && warp == 13)) {
         // ---------------- stage-3 MMA issuer: every plane and y tile ----------------
+        // (dual-issuer form: warp 11 takes the even terms, warp 13 the odd ones.  All terms of an
+        // item accumulate into one phi, so the two hand a token back and forth: a warp issues the
+        // MMAs of term g only after the other has issued those of term g - 1, with tcgen05 fences
+        // around the hand-over, which keeps every MMA into phi in term order)
+        const int mine = DUAL ? (warp == 13 ? 1 : 0) : -1;
         const uint64_t d0 = sdesc_sw128(0);
         const uint32_t id3 = BF3 ? idesc_bf16(128, a.n3p) : idesc_tf32(128, a.n3p);
-        int s3 = 0, yb = 0;
+        int s3 = 0, yb = 0, g = 0;
         uint32_t ph3 = 0, yph = 0;
         bool ok = true;
         for (int k = 0; k < nmine && ok; ++k)
-            for (int t = 0; t < NT; ++t) {
+            for (int t = 0; t < NT; ++t, ++g) {
+                if (DUAL && (g & 1) != mine) {
+                    if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
+                    if (++yb == NYB) { yb = 0; yph ^= 1; }
+                    continue;
+                }
                 // BF3: Y is read once the converters have rounded it to bf16 in place
                 bool w = mbar_wait(BF3 ? &cvtbar[yb] : &s2bar[yb], yph, a.err, 44);
                 if (w) w = mbar_wait(&full3[s3], ph3, a.err, 48);
-                // the accumulator is free once the epilogue of the previous item holds phi (BF3:
-                // once the epilogue of item k - 2 has read this item's phi buffer)
-                if constexpr (BF3) {
+                // the accumulator is free once the epilogue of the previous item holds phi (BF3,
+                // DUAL: once the epilogue of item k - 2 has read this item's phi buffer)
+                if constexpr (PHI2) {
                     if (w && t == 0 && k > 1) w = mbar_wait(&phif[k & 1], (uint32_t)(((k - 2) >> 1) & 1), a.err, 50);
                 } else {
                     if (w && t == 0 && k > 0) w = mbar_wait(&phifree, (uint32_t)((k - 1) & 1), a.err, 50);
                 }
+                // DUAL: term g - 1 (the other warp's) has been issued: its (g - 1) / 2-th token
+                if (DUAL && w && g > 0) w = mbar_wait(&tok[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), a.err, 52);
                 ok = __all_sync(0xffffffffu, w);
                 if (!ok) break;
                 tc_fence_after();
@@ -1330,7 +1386,7 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 const uint32_t acc0 = t > 0 ? 1u : 0u;
                 for (int p = 0; p < BX; ++p)
                     for (int i = 0; i < a.nY; ++i) {
-                        const uint32_t dT = tPhi + (BF3 ? (uint32_t)(k & 1) * phi_cols : 0u) +
+                        const uint32_t dT = tPhi + (PHI2 ? (uint32_t)(k & 1) * phi_cols : 0u) +
                                             (uint32_t)((p * a.nY + i) * a.n3p);
                         const uint32_t aT = tY + (uint32_t)(i * a.ycol_tile + p * a.gs);
                         if constexpr (BF3)
@@ -1338,15 +1394,22 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                         else
                             s3_mmas<KS3>(a.ks3, dT, aT, b3, b3t, b3_atom >> 4, (uint32_t)a.n3p * 2u, id3, acc0);
                     }
+                if (DUAL) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tok[g & 1]);
+                }
                 mma_commit_w(&ybar[yb]);
                 mma_commit_w(&empty3[s3]);
-                if (t == NT - 1) mma_commit_w(BF3 ? &phid[k & 1] : &phidone);
+                // DUAL: each warp commits phi after its own last term of the item (count 2)
+                if (DUAL ? t + 2 >= NT : t == NT - 1) mma_commit_w(PHI2 ? &phid[k & 1] : &phidone);
                 if (++s3 == NL3) { s3 = 0; ph3 ^= 1; }
                 if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
         // the CTA must not release TMEM while these MMAs run
-        mma_commit_w(&s3fin[1]);
-        mbar_drain(&s3fin[1], 0, a.err);
+        uint64_t* fb = (DUAL && warp == 13) ? &fin2[1] : &s3fin[1];
+        mma_commit_w(fb);
+        mbar_drain(fb, 0, a.err);
     } else if (BF3 && warp >= 4) {
         // ---------------- BF3 converters: Y -> bf16 in place ----------------
         // Two groups of four warps (4-7 and 12-15), one warp per TMEM lane quadrant, take
@@ -1407,12 +1470,15 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 }
                 if (++yb == NYB) { yb = 0; yph ^= 1; }
             }
-    } else if (BF3) {
-        // ---------------- BF3 epilogue, warps 0-3 (one lane quadrant each) ----------------
+    } else if (PHI2) {
+        // ------- BF3 epilogue, warps 0-3 (one lane quadrant each); DUAL: warps 0-7 -------
         // phi is double-buffered in TMEM, so the epilogue reads it chunk by chunk (16 columns)
         // while the next item accumulates into the other buffer, and releases the buffer when
-        // the item is done.  Each lane walks its own grid row as in the other epilogue.
-        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        // the item is done.  Each lane walks its own grid row as in the other epilogue; in the
+        // dual-issuer form the two warps of a lane quadrant take alternate 16-column chunks.
+        constexpr int NE = BF3 ? 4 : 8, NH = NE / 4;
+        const int q = warp & 3, h = warp >> 2;
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
         for (int k = 0; k < nmine; ++k) {
             const bool live = mbar_wait_idle(&phid[k & 1], (uint32_t)((k >> 1) & 1), a.err, 45);
             tc_fence_after();
@@ -1431,14 +1497,14 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 int x, y;
                 bool rowin;
                 if (tail) {
-                    const int l = warp * 32 + lane, pp = l / a.tail_r8, yy = l - pp * a.tail_r8;
+                    const int l = q * 32 + lane, pp = l / a.tail_r8, yy = l - pp * a.tail_r8;
                     x = x0 + pp;
                     y = (a.nyi - 1) * 128 + yy;
                     rowin = pp < a.tailp && yy < a.tail_rows && x < a.n1;
                 } else {
                     const int p = jt / a.nY;
                     x = x0 + p;
-                    y = (iy + jt - p * a.nY) * 128 + warp * 32 + lane;
+                    y = (iy + jt - p * a.nY) * 128 + q * 32 + lane;
                     rowin = x < a.n1 && y < a.n2;
                 }
                 if (!(need0 || need1) || !__any_sync(0xffffffffu, rowin)) continue;
@@ -1449,7 +1515,7 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 float* out0 = o0 ? a.OUT0 + (long)rec.o0 * N3 + rowoff : nullptr;
                 float* out1 = o1 ? a.OUT1 + (long)rec.o1 * N3 + rowoff : nullptr;
                 const uint32_t tb = tPhi + lanes + (uint32_t)(k & 1) * phi_cols + (uint32_t)(jt * a.n3p);
-                for (int zc = 0; zc < a.n3; zc += 16) {
+                for (int zc = 16 * h; zc < a.n3; zc += 16 * NH) {
                     uint32_t ph[16];
                     tmem_ld16(tb + (uint32_t)zc, ph);
                     tmem_ld_wait();
@@ -1489,11 +1555,11 @@ __global__ void __launch_bounds__(BF3 ? kThreadsTpB : kThreadsTp, 1)
                 for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
                 if (lane == 0) red[k & 1][warp] = e * rec.ew;
             }
-            // the four epilogue warps meet once per item (named barrier 1): energy partial
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            // the epilogue warps meet once per item (named barrier 1): energy partial
+            asm volatile("bar.sync 1, %0;" ::"n"(NE * 32) : "memory");
             if ((a.flags & EPI_ENERGY) && warp == 0 && lane == 0) {
                 double sum = 0.0;
-                for (int w = 0; w < 4; ++w) sum += red[k & 1][w];
+                for (int w = 0; w < NE; ++w) sum += red[k & 1][w];
                 a.epart[(long)blockIdx.x + (long)k * gridDim.x] = sum;
             }
         }
@@ -2112,8 +2178,13 @@ struct ConsumePlan {
     int tailp, tail_r8, tail_rows;
     uint32_t sya_rows, sya;  // rows per K atom and bytes of the A_t2 tile in a shared-memory stage
     bool bf3;                // persistent form with Y rounded to bf16 in TMEM: stage 3 in bf16 (form 4)
+    bool dual;               // persistent form with two stage-2 and two stage-3 MMA warps (form 5)
+    // split kernel, y/z items (one plane, one 128-row y tile of nyi and one z part of nzi per CTA)
+    bool yz;
+    int nzi;
     uint32_t img_stride() const { return ya + b3 + (uint32_t)tailp * ya; }
     int items_per_slab_pair(int n1) const {   // work items per pair
+        if (yz) return ((n1 + bx - 1) / bx) * nyi * nzi;
         return tailp ? (n1 / bx) * (nyi - 1) + (n1 + tailp - 1) / tailp : ((n1 + bx - 1) / bx) * (ts ? nyi : 1);
     }
 };
@@ -2152,6 +2223,9 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
     // form 4 (bf16): stage 3 takes Y rounded to bf16 in TMEM, 32 columns at a time
     // (the persistent kernel only: at most two planes per item)
     p->bf3 = !tf32 && c->consume_form == 4 && p->gs % 32 == 0 && bx <= 2 && bx * p->nY <= 2;
+    // form 5 (bf16): two warps issue the stage-2 MMAs and two the stage-3 MMAs, alternate terms
+    // each (the persistent kernel only, at least two terms)
+    p->dual = !tf32 && c->consume_form == 5 && bx <= 2 && bx * p->nY <= 2 && c->T >= 2;
     p->ks3 = p->bf3 ? (r3 + 15) / 16 : (r3 + 7) / 8;
     // columns of one y tile of Y: each plane chunk writes pad16(planes * gs) columns from p0 * gs
     p->ycol_tile = 0;
@@ -2159,8 +2233,9 @@ static bool plan_ts(const tx_ctx* c, bool tf32, int bx, int nload, ConsumePlan* 
         p->ycol_tile = std::max(p->ycol_tile, p0 * p->gs + pad16(std::min(p->npc, bx - p0) * p->gs));
     p->y_cols = (uint32_t)(p->nY * p->ycol_tile);
     p->nT3 = bx * p->nY;
-    // (form 4 keeps two phi buffers, so that its epilogue reads one while the next item fills the other)
-    const uint32_t phi = (uint32_t)(p->nT3 * p->n3p) * (p->bf3 ? 2u : 1u);
+    // (forms 4 and 5 keep two phi buffers, so that the epilogue reads one while the next item
+    // fills the other)
+    const uint32_t phi = (uint32_t)(p->nT3 * p->n3p) * ((p->bf3 || p->dual) ? 2u : 1u);
     // one Y buffer per load stage when TMEM allows (the kernel then needs no Y-buffer barrier)
     p->nyb = std::min(nload, tcc::kMaxYBuf);
     while (p->nyb > 2 && p->nyb * p->y_cols + phi > 512) --p->nyb;
@@ -2211,7 +2286,8 @@ static double ts_cost(const ConsumePlan& p) {
     return (p.nY * p.ks2 * s2 + p.nY * p.ks3 * s3) / p.bx;
 }
 
-static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p);
+static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p,
+                    int nzi = 0);
 
 // bf16 persistent plan (k_consume_tb): bx planes, nload stage-2 stages.  phi (double-buffered),
 // at least two float32 Y buffers in TMEM; the stage-3 ring, the bf16 Y tiles and the epilogue
@@ -2308,22 +2384,29 @@ static bool plan_for(const tx_ctx* c, bool tf32, bool split, int bx, int nload, 
     return plan_cv(c, tf32, split, bx, nload, na3, p);
 }
 
-// Converter plan (split precisions)
-static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p) {
+// Converter plan (split precisions).  nzi > 0: y/z items, one plane per CTA, one 128-row y tile
+// of the plane and one of nzi parts of its z columns: for planes whose phi and operand tiles do
+// not fit TMEM, the register accumulator or shared memory whole.
+static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, int na3, ConsumePlan* p, int nzi) {
     const int MK = tf32 ? 8 : 16;
     const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2], r2 = c->r[1], r3 = c->r[2];
     if (bx < 1 || bx > n1 || bx > tcc::kMaxPlanes || nload < 1 || nload > tcc::kMaxLoad || na3 < 1 || na3 > 2)
         return false;
+    if (nzi > 0 && (bx != 1 || nzi > 16)) return false;
     *p = ConsumePlan{};
     p->bx = bx;
     p->n2p = pad16(n2);
-    p->n3p = pad16(n3);
+    p->n3p = nzi > 0 ? pad16((n3 + nzi - 1) / nzi) : pad16(n3);
     p->Nz = pad16(r3);
     if (p->n2p > 256 || p->n3p > 256 || p->Nz > 256) return false;
-    p->nY = (n2 + 127) / 128;
-    p->nq = std::min(4, (n2 + 31) / 32);
+    if (nzi > 0 && (nzi - 1) * p->n3p >= n3) return false;      // no empty z part
+    p->yz = nzi > 0;
+    p->nzi = nzi;
+    p->nyi = nzi > 0 ? (n2 + 127) / 128 : 1;
+    p->nY = nzi > 0 ? 1 : (n2 + 127) / 128;
+    p->nq = std::min(4, (std::min(n2, nzi > 0 ? 128 : n2) + 31) / 32);
     p->npc = std::min(bx, 256 / p->Nz);                  // planes per stage-2 MMA (N <= 256)
-    p->nT3 = (bx * n2 + 127) / 128;
+    p->nT3 = nzi > 0 ? 1 : (bx * n2 + 127) / 128;
     p->ks2 = (r2 + MK - 1) / MK;
     p->ks3 = (r3 + MK - 1) / MK;
     p->y_cols = (uint32_t)(bx * p->nY * p->Nz);
@@ -2399,7 +2482,15 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
                 *best = p;
             }
         }
-    return best_score > 0;
+    if (best_score > 0 || !split) return best_score > 0;
+    // split precisions on planes no whole-slab plan holds: y/z items, the fewest z parts (each
+    // part repeats stage 2), then the deepest pipeline
+    for (int nzi = 1; nzi <= 16; ++nzi) {
+        for (int nl = tcc::kMaxLoad; nl >= 1; --nl)
+            for (int na3 = 2; na3 >= 1; --na3)
+                if (plan_cv(c, tf32, split, 1, nl, na3, best, nzi)) return true;
+    }
+    return false;
 }
 
 // every (bx, stages) that fits, for the autotuner; returns the count written (<= cap)
@@ -2503,7 +2594,7 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
     ConsumePlan p;
     if (!choose_plan(c, tf32, split, &p)) return fail(TX_ERR_UNSUPPORTED_SHAPE, "no expansion tile plan");
     const TpSplit t = (p.ts && !p.tb) ? tp_split(c, p, false, false) : TpSplit{};
-    const int v[13] = {p.tb ? 4 : (t.on ? (p.bf3 ? 5 : 3) : (p.ts ? 2 : 1)),
+    const int v[14] = {p.tb ? 4 : (t.on ? (p.bf3 ? 5 : (p.dual ? 6 : 3)) : (p.ts ? 2 : 1)),
                        p.bx,
                        t.on ? t.nl1 : p.nload,
                        p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
@@ -2511,13 +2602,15 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
                        (int)p.tmem_cols,
                        (int)(t.on ? t.smem : p.smem),
                        p.tb ? tcc::kThreadsTb
-                            : (t.on ? (p.bf3 ? tcc::kThreadsTpB : tcc::kThreadsTp) : (p.ts ? tcc::kThreadsTs : tcc::kThreads)),
+                            : (t.on ? (p.bf3 ? tcc::kThreadsTpB : (p.dual ? tcc::kThreadsTpD : tcc::kThreadsTp))
+                                    : (p.ts ? tcc::kThreadsTs : tcc::kThreads)),
                        p.ks2,
                        p.ks3,
                        p.n3p,
                        p.items_per_slab_pair(c->n[0]),
-                       p.tailp};
-    for (int i = 0; i < nout && i < 13; ++i) out[i] = v[i];
+                       p.tailp,
+                       p.yz ? p.nzi : 0};
+    for (int i = 0; i < nout && i < 14; ++i) out[i] = v[i];
     return TX_OK;
 }
 
@@ -2675,6 +2768,14 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     const int eb = op->esize;
     const uint32_t MK = op->tf32 ? 8 : 16;
     dim3 grid((unsigned)((n1 + p.bx - 1) / p.bx), (unsigned)np);
+    if (p.yz) {
+        // split kernel, y/z items: one CTA per (plane, y tile, z part); A_t2 boxes of 128 rows
+        a.yz = 1;
+        a.nyi = p.nyi;
+        a.nzi = p.nzi;
+        grid.x *= (unsigned)(p.nyi * p.nzi);
+        a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * 128 + p.ks2 * p.bx * r3 + p.ks3 * p.n3p));
+    }
     if (p.ts) {
         a.gs = p.gs; a.ycol_tile = p.ycol_tile; a.ns3 = std::min(p.bx, 8);
         a.nload3 = p.nload3; a.load3_bytes = p.load3;
@@ -2759,6 +2860,10 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
             kern = (Kern)tcc::k_consume_tp<false, 0, 0, true>;
             if (p.ks2 == 4 && p.ks3 == 4) kern = tcc::k_consume_tp<false, 4, 4, true>;
             if (p.ks2 == 3 && p.ks3 == 3) kern = tcc::k_consume_tp<false, 3, 3, true>;
+        } else if (tp && p.dual) {
+            kern = (Kern)tcc::k_consume_tp<false, 0, 0, false, true>;
+            if (p.ks2 == 4 && p.ks3 == 8) kern = tcc::k_consume_tp<false, 4, 8, false, true>;
+            if (p.ks2 == 3 && p.ks3 == 6) kern = tcc::k_consume_tp<false, 3, 6, false, true>;
         } else if (tp) {
             kern = op->tf32 ? (Kern)tcc::k_consume_tp<true, 0, 0> : (Kern)tcc::k_consume_tp<false, 0, 0>;
 #define TX_TP_CASE(TF, K2, K3) \
@@ -2798,7 +2903,9 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         const int ps = prof_begin("tc_consume", s);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (p.bf3 && !tp) return fail(TX_ERR_UNSUPPORTED_SHAPE, "bf16 stage 3 in TMEM needs the persistent kernel");
-        kern<<<grid, tp ? (p.bf3 ? tcc::kThreadsTpB : tcc::kThreadsTp) : tcc::kThreadsTs, smem, s>>>(mZ, em, a);
+        if (p.dual && !tp) return fail(TX_ERR_UNSUPPORTED_SHAPE, "the dual-issuer form needs the persistent kernel");
+        kern<<<grid, tp ? (p.bf3 ? tcc::kThreadsTpB : (p.dual ? tcc::kThreadsTpD : tcc::kThreadsTp)) : tcc::kThreadsTs,
+               smem, s>>>(mZ, em, a);
         prof_end(ps, s);
         TX_LAUNCHED();
         return TX_OK;
@@ -2810,13 +2917,14 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     const int l2 = ldk(r2, eb), l3 = ldk(r3, eb);
     TX_TRY(make_map_sw(&mZ, Z, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b, (uint64_t)n1 * r3 * sc.ld_b, MK,
                        (uint32_t)r3, sw));
-    TX_TRY(make_map_sw(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, MK, (uint32_t)p.n2p, sw));
+    const uint32_t a2_box = p.yz ? 128u : (uint32_t)p.n2p;     // rows of one A_t2 box
+    TX_TRY(make_map_sw(&mA2, op->st.A2, eb, l2, n2, T, l2, (uint64_t)n2 * l2, MK, a2_box, sw));
     TX_TRY(make_map_sw(&mA3, op->st.A3, eb, l3, n3, T, l3, (uint64_t)n3 * l3, MK, (uint32_t)p.n3p, sw));
     if (op->split) {
         TX_TRY(make_map_sw(&mZlo, (const char*)Z + zlo, eb, sc.ld_b, (uint64_t)n1 * r3, (uint64_t)np * T, sc.ld_b,
                            (uint64_t)n1 * r3 * sc.ld_b, MK, (uint32_t)r3, sw));
         TX_TRY(make_map_sw(&mA2lo, (const char*)op->st.A2 + op->st.off_lo, eb, l2, n2, T, l2, (uint64_t)n2 * l2, MK,
-                           (uint32_t)p.n2p, sw));
+                           a2_box, sw));
         TX_TRY(make_map_sw(&mA3lo, (const char*)op->st.A3 + op->st.off_lo, eb, l3, n3, T, l3, (uint64_t)n3 * l3, MK,
                            (uint32_t)p.n3p, sw));
     } else {

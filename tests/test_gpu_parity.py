@@ -284,7 +284,7 @@ def test_expansion_forms_agree(prec, system):
         ref = O.exchange_apply(s.psi, S, psi_tgt=s.psi[3:4])
         assert_close(outs[0][3:4], ref, prec, "forms-pt8")
     with pytest.raises(P.TuckerExchangeError):
-        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 5)
+        P.tx_set_expansion_form(P.Context.from_system(s, precision=prec), 6)
 
 
 @pytest.mark.parametrize("rank,prec,kernel", [(64, "bf16", "persistent"), (64, "tf32", "persistent"),
@@ -319,7 +319,8 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
     window of A_t2).  27 planes in groups of 5 leave a partial group of 2; 150 rows leave a
     22-row tail (two zero rows of padding per plane).  Apply and energy against the unpacked form
     (form 3: the same arithmetic per element, so float32 summation order only) and the oracle;
-    for bf16 also form 4 (stage 3 in bf16 from TMEM) against the oracle."""
+    for bf16 also form 4 (stage 3 in bf16 from TMEM) against the oracle and form 5 (two warps
+    issuing each stage's MMAs, the same arithmetic) against form 0."""
     P = _P()
     d = P.tx_describe_expansion_plan(n, r, 6, prec)
     assert d["kernel"] == "persistent" and d["tail_planes"] == tail
@@ -327,7 +328,7 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
     S = O.Setup.from_system(s)
     occ = to_gpu(s.psi)
     outs, energies = [], []
-    forms = (0, 3, 4) if prec == "bf16" else (0, 3)
+    forms = (0, 3, 4, 5) if prec == "bf16" else (0, 3)
     for form in forms:
         ctx = P.Context.from_system(s, precision=prec)
         P.tx_set_expansion_form(ctx, form)
@@ -344,9 +345,36 @@ def test_packed_short_y_tiles_match_the_unpacked_kernel_and_the_oracle(prec, n, 
         assert P.tx_describe_expansion_plan(n, r, 6, prec, 4)["kernel"] == "persistent_bf16_tmem"
         assert_close(outs[2], ref, prec, f"packed-{n[0]}x{n[1]}-bf16tmem")
         assert abs(energies[2] - energies[0]) <= E_TOL[prec] * abs(energies[0])
+        # form 5: the same MMAs in the same term order, issued by two warps per stage
+        assert P.tx_describe_expansion_plan(n, r, 6, prec, 5)["kernel"] == "persistent_dual_issue"
+        assert rel(outs[3], outs[0]) < 1e-5 and elem_rel(outs[3], outs[0])[0] < 1e-5
+        assert abs(energies[3] - energies[0]) <= 1e-5 * abs(energies[0])
     e_ref = O.exchange_energy(s.psi, S)
     log_energy(prec, f"packed-{n[0]}x{n[1]}", energies[0], e_ref)
     assert abs(energies[0] - e_ref) / abs(e_ref) < E_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("n,r,items", [((5, 150, 160), (5, 64, 64), 20), ((4, 100, 200), (4, 40, 64), 8)])
+def test_split_precisions_on_y_z_items_match_oracle(prec, n, r, items):
+    """Planes too large for the split kernel's whole-slab plan (phi and its cross-product
+    accumulator exceed TMEM, or the register accumulator): one CTA per (plane, 128-row y tile,
+    z part).  150 rows leave a 22-row second tile; 200 columns split 112 + 88.  Apply and energy
+    against the oracle at the split tolerances, elementwise."""
+    P = _P()
+    d = P.tx_describe_expansion_plan(n, r, 6, prec)
+    assert d["kernel"] == "converter" and d["planes"] == 1 and d["items_per_pair"] == items
+    s = ragged_system(n=n, r=r, T=6, n_orb=3, seed=9)
+    S = O.Setup.from_system(s)
+    ctx = P.Context.from_system(s, precision=prec)
+    occ = to_gpu(s.psi)
+    got = P.tx_exchange_apply(ctx, occ).cpu().numpy()
+    e = float(P.tx_exchange_energy(ctx, occ).item())
+    ctx.check_device_error()
+    assert_close(got, O.exchange_apply(s.psi, S), prec, f"yz-{n[1]}x{n[2]}")
+    e_ref = O.exchange_energy(s.psi, S)
+    log_energy(prec, f"yz-{n[1]}x{n[2]}", e, e_ref)
+    assert abs(e - e_ref) / abs(e_ref) < E_TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16"])
@@ -549,10 +577,11 @@ def tio2_case():
     return s, refs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32", "tf32x3"])
 def test_tio2_shaped_block_45_terms(prec, tio2_case):
     """Full target rows of the TiO2-shaped grid at all 45 terms against the oracle (the largest
-    configuration's grid, rank and terms; the bench runs its full 256 x 1842 block)."""
+    configuration's grid, rank and terms; the bench runs its full 256 x 1842 block).  The split
+    precision runs y/z items there (one 128-row y tile and half the z columns per CTA)."""
     s, refs = tio2_case
     got = gpu_apply(s, prec, "self")
     for i, ref in refs.items():

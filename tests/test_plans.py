@@ -85,7 +85,7 @@ def test_every_plan_respects_the_hardware_limits(prec):
     split = prec.endswith("x3")
     mk = 8 if tf32 else 16
     planned = 0
-    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2, 3, 4)):
+    for n, r, T, form in itertools.product(SIZES, RANKS, (1, 40), (0, 1, 2, 3, 4, 5)):
         rr = tuple(min(r, v) for v in n)
         try:
             d = P.tx_describe_expansion_plan(n, rr, T, prec, form)
@@ -98,17 +98,27 @@ def test_every_plan_respects_the_hardware_limits(prec):
         assert d["tmem_cols"] in (32, 64, 128, 256, 512), key
         slabs = -(-n[0] // d["planes"])
         tp = d["tail_planes"]
+        nz = d["z_parts"]
+        if nz:                                  # split kernel, y/z items: plane x y tile x z part
+            assert split and d["kernel"] == "converter" and d["planes"] == 1, key
+            assert d["n3p"] == pad16(-(-n[2] // nz)) and (nz - 1) * d["n3p"] < n[2], key
+            assert d["items_per_pair"] == n[0] * -(-n[1] // 128) * nz, key
+            assert d["ksteps2"] == -(-rr[1] // mk) and d["ksteps3"] == -(-rr[2] // mk), key
+            # TMEM: Y and phi with their cross-product accumulators; phi folds into 4 x 16 registers
+            assert 2 * (pad16(rr[2]) + d["n3p"]) <= d["tmem_cols"] <= 512 and d["n3p"] <= 128, key
+            continue
         if tp:                                  # packed last y tiles: full tiles, then tail groups
             nyf = -(-n[1] // 128)
             rows = n[1] - 128 * (nyf - 1)
-            assert d["planes"] == 1 and tp == 128 // pad8(rows) >= 2 and form in (0, 2, 4), key
+            assert d["planes"] == 1 and tp == 128 // pad8(rows) >= 2 and form in (0, 2, 4, 5), key
             assert d["items_per_pair"] == n[0] * (nyf - 1) + -(-n[0] // tp), key
             yi = nyf
         else:
             yi = d["items_per_pair"] // slabs   # work items per slab: 1, or one per 128-row y tile
             assert d["planes"] >= 1 and d["items_per_pair"] == slabs * yi and yi in (1, -(-n[1] // 128)), key
         if yi > 1:
-            assert d["kernel"] in ("persistent", "persistent_bf16", "persistent_bf16_tmem") and form in (0, 2, 3, 4), key
+            assert d["kernel"] in ("persistent", "persistent_bf16", "persistent_bf16_tmem", "persistent_dual_issue") \
+                and form in (0, 2, 3, 4, 5), key
         assert d["n3p"] == pad16(n[2]), key
         assert d["ksteps2"] == -(-rr[1] // mk), key
         assert d["stages2"] >= 1, key
@@ -131,8 +141,15 @@ def test_every_plan_respects_the_hardware_limits(prec):
             continue
         assert d["ksteps3"] == -(-rr[2] // 8), key                # stage 3 is tf32 with A from TMEM
         assert d["ybuffers"] >= 2 and d["stages3"] >= 2, key
+        if d["kernel"] == "persistent_dual_issue":
+            # two stage-2 and two stage-3 MMA warps, two phi buffers read in place by eight warps
+            assert prec == "bf16" and form == 5 and T >= 2 and d["threads"] == 448, key
+            assert d["planes"] <= 2 and d["stages2"] <= 4, key
+            tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
+            assert tiles <= 2 and d["ybuffers"] * pad8(rr[2]) * d["planes"] + 2 * tiles * d["n3p"] <= 512, key
+            continue
         if d["kernel"] == "persistent":
-            assert form in (0, 2, 3, 4) and d["threads"] == 384, key
+            assert form in (0, 2, 3, 4, 5) and d["threads"] == 384, key
             assert d["planes"] <= 2 and d["stages2"] <= 4, key
             tiles = d["planes"] * (1 if yi > 1 else -(-n[1] // 128))
             assert tiles <= 2, key                                  # at most one phi tile per epilogue warp
@@ -152,7 +169,7 @@ def test_shapes_the_tensor_cores_cannot_take_are_refused():
         P.tx_describe_expansion_plan((12, 13, 300), (3, 4, 5), 3, "fp32")    # float32 kernels: n3 <= 256
     assert ei.value.status == -9
     for bad, status in [(((1, 8, 8), (1, 1, 1), 3, "bf16", 0), -2), (((8, 8, 8), (9, 1, 1), 3, "bf16", 0), -2),
-                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 5), -1)]:
+                        (((8, 8, 8), (2, 2, 2), 0, "bf16", 0), -1), (((8, 8, 8), (2, 2, 2), 3, "bf16", 6), -1)]:
         with pytest.raises(P.TuckerExchangeError) as ei:
             P.tx_describe_expansion_plan(*bad)
         assert ei.value.status == status, bad
