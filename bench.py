@@ -390,6 +390,7 @@ def main():
         if tio2 and not args.no_secondary:
             secondary = pt_secondary(P, W, dev, run_oracle)
             secondary["transfer"] = transfer_secondary(P, W, ctx, psi[:n_tgt], out, peaks)
+            secondary["tio2_split_precision"] = tio2_split_secondary(P, s, psi, ref)
     if world > 1:
         dist.barrier()
     if rank == 0:
@@ -588,6 +589,39 @@ def pt_secondary(P, W, dev, run_oracle_fn):
         ctx.destroy()
     return dict(workload="Pt-cluster-shaped block", n=96, orbitals=64, rank=40, terms=40,
                 err_sample="row 0 against all 64 orbitals", results=res)
+
+
+def tio2_split_secondary(P, s, psi, ref, n_occ=64, n_tgt=16):
+    """The split precision (TF32x3: y/z items, one 128-row y tile and half the z columns per CTA)
+    and the float32 CUDA-core form on the TiO2-shaped block: n_tgt targets against the first n_occ
+    occupied orbitals (one warm-up and two timed applies), and targets 0 and 5 against the first 8
+    occupied orbitals against the oracle's rows (`ref`)."""
+    import numpy as np
+    import torch
+    occ, tgt = psi[:n_occ], psi[:n_tgt]
+    out = torch.empty_like(tgt)
+    res = {}
+    for prec in ("tf32x3", "fp32"):
+        ctx = P.Context.from_system(s, precision=prec)
+        P.tx_exchange_apply(ctx, occ, tgt, out=out)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(2):
+            P.tx_exchange_apply(ctx, occ, tgt, out=out)
+        a1.record()
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / 2
+        occ8 = psi[:8]
+        got = P.tx_exchange_apply(ctx, occ8, occ8[[0, 5]].contiguous()).double().cpu().numpy()
+        ctx.check_device_error()
+        res[prec] = dict(value=n_occ * n_tgt / (ms / 1000.0), unit="pairs/s", ms_per_call=ms, calls=2,
+                         rel_max_abs=float(np.abs(got - ref).max() / np.abs(ref).max()),
+                         rel_frobenius=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        ctx.destroy()
+    return dict(sample=f"{n_tgt} targets against the first {n_occ} occupied orbitals of the block; error: "
+                       "targets 0 and 5 against the first 8", results=res)
 
 
 def dtype_name(prec):
