@@ -2469,19 +2469,25 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
             }
         return best_score > 0;
     }
-    // deepest load pipeline first, then the slab with the least padding per useful row
+    // deepest load pipeline first, then the slab with the least padding per useful row.  With
+    // more than one load stage a single converted stage-3 operand buffer still lets the loads
+    // and stage 2 of the next term run under the conversion and stage 3 of this one (measured
+    // on the Pt-shaped block in TF32x3, one load stage runs load, stage 2, conversion and
+    // stage 3 of every term back to back), so two load stages with one operand buffer rank
+    // above one load stage.
     for (int nl = tcc::kMaxLoad; nl >= 1; --nl)
-        for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx) {
-            ConsumePlan p;
-            if (!plan_for(c, tf32, split, bx, nl, nl > 1 ? 2 : 1, &p)) continue;
-            const double use3 = (double)(bx * c->n[1]) / (p.nT3 * 128.0);
-            const double depth = nl >= 4 ? 1.0 : (nl == 3 ? 0.95 : (nl == 2 ? 0.8 : 0.5));
-            const double score = depth * use3 * (1.0 + 0.03 * std::min(bx, 8));
-            if (score > best_score) {
-                best_score = score;
-                *best = p;
+        for (int bx = 1; bx <= tcc::kMaxPlanes; ++bx)
+            for (int na3 = nl > 1 ? 2 : 1; na3 >= 1; --na3) {
+                ConsumePlan p;
+                if (!plan_for(c, tf32, split, bx, nl, na3, &p)) continue;
+                const double use3 = (double)(bx * c->n[1]) / (p.nT3 * 128.0);
+                const double depth = nl >= 4 ? 1.0 : (nl == 3 ? 0.95 : (nl == 2 ? 0.8 : 0.5));
+                const double score = depth * use3 * (1.0 + 0.03 * std::min(bx, 8)) * (na3 == 2 ? 1.0 : 0.97);
+                if (score > best_score) {
+                    best_score = score;
+                    *best = p;
+                }
             }
-        }
     if (best_score > 0 || !split) return best_score > 0;
     // split precisions on planes no whole-slab plan holds: y/z items, the fewest z parts (each
     // part repeats stage 2), then the deepest pipeline
