@@ -336,7 +336,7 @@ int tx_set_expansion_form(tx_ctx* ctx, int form);
  *       (pair, x slab) item, 3 persistent (one CTA per SM walks the items), 4 persistent with
  *       stage 3 in bf16 from shared memory (form 2), 5 persistent with stage 3 in bf16 from
  *       TMEM (form 4), 6 persistent with two MMA-issuing warps per stage (form 5)
- *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 2, 3)
+ *   [1] x planes per item   [2] stage-2 load stages   [3] stage-3 load stages (kernels 1-3)
  *   [4] stage-2 output buffers in TMEM (kernels 2, 3)   [5] TMEM columns allocated
  *   [6] dynamic shared memory bytes   [7] threads per CTA   [8] MMA K steps of stage 2
  *   [9] MMA K steps of stage 3   [10] n3 padded to 16   [11] items per pair (x slabs, times y

@@ -89,9 +89,14 @@ struct ConsumeArgs {
     // split kernel, y/z items: each CTA covers one 128-row y tile (of nyi per plane) and one part
     // of nzi of the z columns (n3p of them) of one plane; 0: the CTA covers its whole slab
     int yz, nzi;
+    // converter kernel: the stage-3 B operand (mu_t A_t3) has a ring of its own after the
+    // [A_t2][Z] stages, so that stage 2 releases its stage as soon as its MMAs have run
+    uint32_t loadB_bytes, b_off, stageB_tx;
+    int nloadB;
 };
 
 constexpr int kThreads = 320;
+constexpr int kMaxLoadB = 2;       // converter kernel: stages of the stage-3 operand ring
 constexpr int kThreadsTs = 352;   // single-pass kernel: one more producer warp (10)
 constexpr int kThreadsTp = 384;   // persistent single-pass kernel: a separate stage-3 warp (11)
 // epilogue shared memory (reuses the pipeline buffers): phi staging, 8 warps x 32 rows x 68
@@ -431,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int CV = 16 / ES;              // values per 16-byte chunk
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[kMaxLoad], empty_bar[kMaxLoad], a3full[2], a3free[2], phidone;
+    __shared__ uint64_t fullB[kMaxLoadB], emptyB[kMaxLoadB];
     __shared__ uint64_t yfull, yfree, chunkdone, phifree;
     __shared__ uint32_t tmem_base;
     __shared__ double red[8];
@@ -454,10 +460,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Gaussian terms in the order of the exponential sum (theta ascending: wide terms first)
     auto term_of = [&](int t) { return t; };
 
-    // load stage s: [A_t2 tile][Z tile][A_t3 tile], each hi then lo; then the NA stage-3 operands
+    // load stage s: [A_t2 tile][Z tile], each hi then lo; stage-3 stage sb: [A_t3 tile] hi then lo;
+    // then the NA converted stage-3 operands
+    const int NB = a.nloadB;
     auto YAs = [&](int s) { return smem + s * a.load_bytes; };
     auto Zs = [&](int s) { return YAs(s) + (SPLIT ? 2 : 1) * a.ya_bytes; };
-    auto B3s = [&](int s) { return Zs(s) + (SPLIT ? 2 : 1) * a.z_bytes; };
+    auto B3s = [&](int sb) { return smem + a.b_off + sb * a.loadB_bytes; };
     auto A3s = [&](int b) { return smem + a.a3_off + b * (SPLIT ? 2 : 1) * a.a3_bytes; };
 
     if (threadIdx.x == 0) {
@@ -468,6 +476,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&a3full[b], 8);
             mbar_init(&a3free[b], 1);
+        }
+        for (int b = 0; b < kMaxLoadB; ++b) {
+            mbar_init(&fullB[b], 1);
+            mbar_init(&emptyB[b], 1);
         }
         mbar_init(&yfull, 1);
         mbar_init(&yfree, 2 * a.nq);
@@ -500,7 +512,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t a3_sub = (uint32_t)a.nT3 * 128u * 32u;
 
     if (warp == 8) {
-        // ------------------------------ TMA producer ------------------------------
+        // ------------------------------ TMA producers ------------------------------
+        // lane 0: the [A_t2][Z] ring; lane 1: the [mu_t A_t3] ring (each waits on its own ring)
+        if (lane == 1) {
+            int issued = 0;
+            for (int t = 0; t < a.nt; ++t) {
+                const int sb = t % NB;
+                if (!mbar_wait(&emptyB[sb], ((t / NB) & 1) ^ 1, a.err, 39)) break;
+                issued = t + 1;
+                mbar_arrive_expect_tx(&fullB[sb], a.stageB_tx);
+                const int tt = term_of(t);
+                for (int k = 0; k < a.ks3; ++k) {
+                    tma_load_3d(B3s(sb) + k * a.n3p * 32u, &mA3, &fullB[sb], k * MK, z0, tt);
+                    if constexpr (SPLIT)
+                        tma_load_3d(B3s(sb) + a.b3_bytes + k * a.n3p * 32u, &mA3lo, &fullB[sb], k * MK, z0, tt);
+                }
+            }
+            if (issued < a.nt)
+                for (int t = (issued > NB ? issued - NB : 0); t < issued; ++t)
+                    mbar_drain(&fullB[t % NB], (t / NB) & 1, a.err);
+        }
         if (lane == 0) {
             int issued = 0;
             bool ok = true;
@@ -527,11 +558,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if constexpr (SPLIT)
                             tma_load_3d(Zs(s) + a.z_bytes + off, &mZlo, &full_bar[s], k * MK, (x0 + p) * a.r3, zdep);
                     }
-                }
-                for (int k = 0; k < a.ks3; ++k) {
-                    tma_load_3d(B3s(s) + k * a.n3p * 32u, &mA3, &full_bar[s], k * MK, z0, tt);
-                    if constexpr (SPLIT)
-                        tma_load_3d(B3s(s) + a.b3_bytes + k * a.n3p * 32u, &mA3lo, &full_bar[s], k * MK, z0, tt);
                 }
             }
             if (!ok)
@@ -571,10 +597,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 mma_commit(&yfull);
+                mma_commit(&empty_bar[s]);          // the [A_t2][Z] stage is free once these have run
             };
             auto stage3 = [&](int t) {
-                const int s = t % NL, b = t % NA;
-                const uint64_t a3 = d0 + (smem_u32(A3s(b)) >> 4), b3 = d0 + (smem_u32(B3s(s)) >> 4);
+                const int sb = t % NB, b = t % NA;
+                const uint64_t a3 = d0 + (smem_u32(A3s(b)) >> 4), b3 = d0 + (smem_u32(B3s(sb)) >> 4);
                 const bool first = (t % C) == 0;
                 for (int j = 0; j < a.nT3; ++j) {
                     uint64_t ad = a3 + (uint32_t)j * 256u, bd = b3;
@@ -590,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 mma_commit(&a3free[b]);
-                mma_commit(&empty_bar[s]);
+                mma_commit(&emptyB[sb]);
             };
             bool ok = true, fresh = true;
             int t2 = 0, t3 = 0;
@@ -607,6 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 // a new accumulation chunk starts once the previous one has been folded out of TMEM
                 if (t3 < t2 && mbar_try_wait(&a3full[t3 % NA], (t3 / NA) & 1) &&
+                    mbar_try_wait(&fullB[t3 % NB], (t3 / NB) & 1) &&
                     (t3 % C != 0 || t3 == 0 || mbar_try_wait(&phifree, (t3 / C - 1) & 1))) {
                     tc_fence_after();
                     stage3(t3);
@@ -2182,6 +2210,8 @@ struct ConsumePlan {
     // split kernel, y/z items (one plane, one 128-row y tile of nyi and one z part of nzi per CTA)
     bool yz;
     int nzi;
+    uint32_t loadB;          // converter kernel: stride and stages of the stage-3 operand ring
+    int nloadB;
     uint32_t img_stride() const { return ya + b3 + (uint32_t)tailp * ya; }
     int items_per_slab_pair(int n1) const {   // work items per pair
         if (yz) return ((n1 + bx - 1) / bx) * nyi * nzi;
@@ -2424,14 +2454,19 @@ static bool plan_cv(const tx_ctx* c, bool tf32, bool split, int bx, int nload, i
     p->zb = (uint32_t)p->ks2 * p->z_rows * 32u;
     p->b3 = (uint32_t)(p->ks3 * p->n3p * 32);
     p->a3 = (uint32_t)(p->ks3 * p->nT3 * 128 * 32);
-    p->load = (uint32_t)(m * (p->ya + p->zb + p->b3));
-    p->load = (p->load + 1023) & ~1023u;
+    // two rings: nload stages of [A_t2][Z] (released by stage 2), then up to two stages of
+    // [mu_t A_t3] (released by stage 3), then the na3 converted stage-3 A operands
+    p->load = ((uint32_t)(m * (p->ya + p->zb)) + 1023) & ~1023u;
+    p->loadB = ((uint32_t)(m * p->b3) + 1023) & ~1023u;
     p->nload = nload;
     p->na3 = na3;
-    p->a3_off = p->load * nload;
-    const size_t total = (size_t)p->a3_off + (size_t)na3 * m * p->a3;
-    p->smem = std::max(total, (size_t)tcc::kEpiBytes) + 1024;   // the epilogue reuses the front
-    return p->smem <= 226 * 1024;
+    for (p->nloadB = std::min(tcc::kMaxLoadB, nload + 1); p->nloadB >= 1; --p->nloadB) {
+        p->a3_off = p->load * nload + p->loadB * p->nloadB;
+        const size_t total = (size_t)p->a3_off + (size_t)na3 * m * p->a3;
+        p->smem = std::max(total, (size_t)tcc::kEpiBytes) + 1024;   // the epilogue reuses the front
+        if (p->smem <= 226 * 1024) return true;
+    }
+    return false;
 }
 
 static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* best) {
@@ -2482,7 +2517,8 @@ static bool choose_plan(const tx_ctx* c, bool tf32, bool split, ConsumePlan* bes
                 if (!plan_for(c, tf32, split, bx, nl, na3, &p)) continue;
                 const double use3 = (double)(bx * c->n[1]) / (p.nT3 * 128.0);
                 const double depth = nl >= 4 ? 1.0 : (nl == 3 ? 0.95 : (nl == 2 ? 0.8 : 0.5));
-                const double score = depth * use3 * (1.0 + 0.03 * std::min(bx, 8)) * (na3 == 2 ? 1.0 : 0.97);
+                const double score = depth * use3 * (1.0 + 0.03 * std::min(bx, 8)) * (na3 == 2 ? 1.0 : 0.97) *
+                                     (p.nloadB >= 2 ? 1.0 : 0.9);
                 if (score > best_score) {
                     best_score = score;
                     *best = p;
@@ -2603,7 +2639,7 @@ int tc_describe_plan(const tx_ctx* c, int* out, int nout) {
     const int v[14] = {p.tb ? 4 : (t.on ? (p.bf3 ? 5 : (p.dual ? 6 : 3)) : (p.ts ? 2 : 1)),
                        p.bx,
                        t.on ? t.nl1 : p.nload,
-                       p.ts ? (t.on ? t.nl3 : p.nload3) : 0,
+                       p.ts ? (t.on ? t.nl3 : p.nload3) : (p.tb ? 0 : p.nloadB),
                        p.ts ? p.nyb : 0,
                        (int)p.tmem_cols,
                        (int)(t.on ? t.smem : p.smem),
@@ -2762,8 +2798,11 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
     a.ya_rows = p.ya_rows; a.z_rows = p.z_rows; a.img_ya_rows = p.ya_rows;
     a.ya_bytes = p.ya; a.z_bytes = p.zb; a.b3_bytes = p.b3; a.a3_bytes = p.a3;
     a.load_bytes = p.load; a.a3_off = p.a3_off;
-    // bytes the TMA delivers per stage (out-of-range rows and columns count: they are zero-filled)
-    a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * p.n2p + p.ks2 * p.bx * r3 + p.ks3 * p.n3p));
+    // bytes the TMA delivers per stage (out-of-range rows and columns count: they are zero-filled):
+    // converter kernel, [A_t2][Z] stages and the stage-3 operand ring after them
+    a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * p.n2p + p.ks2 * p.bx * r3));
+    a.loadB_bytes = p.loadB; a.nloadB = p.nloadB; a.b_off = p.load * (uint32_t)p.nload;
+    a.stageB_tx = (uint32_t)(m * 32 * p.ks3 * p.n3p);
     a.tmem_cols = p.tmem_cols; a.y_cols = p.y_cols;
     a.p0 = p0; a.recs = recs;
     a.SA = SA; a.SB = SB; a.MUL0 = MUL0; a.MUL1 = MUL1; a.OUT0 = OUT0; a.OUT1 = OUT1;
@@ -2780,7 +2819,7 @@ int tc_consume(const tx_ctx* c, const PairRec* recs, int p0, int np, const void*
         a.nyi = p.nyi;
         a.nzi = p.nzi;
         grid.x *= (unsigned)(p.nyi * p.nzi);
-        a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * 128 + p.ks2 * p.bx * r3 + p.ks3 * p.n3p));
+        a.stage_tx = (uint32_t)(m * 32 * (p.ks2 * 128 + p.ks2 * p.bx * r3));
     }
     if (p.ts) {
         a.gs = p.gs; a.ycol_tile = p.ycol_tile; a.ns3 = std::min(p.bx, 8);
