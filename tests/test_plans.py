@@ -125,8 +125,10 @@ def test_every_plan_respects_the_hardware_limits(prec):
         if split:
             assert d["kernel"] == "converter", key
             assert d["ksteps3"] == -(-rr[2] // mk), key
+            assert 1 <= d["stages3"] <= 2, key     # the stage-3 operand ring
             continue
         if d["kernel"] == "converter":          # single-pass shapes no TMEM plan holds
+            assert 1 <= d["stages3"] <= 2, key     # the stage-3 operand ring
             continue
         if d["kernel"] == "persistent_bf16":
             assert prec == "bf16" and form == 2 and d["threads"] == 512, key
