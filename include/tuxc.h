@@ -320,8 +320,8 @@ int tx_set_accumulation_chunk(tx_ctx* ctx, int terms);
  * warps issuing the stage-2 MMAs and two the stage-3 MMAs, each pair taking alternate Gaussian
  * terms (the stage-3 pair hands a token back and forth so that phi accumulates in term order);
  * phi is double-buffered in TMEM and read in place by eight epilogue warps (measured 2% faster
- * than form 0 on the TiO2-shaped block, slower on the Pt-shaped one, where the second phi buffer
- * leaves room for one plane per item instead of two).  All forms give the same result up to
+ * than form 0 on a 64 x 32 cut of the TiO2-shaped block and equal on the whole block, slower on
+ * the Pt-shaped one, where the second phi buffer leaves room for one plane per item, not two).  All forms give the same result up to
  * float32 summation order (forms 2 and 4 up to the bf16 rounding of Y).  TX_ERR_INVALID_ARG
  * outside 0..5. */
 int tx_set_expansion_form(tx_ctx* ctx, int form);
